@@ -1,0 +1,427 @@
+"""Benchmark of the Kerdock fast sparsifying transform on one GB300 per rank.
+
+One step = one pass of the whole hot path over one batch: build the Kerdock
+sign tables (plan bind), preprocess A into its representation (Lemma 6), and
+answer a batch of thresholded-Ax queries (Algorithm 1's streaming step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs the same
+workload on its own GPU (independent queries, no data-path collective: weak
+scaling); the timing barrier and max-over-ranks use torch.distributed.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "n1024"
+METRIC = "thresholded-Ax queries/sec and preprocess GB/s (frac HBM peak) vs plain FP32 at equal support"
+
+
+def workload_config(wl):
+    return {
+        "workload": (f"n=m={wl.n} random orthogonal A (seeded Gaussian QR), d={wl.n}, "
+                     f"{wl.n // 2 + 1} Kerdock bases, FP32 representation; {wl.queries} queries "
+                     f"x=A^T z, z {wl.s}-sparse +-{wl.amp} + N(0,{wl.noise}^2), eps={wl.eps}, "
+                     f"J={wl.J}, K={wl.K}, S={wl.S}"),
+        "n": wl.n, "m": wl.m, "queries_per_step": wl.queries, "J": wl.J, "K": wl.K, "S": wl.S,
+        "eps": wl.eps, "representation": "f32",
+        "step": "plan tables + preprocess(A) + apply(all queries)",
+        "l2": "256 MiB buffer written between timed steps (L2 flush); the 2.15 GB "
+              "representation is larger than L2 as well",
+    }
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2105_05879_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return p.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, workload):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        t = json.load(fh)
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"kerdock_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2105_05879_gb300 import build as kbuild
+    from paper_2105_05879_gb300 import kerdock as K
+
+    if rank == 0 or world == 1:
+        kbuild.build()
+    if world > 1:
+        dist.barrier()
+    K.load_library()
+    wl = workloads.WORKLOADS[WORKLOAD]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    A_np = wl.make_A().astype(np.float32)
+    X_np = workloads.queries_from_codes(A_np.astype(np.float64), wl.make_codes()).astype(np.float32)
+    A = torch.from_numpy(A_np).to(dev)
+    X = torch.from_numpy(X_np).to(dev)
+    q = X.shape[0]
+
+    plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S, dtype="f32", device=dev)
+    info = plan.info
+    idx, val, cnt = plan.alloc_outputs(q)
+    ws = plan.workspace(q)
+    wsp, wsb = (ws.data_ptr(), ws.numel()) if ws is not None else (None, 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    sptr = stream.cuda_stream
+
+    def step():
+        K.kerdock_plan_bind(plan.handle, plan.repr.data_ptr(), plan.repr.numel(),
+                            plan.table.data_ptr(), plan.table.numel(), sptr)
+        K.kerdock_preprocess(plan.handle, A.data_ptr(), A.stride(0))
+        e_mid.record(stream)
+        K.kerdock_apply(plan.handle, X.data_ptr(), q, X.stride(0), wl.eps, wl.seed_apply, 0,
+                        idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), wsp, wsb)
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e_mid = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    # correctness gate on the warm-up output: every query equals the dense truth
+    A64 = A_np.astype(np.float64)
+    cnt_h = cnt.cpu().numpy()
+    idx_h = idx.cpu().numpy()
+    support_ok = 0
+    V = X_np.astype(np.float64) @ A64.T
+    for r in range(q):
+        truth = np.nonzero(np.abs(V[r]) >= wl.eps)[0]
+        support_ok += np.array_equal(idx_h[r, :cnt_h[r]], truth)
+
+    clocks = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ
+                          else os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_pre, t_app = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        t_pre.append(e0.elapsed_time(e_mid))
+        t_app.append(e_mid.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    plan.sync()
+    step_ms = float(np.sum(t_pre) + np.sum(t_app)) / args.steps
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+        dist.barrier()
+
+    # end to end through the C ABI: pinned host inputs in, results out, every step
+    A_h = torch.from_numpy(A_np).pin_memory()
+    X_h = torch.from_numpy(X_np).pin_memory()
+    idx_hp = torch.empty(idx.shape, dtype=idx.dtype).pin_memory()
+    val_hp = torch.empty(val.shape, dtype=val.dtype).pin_memory()
+    cnt_hp = torch.empty(cnt.shape, dtype=cnt.dtype).pin_memory()
+    A_d = torch.empty_like(A)
+    X_d = torch.empty_like(X)
+
+    def step_e2e():
+        A_d.copy_(A_h, non_blocking=True)
+        X_d.copy_(X_h, non_blocking=True)
+        K.kerdock_plan_bind(plan.handle, plan.repr.data_ptr(), plan.repr.numel(),
+                            plan.table.data_ptr(), plan.table.numel(), sptr)
+        K.kerdock_preprocess(plan.handle, A_d.data_ptr(), A_d.stride(0))
+        K.kerdock_apply(plan.handle, X_d.data_ptr(), q, X_d.stride(0), wl.eps, wl.seed_apply, 0,
+                        idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), wsp, wsb)
+        idx_hp.copy_(idx, non_blocking=True)
+        val_hp.copy_(val, non_blocking=True)
+        cnt_hp.copy_(cnt, non_blocking=True)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    t_e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        step_e2e()
+        e1.record(stream)
+        e1.synchronize()
+        t_e2e.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(t_e2e))
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    h2d = A_np.nbytes + X_np.nbytes
+    d2h = idx.numel() * 4 + val.numel() * 4 + cnt.numel() * 4
+
+    peak, peak_kind = measured_peaks()
+    pre_ms = float(np.mean(t_pre))
+    app_ms = float(np.mean(t_app))
+    eb = 4
+    pre_bytes = info["num_bases"] * info["d"] * info["ldr"] * eb + wl.m * wl.n * 4
+    N = wl.J * wl.K
+    gather_bytes = q * N * info["ldr"] * eb
+    app_bytes = gather_bytes + q * (wl.S * wl.n * 4 + wl.n * 4)
+    pre_gbs = pre_bytes / (pre_ms * 1e6)
+    app_gbs = app_bytes / (app_ms * 1e6)
+    gather_gbs = gather_bytes / (app_ms * 1e6)
+    if app_ms >= pre_ms:
+        roof = {"kernel": "query_kernel", "bound": "hbm", "achieved": round(app_gbs, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(app_gbs / peak, 4),
+                "traffic": profiled_traffic("query_kernel", WORKLOAD),
+                "algorithmic_bytes_per_launch": app_bytes, "peak_source": peak_kind}
+    else:
+        roof = {"kernel": "preprocess_small_kernel", "bound": "hbm", "achieved": round(pre_gbs, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(pre_gbs / peak, 4),
+                "traffic": profiled_traffic("preprocess_small_kernel", WORKLOAD),
+                "algorithmic_bytes_per_launch": pre_bytes, "peak_source": peak_kind}
+
+    result = {
+        "metric": METRIC,
+        "value": round(world * q / (step_ms / 1e3), 2),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded random orthogonal A, sparse codes; Sec. 4 recipe)",
+        "config": dict(workload_config(wl), parallelism=f"replicas x{world} (independent queries)"),
+        "preprocess": {"ms": round(pre_ms, 4), "GB/s": round(pre_gbs, 1),
+                       "frac_hbm": round(pre_gbs / peak, 4), "bytes": pre_bytes},
+        "query": {"ms": round(app_ms, 4), "queries/s": round(q / (app_ms / 1e3), 1),
+                  "GB/s": round(app_gbs, 1), "frac_hbm": round(app_gbs / peak, 4),
+                  "gather_GB/s": round(gather_gbs, 1), "gather_frac_hbm": round(gather_gbs / peak, 4),
+                  "bytes": app_bytes},
+        "support_match_dense": f"{support_ok}/{q}",
+        "roofline": roof,
+        "e2e": {"value": round(world * q / (e2e_ms / 1e3), 2), "unit": "queries/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "source_hash": source_hash(),
+    }
+    if rank == 0 and args.cpu_baseline and world == 1:
+        result["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, budget_s=20.0, queries=None):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
+    workload: the Lemma 6 preprocessing of a subset of bases and the streaming
+    step for a few queries; scaled to queries/s for one full step."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_sample", str(budget_s)]
+    if queries:
+        cmd += ["--_oracle_queries", str(queries)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return {"value": None, "error": out.stderr[-400:]}
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_sample(budget_s, queries=None):
+    from oracle import kerdock as okd
+    from oracle import query as oq
+
+    wl = workloads.WORKLOADS[WORKLOAD]
+    A = wl.make_A().astype(np.float32).astype(np.float64)
+    X = workloads.queries_from_codes(A, wl.make_codes()).astype(np.float32).astype(np.float64)
+    k = int(round(math.log2(wl.n)))
+    nb = wl.n // 2 + 1
+    # preprocessing: as many bases as fit in ~40% of the budget (at least 4)
+    t0 = time.perf_counter()
+    done = 0
+    while done < nb:
+        okd.representation_lemma6(A, k, bases=[done])
+        done += 1
+        if done >= 4 and time.perf_counter() - t0 > 0.4 * budget_s:
+            break
+    t_pre = (time.perf_counter() - t0) / done * nb
+    # streaming step: rows computed lazily (the full FP64 representation is
+    # 4.3 GB; the per-query arithmetic is the same as with it materialised)
+    t1 = time.perf_counter()
+    nq = 0
+    while nq < (queries or wl.queries):
+        oq.apply_one(A, None, X[nq], wl.eps, wl.seed_apply, nq, wl.J, wl.K, wl.S, k, lazy=True)
+        nq += 1
+        if queries is None and nq >= 2 and time.perf_counter() - t1 > 0.6 * budget_s:
+            break
+    t_q = (time.perf_counter() - t1) / nq
+    step_s = t_pre + wl.queries * t_q
+    return {"value": round(wl.queries / step_s, 4), "unit": "queries/s", "cores": 1,
+            "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, 1 thread: Lemma 6 preprocessing of {done}/{nb} bases "
+                       f"and {nq}/{wl.queries} queries (lazy rows), scaled to one step "
+                       f"(preprocess + {wl.queries} queries)"),
+            "preprocess_s_est": round(t_pre, 2), "query_s": round(t_q, 3)}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle, single-threaded, each step a bounded
+    sample (a few Lemma 6 bases + one query) scaled to the same metric."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    wl = workloads.WORKLOADS[WORKLOAD]
+    vals = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        res = cpu_baseline(wl, budget_s=4.0, queries=1)
+        if res.get("value") is None:
+            print(json.dumps({"impl": "reference", "unavailable": res.get("error", "oracle failed")}))
+            return
+        if i >= args.warmup:
+            vals.append(res["value"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * wl.queries / value, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random orthogonal A, sparse codes; Sec. 4 recipe)",
+        "config": dict(workload_config(wl), parallelism="cpu oracle"),
+        "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": 1,
+                         "kind": "oracle", "sample": res["sample"]},
+        "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--_oracle_queries", type=int, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args._oracle_sample is not None:
+        print(json.dumps(oracle_sample(args._oracle_sample, args._oracle_queries)))
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * kerdock.h -- C ABI of the GB300 (sm_103a) Kerdock fast sparsifying transform.
+ *
+ * Method: Fuchs, Gross, Krahmer, Kueng, Mixon, "Sketching with Kerdock's
+ * crayons: fast sparsifying transforms for arbitrary linear maps"
+ * (arXiv 2105.05879).  Problem 1 (Sec. 1.1): preprocess an arbitrary
+ * A in R^{m x n} so that h_eps(Ax), the entrywise eps-hard threshold of Ax,
+ * is fast to compute for every unit x whose Ax is (nearly) s-sparse.
+ * Algorithm 1 gives the two halves this library implements:
+ *
+ *   kerdock_preprocess  -- the preprocessing step: the representation
+ *                          {A s_l : l in [L]} in the d/2+1 real mutually
+ *                          unbiased Kerdock bases, by sign flips and fast
+ *                          Walsh-Hadamard transforms of the rows of A (Lemma 6).
+ *   kerdock_apply       -- the streaming step: draw N = JK indices l_j,
+ *                          y_j = (A s_{l_j})(s_{l_j}^T x), median of means over
+ *                          K batches of J (Theorem 3), top-S of |mu|, exact
+ *                          A_S x, output entries with |value| >= eps.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - d = 2^k is the smallest power of FOUR with d >= n (Lemma 6 needs k even;
+ *    Algorithm 1's "power of 2" is read as "power of 4").  Supported:
+ *    1 <= n <= 4096, 1 <= m <= 4096 with m == n checked by the caller's
+ *    workload only (m != n is accepted).
+ *  - Bases b in [0, d/2) are the Kerdock bases of the field elements with
+ *    integer code b in GF(2^(k-1)) (Prop. 5; polynomial basis, irreducible
+ *    polynomials t+1, t^3+t+1, t^5+t^2+1, t^7+t+1, t^9+t^4+1, t^11+t^2+1;
+ *    basis of V = (t^0,0),...,(t^(k-2),0),(0,1)).  Basis d/2 is the identity.
+ *    Sample index l = b*d + w, L = d*(d/2+1).  s_l = sqrt(d) Pi u_l with
+ *    u_{M,w}(p) = 2^(-k/2) (-1)^(Q_M(p) + w.p) (Eq. "definition of vectors")
+ *    and Pi the projection onto the first n coordinates (Algorithm 1).
+ *  - Representation layout in device memory: R[b][w][i] = (A s_{b,w})_i,
+ *    i contiguous, row stride ldr = m rounded up to a multiple of 8 elements
+ *    (entries i in [m, ldr) are written as 0).  Element type float32 or
+ *    bfloat16 (round-to-nearest-even of the float32 result).
+ *  - Sampling: sample j of query q uses z = SplitMix64 output function applied
+ *    to seed + 0x9E3779B97F4A7C15 * (q*N + j + 1) (mod 2^64) and
+ *    l = floor(z * L / 2^64).  Batch k holds samples j in [kJ, (k+1)J).
+ *  - Median of an even number K of batch means is the mean of the two middle
+ *    values (Sec. 4: K = 2 gives the plain mean).  Top-S ties go to the
+ *    smaller index.  The threshold is inclusive: |v| >= eps (Sec. 1.1).
+ *  - Memory ownership: the library never allocates device memory.  The
+ *    caller allocates the representation, the table buffer, inputs, outputs
+ *    and (optional) workspace and keeps them alive while a plan uses them.
+ *    A plan owns only host metadata.
+ *  - Streams: every launch goes to the stream given to kerdock_plan_bind (or
+ *    kerdock_set_stream).  Calls are asynchronous; results are ready after
+ *    the stream is synchronised (kerdock_sync does that and also reports any
+ *    device-side error recorded by the kernels).
+ *  - Errors: every call returns KERDOCK_OK (0) or a negative KERDOCK_ERR_*.
+ *    No exception crosses the ABI.  Arguments are validated on the host
+ *    before anything is launched; a failing call launches nothing.
+ *  - Threading: a plan must not be used from two host threads at once.
+ */
+#ifndef KERDOCK_H
+#define KERDOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KERDOCK_OK 0
+#define KERDOCK_ERR_INVALID_ARG (-1)      /* null pointer, bad size, bad value */
+#define KERDOCK_ERR_UNSUPPORTED (-2)      /* sizes outside the supported range */
+#define KERDOCK_ERR_NOT_BOUND (-3)        /* plan has no device buffers yet */
+#define KERDOCK_ERR_NOT_PREPROCESSED (-4) /* apply before preprocess */
+#define KERDOCK_ERR_CAPACITY (-5)         /* a caller buffer is too small */
+#define KERDOCK_ERR_CUDA (-6)             /* a CUDA runtime call failed */
+#define KERDOCK_ERR_DEVICE_TIMEOUT (-7)   /* a bounded device-side wait gave up */
+#define KERDOCK_ERR_ALIGNMENT (-8)        /* a device pointer is not 16-byte aligned */
+
+#define KERDOCK_F32 0  /* representation stored as float32 */
+#define KERDOCK_BF16 1 /* representation stored as bfloat16 */
+
+/* kerdock_apply flags */
+#define KERDOCK_FLAG_FULL_OUTPUT 1 /* return all S refined entries, unthresholded
+                                      ("we would not discard this information",
+                                      Sec. 1.1) */
+
+typedef struct kerdock_plan_s* kerdock_plan_t;
+
+typedef struct {
+  int64_t m, n;        /* A is m x n */
+  int32_t k;           /* d = 2^k */
+  int32_t dtype;       /* KERDOCK_F32 / KERDOCK_BF16 */
+  int64_t d;           /* padded dimension, a power of four */
+  int64_t num_bases;   /* d/2 + 1 */
+  int64_t L;           /* design size d*(d/2+1) */
+  int64_t ldr;         /* representation row stride in elements */
+  int32_t J, K, S;     /* batch size, number of batches, candidate-set size */
+  int32_t reserved;
+  size_t repr_bytes;   /* bytes the caller must provide for R */
+  size_t table_bytes;  /* bytes the caller must provide for the tables */
+} kerdock_plan_info_t;
+
+/* Create a plan for an m x n matrix.  dtype: KERDOCK_F32 or KERDOCK_BF16.
+ * J >= 1, 1 <= K <= 16, 1 <= S; S is clamped to m.  N = J*K <= 2^24.
+ * Host only (no CUDA call).  *plan is set to NULL on failure. */
+int kerdock_plan_create(kerdock_plan_t* plan, int64_t m, int64_t n, int32_t dtype,
+                        int32_t J, int32_t K, int32_t S);
+
+/* Fill *info.  Host only. */
+int kerdock_plan_info(kerdock_plan_t plan, kerdock_plan_info_t* info);
+
+/* Attach caller-owned device memory and a CUDA stream (cudaStream_t passed
+ * as void*; NULL = legacy default stream).  repr_dev needs info.repr_bytes
+ * bytes, table_dev info.table_bytes bytes; both 256-byte aligned.  Builds the
+ * Kerdock sign tables D_b on the device (step (i) of Lemma 6: one bit
+ * Q_{M_b}(p) per (b, p), computed from the GF(2^(k-1)) construction of
+ * Prop. 5) and clears the device status word, asynchronously on the stream. */
+int kerdock_plan_bind(kerdock_plan_t plan, void* repr_dev, size_t repr_bytes,
+                      void* table_dev, size_t table_bytes, void* stream);
+
+/* Change the stream later launches of this plan go to. */
+int kerdock_set_stream(kerdock_plan_t plan, void* stream);
+
+/* Preprocessing step of Algorithm 1 / Lemma 6.  A_dev: m x n float32,
+ * row-major with leading dimension lda >= n (elements).  Writes the whole
+ * representation R.  The plan remembers (A_dev, lda): kerdock_apply reads
+ * rows of A for the exact refinement A_S x, so A_dev must stay valid and
+ * unchanged while the plan is applied. */
+int kerdock_preprocess(kerdock_plan_t plan, const float* A_dev, int64_t lda);
+
+/* Bytes of device workspace kerdock_apply needs for q queries (may be 0). */
+size_t kerdock_apply_workspace_bytes(kerdock_plan_t plan, int64_t q);
+
+/* Streaming step of Algorithm 1 for q queries.
+ *   X_dev     q x n float32 row-major, leading dimension ldx >= n.  Used as
+ *             given: the guarantees of Theorem 3 assume unit-norm x.
+ *   eps       threshold (> 0 unless KERDOCK_FLAG_FULL_OUTPUT).
+ *   seed      sampling seed (see the sampling convention above).
+ *   out_idx   q x S int32, out_val q x S float32 (row r of query q at
+ *             offset q*S + r): the kept (index, value) pairs in ascending
+ *             index order; out_count[q] = how many were kept (<= S).
+ *             Entries past out_count[q] are left unspecified.
+ *   ws_dev    workspace of kerdock_apply_workspace_bytes(plan, q) bytes
+ *             (NULL allowed when that is 0).
+ * q = 0 is a valid no-op. */
+int kerdock_apply(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                  float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
+                  float* out_val, int32_t* out_count, void* ws_dev, size_t ws_bytes);
+
+/* Same as kerdock_apply, and additionally writes, when the pointer is not
+ * NULL: mu_out (q x m float32) the median-of-means estimate mu (Theorem 3),
+ * ells_out (q x N int64) the drawn indices l_j, coef_out (q x N float32)
+ * the coefficients s_{l_j}^T x.  For parity tests. */
+int kerdock_apply_debug(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                        float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
+                        float* out_val, int32_t* out_count, void* ws_dev, size_t ws_bytes,
+                        float* mu_out, int64_t* ells_out, float* coef_out);
+
+/* Synchronise the plan's stream and report the first error any kernel of
+ * this plan recorded in the device status word (then clear it). */
+int kerdock_sync(kerdock_plan_t plan);
+
+/* Copy the device sign table to host memory: (d/2) rows of max(1, d/32)
+ * uint32 words; bit (p mod 32) of word p/32 of row b is Q_{M_b}(p).
+ * Synchronises the stream. */
+int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_words);
+
+/* Destroy a plan (host metadata only; NULL is accepted). */
+int kerdock_plan_destroy(kerdock_plan_t plan);
+
+/* Static, human-readable text for an error code. */
+const char* kerdock_strerror(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int kerdock_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KERDOCK_H */

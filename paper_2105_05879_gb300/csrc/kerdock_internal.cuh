@@ -1,0 +1,148 @@
+// kerdock_internal.cuh -- plan object and device helpers shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/kerdock.h"
+
+namespace kd {
+
+constexpr int kMaxLogD = 12;          // d <= 4096
+constexpr int kMaxK = 16;             // number of median-of-means batches
+constexpr int64_t kMaxN = 1 << 24;    // samples per query
+constexpr size_t kStatusBytes = 256;  // status word area at the start of the table buffer
+
+// Device status word codes (first error wins).
+enum : uint32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadIndex = 2 };
+
+struct Plan {
+  int64_t m = 0, n = 0, d = 0, B = 0, L = 0, ldr = 0;
+  int k = 0, dtype = KERDOCK_F32, J = 0, K = 0, S = 0;
+  int64_t N = 0;
+  int64_t sign_words = 0;  // uint32 words per sign-table row: max(1, d/32)
+  size_t repr_bytes = 0, table_bytes = 0;
+  // bound device memory
+  void* repr = nullptr;
+  void* table = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  // preprocess state
+  const float* A = nullptr;
+  int64_t lda = 0;
+  bool preprocessed = false;
+  // device properties
+  int device = -1;
+  int num_sms = 0;
+
+  uint32_t* status() const { return reinterpret_cast<uint32_t*>(table); }
+  uint32_t* signs() const {
+    return reinterpret_cast<uint32_t*>(static_cast<char*>(table) + kStatusBytes);
+  }
+  size_t elem_bytes() const { return dtype == KERDOCK_BF16 ? 2 : 4; }
+};
+
+// Launchers (return KERDOCK_OK or a negative error code).
+int launch_signs(const Plan& p);
+int launch_preprocess(const Plan& p);
+int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps,
+                 uint64_t seed, int flags, int32_t* out_idx, float* out_val,
+                 int32_t* out_count, void* ws, size_t ws_bytes, float* mu_out,
+                 int64_t* ells_out, float* coef_out);
+size_t apply_workspace_bytes(const Plan& p, int64_t q);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Record the first device-side error in the plan's status word.
+__device__ __forceinline__ void set_status(uint32_t* status, uint32_t code) {
+  atomicCAS(status, kStatusOk, code);
+}
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Sample index l_j of the counter-based sampling convention of kerdock.h.
+__device__ __forceinline__ uint64_t sample_index(uint64_t seed, uint64_t ctr, uint64_t L) {
+  const uint64_t z = splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * (ctr + 1));
+  return __umul64hi(z, L);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false after ~2^22 polls (each
+// try_wait itself blocks for a hardware-defined slice), i.e. seconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.
+// dst/src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float flip_sign(float v, uint32_t bit) {
+  return __uint_as_float(__float_as_uint(v) ^ (bit << 31));
+}
+
+}  // namespace kd
+
+#define KD_CUDA_TRY(expr)                           \
+  do {                                              \
+    cudaError_t kd_err_ = (expr);                   \
+    if (kd_err_ != cudaSuccess) return KERDOCK_ERR_CUDA; \
+  } while (0)

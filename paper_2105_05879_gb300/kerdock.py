@@ -1,0 +1,287 @@
+"""Thin Python binding of libkerdock.so (ctypes).
+
+The functions below carry the C-ABI names of ``include/kerdock.h`` and only
+marshal arguments; every step of the transform runs in the library's CUDA
+kernels.  ``KerdockPlan`` adds convenience on top: it lets PyTorch allocate the
+device buffers the library asks for and passes torch's current CUDA stream.
+
+There is no fallback: if the library cannot be loaded, importing the binding
+works but the first call raises ``KerdockError``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+KERDOCK_OK = 0
+KERDOCK_F32 = 0
+KERDOCK_BF16 = 1
+KERDOCK_FLAG_FULL_OUTPUT = 1
+
+_ERRORS = {
+    -1: "KERDOCK_ERR_INVALID_ARG", -2: "KERDOCK_ERR_UNSUPPORTED", -3: "KERDOCK_ERR_NOT_BOUND",
+    -4: "KERDOCK_ERR_NOT_PREPROCESSED", -5: "KERDOCK_ERR_CAPACITY", -6: "KERDOCK_ERR_CUDA",
+    -7: "KERDOCK_ERR_DEVICE_TIMEOUT", -8: "KERDOCK_ERR_ALIGNMENT",
+}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkerdock.so")
+
+# Every symbol include/kerdock.h declares.
+EXPORTED = [
+    "kerdock_plan_create", "kerdock_plan_info", "kerdock_plan_bind", "kerdock_set_stream",
+    "kerdock_preprocess", "kerdock_apply_workspace_bytes", "kerdock_apply",
+    "kerdock_apply_debug", "kerdock_sync", "kerdock_debug_signs", "kerdock_plan_destroy",
+    "kerdock_strerror", "kerdock_version",
+]
+
+
+class KerdockError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        name = _ERRORS.get(code, str(code))
+        text = ""
+        if _lib is not None:
+            text = _lib.kerdock_strerror(code).decode()
+        super().__init__(f"{where}: {name} ({text})")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int32),
+        ("dtype", ctypes.c_int32), ("d", ctypes.c_int64), ("num_bases", ctypes.c_int64),
+        ("L", ctypes.c_int64), ("ldr", ctypes.c_int64), ("J", ctypes.c_int32),
+        ("K", ctypes.c_int32), ("S", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("repr_bytes", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libkerdock.so (built by ``paper_2105_05879_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise KerdockError(-6, f"libkerdock.so not found at {path}; run the build first")
+    lib = ctypes.CDLL(path)
+    c_i64, c_i32, c_vp, c_sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.c_void_p
+    sig = {
+        "kerdock_plan_create": (ctypes.c_int, [ctypes.POINTER(P), c_i64, c_i64, c_i32, c_i32, c_i32, c_i32]),
+        "kerdock_plan_info": (ctypes.c_int, [P, ctypes.POINTER(PlanInfo)]),
+        "kerdock_plan_bind": (ctypes.c_int, [P, c_vp, c_sz, c_vp, c_sz, c_vp]),
+        "kerdock_set_stream": (ctypes.c_int, [P, c_vp]),
+        "kerdock_preprocess": (ctypes.c_int, [P, c_vp, c_i64]),
+        "kerdock_apply_workspace_bytes": (c_sz, [P, c_i64]),
+        "kerdock_apply": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float, ctypes.c_uint64,
+                                         c_i32, c_vp, c_vp, c_vp, c_vp, c_sz]),
+        "kerdock_apply_debug": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float,
+                                               ctypes.c_uint64, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                               c_sz, c_vp, c_vp, c_vp]),
+        "kerdock_sync": (ctypes.c_int, [P]),
+        "kerdock_debug_signs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32), c_sz]),
+        "kerdock_plan_destroy": (ctypes.c_int, [P]),
+        "kerdock_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "kerdock_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, where):
+    if rc != KERDOCK_OK:
+        raise KerdockError(rc, where)
+
+
+# --- C-ABI mirrors -----------------------------------------------------------
+
+def kerdock_plan_create(m, n, dtype, J, K, S):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.kerdock_plan_create(ctypes.byref(h), m, n, dtype, J, K, S), "kerdock_plan_create")
+    return h
+
+
+def kerdock_plan_info(plan):
+    info = PlanInfo()
+    _check(load_library().kerdock_plan_info(plan, ctypes.byref(info)), "kerdock_plan_info")
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_ if f != "reserved"}
+
+
+def kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes, stream):
+    _check(load_library().kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes,
+                                            stream), "kerdock_plan_bind")
+
+
+def kerdock_set_stream(plan, stream):
+    _check(load_library().kerdock_set_stream(plan, stream), "kerdock_set_stream")
+
+
+def kerdock_preprocess(plan, A_ptr, lda):
+    _check(load_library().kerdock_preprocess(plan, A_ptr, lda), "kerdock_preprocess")
+
+
+def kerdock_apply_workspace_bytes(plan, q):
+    return load_library().kerdock_apply_workspace_bytes(plan, q)
+
+
+def kerdock_apply(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr, cnt_ptr, ws_ptr, ws_bytes):
+    _check(load_library().kerdock_apply(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr,
+                                        cnt_ptr, ws_ptr, ws_bytes), "kerdock_apply")
+
+
+def kerdock_apply_debug(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr, cnt_ptr, ws_ptr,
+                        ws_bytes, mu_ptr, ells_ptr, coef_ptr):
+    _check(load_library().kerdock_apply_debug(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
+                                              val_ptr, cnt_ptr, ws_ptr, ws_bytes, mu_ptr,
+                                              ells_ptr, coef_ptr), "kerdock_apply_debug")
+
+
+def kerdock_sync(plan):
+    _check(load_library().kerdock_sync(plan), "kerdock_sync")
+
+
+def kerdock_debug_signs(plan):
+    info = kerdock_plan_info(plan)
+    words = max(1, info["d"] // 32)
+    out = np.zeros((info["d"] // 2, words), dtype=np.uint32)
+    _check(load_library().kerdock_debug_signs(
+        plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out.size), "kerdock_debug_signs")
+    return out
+
+
+def kerdock_plan_destroy(plan):
+    if plan is not None and load_library() is not None:
+        _lib.kerdock_plan_destroy(plan)
+
+
+def kerdock_strerror(code):
+    return load_library().kerdock_strerror(code).decode()
+
+
+def kerdock_version():
+    return load_library().kerdock_version()
+
+
+# --- torch convenience ---------------------------------------------------------
+
+class KerdockPlan:
+    """A plan whose device buffers PyTorch allocates.
+
+    >>> plan = KerdockPlan(m, n, J=375, K=2, S=160, dtype="f32")
+    >>> plan.preprocess(A)                        # A: (m, n) float32 CUDA tensor
+    >>> idx, val, cnt = plan.apply(X, eps, seed)  # X: (q, n) float32 CUDA tensor
+    """
+
+    def __init__(self, m, n, J, K, S, dtype="f32", device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.dtype = KERDOCK_BF16 if dtype in ("bf16", KERDOCK_BF16) else KERDOCK_F32
+        self.device = torch.device(device or "cuda")
+        self.handle = kerdock_plan_create(m, n, self.dtype, J, K, S)
+        self.info = kerdock_plan_info(self.handle)
+        self.repr = torch.empty(self.info["repr_bytes"], dtype=torch.uint8, device=self.device)
+        self.table = torch.empty(self.info["table_bytes"], dtype=torch.uint8, device=self.device)
+        self._stream = stream
+        kerdock_plan_bind(self.handle, self.repr.data_ptr(), self.repr.numel(),
+                          self.table.data_ptr(), self.table.numel(), self._stream_ptr())
+        self.A = None
+        self._ws = None
+
+    def _stream_ptr(self):
+        s = self._stream if self._stream is not None else self.torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def _sync_stream(self):
+        kerdock_set_stream(self.handle, self._stream_ptr())
+
+    @property
+    def S(self):
+        return self.info["S"]
+
+    @property
+    def N(self):
+        return self.info["J"] * self.info["K"]
+
+    def representation(self):
+        """R as a (num_bases, d, ldr) tensor view (float32 or bfloat16)."""
+        t = self.torch
+        dt = t.bfloat16 if self.dtype == KERDOCK_BF16 else t.float32
+        i = self.info
+        return self.repr.view(dt).view(i["num_bases"], i["d"], i["ldr"])
+
+    def preprocess(self, A):
+        t = self.torch
+        assert A.dtype == t.float32 and A.is_cuda and A.dim() == 2 and A.stride(1) == 1
+        self._sync_stream()
+        self.A = A  # the library reads rows of A in kerdock_apply
+        kerdock_preprocess(self.handle, A.data_ptr(), A.stride(0))
+
+    def workspace(self, q):
+        nb = kerdock_apply_workspace_bytes(self.handle, q)
+        if nb == 0:
+            return None
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
+        return self._ws
+
+    def alloc_outputs(self, q):
+        t = self.torch
+        S = self.S
+        return (t.empty((q, S), dtype=t.int32, device=self.device),
+                t.empty((q, S), dtype=t.float32, device=self.device),
+                t.empty((q,), dtype=t.int32, device=self.device))
+
+    def apply(self, X, eps, seed, flags=0, out=None, debug=False):
+        t = self.torch
+        assert X.dtype == t.float32 and X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        q = X.shape[0]
+        idx, val, cnt = out if out is not None else self.alloc_outputs(q)
+        ws = self.workspace(q)
+        wsp, wsb = (ws.data_ptr(), ws.numel()) if ws is not None else (None, 0)
+        self._sync_stream()
+        if not debug:
+            kerdock_apply(self.handle, X.data_ptr(), q, X.stride(0), float(eps), int(seed), flags,
+                          idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), wsp, wsb)
+            return idx, val, cnt
+        m = self.info["m"]
+        mu = t.empty((q, m), dtype=t.float32, device=self.device)
+        ells = t.empty((q, self.N), dtype=t.int64, device=self.device)
+        coef = t.empty((q, self.N), dtype=t.float32, device=self.device)
+        kerdock_apply_debug(self.handle, X.data_ptr(), q, X.stride(0), float(eps), int(seed), flags,
+                            idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), wsp, wsb,
+                            mu.data_ptr(), ells.data_ptr(), coef.data_ptr())
+        return idx, val, cnt, mu, ells, coef
+
+    def sync(self):
+        kerdock_sync(self.handle)
+
+    def signs(self):
+        return kerdock_debug_signs(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            kerdock_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def results_to_lists(idx, val, cnt):
+    """Host lists [(indices, values)] per query from the output tensors."""
+    idx = idx.cpu().numpy()
+    val = val.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    return [(idx[r, :cnt[r]].astype(np.int64), val[r, :cnt[r]].astype(np.float64))
+            for r in range(len(cnt))]

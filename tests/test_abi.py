@@ -1,0 +1,98 @@
+"""The C-ABI library builds, loads and exports every symbol include/kerdock.h
+declares; host-side argument validation works without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2105_05879_gb300 import build as kbuild
+from paper_2105_05879_gb300 import kerdock as K
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kerdock.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    kbuild.build()
+    return K.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kerdock_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_list():
+    assert declared_functions() == sorted(K.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_plan_info_sizes(lib):
+    h = K.kerdock_plan_create(1024, 1024, K.KERDOCK_F32, 375, 2, 160)
+    info = K.kerdock_plan_info(h)
+    assert info["d"] == 1024 and info["k"] == 10 and info["num_bases"] == 513
+    assert info["L"] == 1024 * 513 and info["ldr"] == 1024
+    assert info["repr_bytes"] == 513 * 1024 * 1024 * 4
+    assert info["table_bytes"] == 256 + 512 * 32 * 4
+    K.kerdock_plan_destroy(h)
+    # padding: n = 2048 -> d = 4096 (power of four), m ragged -> ldr multiple of 8
+    h = K.kerdock_plan_create(1001, 2048, K.KERDOCK_BF16, 10, 3, 5000)
+    info = K.kerdock_plan_info(h)
+    assert info["d"] == 4096 and info["ldr"] == 1008 and info["S"] == 1001
+    assert info["repr_bytes"] == 2049 * 4096 * 1008 * 2
+    K.kerdock_plan_destroy(h)
+    for n, d in [(1, 4), (4, 4), (5, 16), (17, 64), (65, 256), (257, 1024), (1025, 4096)]:
+        h = K.kerdock_plan_create(8, n, 0, 1, 1, 1)
+        assert K.kerdock_plan_info(h)["d"] == d
+        K.kerdock_plan_destroy(h)
+
+
+@pytest.mark.parametrize("args,code", [
+    ((0, 4, 0, 1, 1, 1), -1), ((4, 0, 0, 1, 1, 1), -1), ((4, 4, 2, 1, 1, 1), -1),
+    ((4, 4, 0, 0, 1, 1), -1), ((4, 4, 0, 1, 0, 1), -1), ((4, 4, 0, 1, 1, 0), -1),
+    ((4097, 4, 0, 1, 1, 1), -2), ((4, 4097, 0, 1, 1, 1), -2), ((4, 4, 0, 1, 17, 1), -2),
+    ((4, 4, 0, 1 << 21, 16, 1), -2),
+])
+def test_create_rejects_bad_arguments(lib, args, code):
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_plan_create(*args)
+    assert e.value.code == code
+
+
+def test_calls_before_bind_fail_cleanly(lib):
+    h = K.kerdock_plan_create(16, 16, 0, 4, 2, 4)
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_preprocess(h, 1 << 20, 16)
+    assert e.value.code == -3
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_apply(h, 1 << 20, 1, 16, 0.1, 0, 0, 1 << 20, 1 << 20, 1 << 20, None, 0)
+    assert e.value.code == -3
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_sync(h)
+    assert e.value.code == -3
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_plan_bind(h, None, 0, None, 0, None)
+    assert e.value.code == -1
+    info = K.kerdock_plan_info(h)
+    with pytest.raises(K.KerdockError) as e:   # too small
+        K.kerdock_plan_bind(h, 256, info["repr_bytes"] - 1, 512, info["table_bytes"], None)
+    assert e.value.code == -5
+    with pytest.raises(K.KerdockError) as e:   # misaligned
+        K.kerdock_plan_bind(h, 256 + 16, info["repr_bytes"], 512, info["table_bytes"], None)
+    assert e.value.code == -8
+    K.kerdock_plan_destroy(h)
+    K.kerdock_plan_destroy(None)
+
+
+def test_strerror_and_version(lib):
+    assert K.kerdock_strerror(0) == "ok"
+    assert "timed out" in K.kerdock_strerror(-7)
+    assert K.kerdock_strerror(-99) == "unknown error"
+    assert K.kerdock_version() >= 100

@@ -1,0 +1,192 @@
+"""GPU parity of the streaming step (Algorithm 1) against the FP64 oracle,
+through the C ABI: drawn indices (bit-exact), coefficients, the median-of-means
+estimate mu, the top-S set, the refined values and the thresholded output."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import (build_and_load, check_topS_valid, f32, okd, oq, oracle_mu_bound_bf16,
+                        torch_cuda)
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    return build_and_load()
+
+
+def run_case(K, A, X, J, Kb, S, eps, seed, dtype="f32", flags=0):
+    torch = torch_cuda()
+    m, n = A.shape
+    plan = K.KerdockPlan(m, n, J=J, K=Kb, S=S, dtype=dtype)
+    plan.preprocess(torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda())
+    Xt = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    out = plan.apply(Xt, eps, seed, flags=flags, debug=True)
+    plan.sync()
+    idx, val, cnt, mu, ells, coef = (t.cpu().numpy() for t in out)
+    return plan, idx, val, cnt, mu, ells, coef
+
+
+def check_query(A64, R, X64, plan, res, eps, seed, J, Kb, S, k, dtype="f32", lazy=False,
+                queries=None, full=False):
+    idx, val, cnt, mu, ells, coef = res
+    m, n = A64.shape
+    d = 1 << k
+    L = d * (d // 2 + 1)
+    S = min(S, m)
+    for q in (queries if queries is not None else range(X64.shape[0])):
+        x = X64[q]
+        ell_ref = oq.sample_indices(seed, q, J * Kb, L)
+        np.testing.assert_array_equal(ells[q], ell_ref)            # a3: bit-exact
+        s_rows = np.stack([okd.sample_vector(l, n, k) for l in ell_ref])
+        c_ref = s_rows @ x
+        np.testing.assert_allclose(coef[q], c_ref, rtol=0, atol=2e-6 * np.abs(x).sum() + 1e-7)
+        rows = s_rows @ A64.T if lazy else R.reshape(L, m)[ell_ref]
+        mu_ref = oq.median_of_means(rows * c_ref[:, None], J, Kb)
+        if dtype == "f32":
+            tol = 1e-4 * max(np.abs(mu_ref).max(), 1e-30)
+            np.testing.assert_allclose(mu[q], mu_ref, rtol=0, atol=tol)
+        else:
+            tol_vec = oracle_mu_bound_bf16(rows, c_ref, J, Kb) + 1e-5 * np.abs(mu_ref).max()
+            assert (np.abs(mu[q] - mu_ref) <= tol_vec).all()
+            tol = tol_vec.max()
+        v_ref_all = A64 @ x
+        if full:
+            # every selected entry is returned: check the set and the values
+            c = cnt[q]
+            assert c == S
+            sel = idx[q, :c]
+            check_topS_valid(sel, mu_ref, S, 2 * tol)
+            np.testing.assert_allclose(val[q, :c], v_ref_all[sel], rtol=0, atol=1e-5)
+        else:
+            ref_idx, ref_val, ref_mu = oq.apply_one(A64, R, x, eps, seed, q, J, Kb, S, k,
+                                                    lazy=lazy, return_mu=True)[:3]
+            c = cnt[q]
+            got = idx[q, :c]
+            assert (np.diff(got) > 0).all()
+            # values are exact refinements a_i^T x of the returned indices
+            np.testing.assert_allclose(val[q, :c], v_ref_all[got], rtol=0, atol=1e-5)
+            assert (np.abs(val[q, :c]) >= eps).all()
+            np.testing.assert_array_equal(got, ref_idx)
+
+
+def test_query_n64_workload(K):
+    wl = workloads.WORKLOADS["n64"]
+    A = wl.make_A().astype(np.float32)
+    X = workloads.queries_from_codes(f32(A), wl.make_codes()).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    R = okd.representation_lemma6(A64, 6)
+    plan, *res = run_case(K, A, X, wl.J, wl.K, wl.S, wl.eps, wl.seed_apply)
+    check_query(A64, R, X64, plan, res, wl.eps, wl.seed_apply, wl.J, wl.K, wl.S, 6)
+    # against the dense truth h_eps(Ax): exact recovery on every query
+    idx, val, cnt = res[0], res[1], res[2]
+    for q in range(X.shape[0]):
+        tidx, tval = oq.dense_truth(A64, X64[q], wl.eps)
+        np.testing.assert_array_equal(idx[q, :cnt[q]], tidx)
+    plan.close()
+
+
+@pytest.mark.parametrize("Kb", [1, 3, 4, 5])
+def test_query_median_variants(K, Kb):
+    # K = 1 (plain mean), odd K (middle value), even K > 2 (two middle values)
+    n = 64
+    A = workloads.random_orthogonal(n, 21).astype(np.float32)
+    Z = workloads.sparse_codes(n, 24, 4, 0.5, 22)
+    X = workloads.queries_from_codes(f32(A), Z).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    R = okd.representation_lemma6(A64, 6)
+    J = 48
+    plan, *res = run_case(K, A, X, J, Kb, 40, 0.25, 99)
+    check_query(A64, R, X64, plan, res, 0.25, 99, J, Kb, 40, 6)
+    plan.close()
+
+
+def test_query_full_output_and_all_rows(K):
+    # S = m selects every row: the full output is A x exactly (ascending).
+    n = 16
+    A = workloads.random_orthogonal(n, 5).astype(np.float32)
+    X = np.random.default_rng(6).standard_normal((9, n)).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    R = okd.representation_lemma6(A64, 4)
+    plan, *res = run_case(K, A, X, 8, 2, n, 0.0, 7, flags=1)
+    idx, val, cnt = res[0], res[1], res[2]
+    for q in range(9):
+        assert cnt[q] == n
+        np.testing.assert_array_equal(idx[q], np.arange(n))
+        np.testing.assert_allclose(val[q], A64 @ X64[q], atol=1e-5)
+    check_query(A64, R, X64, plan, res, 0.0, 7, 8, 2, n, 4, full=True)
+    plan.close()
+
+
+def test_query_threshold_inclusive_exact(K):
+    # A = I, x with entries exactly 0.5 / 0.25: |v| >= eps keeps the tie.
+    torch = torch_cuda()
+    n = 16
+    A = np.eye(n, dtype=np.float32)
+    X = np.zeros((3, n), dtype=np.float32)
+    X[0, 3] = 0.5
+    X[1, [2, 9]] = [0.25, -0.5]
+    X[2, 5] = 0.2499999
+    plan, *res = run_case(K, A, X, 64, 2, n, 0.25, 1)
+    idx, val, cnt = res[0], res[1], res[2]
+    assert list(idx[0, :cnt[0]]) == [3] and val[0, 0] == 0.5
+    assert list(idx[1, :cnt[1]]) == [2, 9] and list(val[1, :2]) == [0.25, -0.5]
+    assert cnt[2] == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("m,n", [(37, 50), (20, 3), (130, 256)])
+def test_query_ragged_and_padded(K, m, n):
+    # n not a power of four (padding to d, identity samples with w >= n have
+    # coefficient 0 but still count), m not a multiple of 8.
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    A /= np.linalg.norm(A, axis=1, keepdims=True)
+    X = rng.standard_normal((7, n)).astype(np.float32)
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    A64, X64 = f32(A), f32(X)
+    k = 2
+    while (1 << k) < n:
+        k += 2
+    R = okd.representation_lemma6(A64, k)
+    S = min(10, m)
+    plan, *res = run_case(K, A, X, 40, 2, S, 0.3, 12345, flags=1)
+    check_query(A64, R, X64, plan, res, 0.3, 12345, 40, 2, S, k, full=True)
+    plan.close()
+
+
+def test_query_bf16_n256(K):
+    n = 256
+    A = workloads.random_orthogonal(n, 31).astype(np.float32)
+    Z = workloads.sparse_codes(n, 16, 8, 1 / math.sqrt(8), 32)
+    X = workloads.queries_from_codes(f32(A), Z).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    R = okd.representation_lemma6(A64, 8)
+    plan, *res = run_case(K, A, X, 200, 2, 80, 0.5 / math.sqrt(8), 77, dtype="bf16", flags=1)
+    check_query(A64, R, X64, plan, res, 0.5 / math.sqrt(8), 77, 200, 2, 80, 8, dtype="bf16",
+                full=True)
+    plan.close()
+
+
+def test_query_zero_queries_is_noop(K):
+    torch = torch_cuda()
+    plan = K.KerdockPlan(16, 16, J=4, K=2, S=4)
+    plan.preprocess(torch.eye(16, device="cuda"))
+    X = torch.zeros((0, 16), device="cuda")
+    idx, val, cnt = plan.apply(X, 0.1, 0)
+    plan.sync()
+    assert cnt.numel() == 0
+    plan.close()
+
+
+def test_query_apply_before_preprocess_fails(K):
+    torch = torch_cuda()
+    plan = K.KerdockPlan(16, 16, J=4, K=2, S=4)
+    X = torch.zeros((2, 16), device="cuda")
+    with pytest.raises(K.KerdockError) as e:
+        plan.apply(X, 0.1, 0)
+    assert e.value.code == -4
+    plan.close()
