@@ -42,11 +42,12 @@ def representation_slice(plan, b):
 
 def oracle_mu_bound_bf16(rows, c, J, K):
     """Per-entry bound on |mu_bf16 - mu_exact| from rounding each stored entry
-    to bfloat16 (relative error <= 2^-9): |d ybar_k| <= 2^-9 (1/J) sum_j |c_j||R_j|,
+    to bfloat16 (8 significant bits, relative error <= 2^-8):
+    |d ybar_k| <= 2^-8 (1/J) sum_j |c_j||R_j|,
     and the median is 1-Lipschitz in the sup norm, so max_k bounds mu."""
     contrib = np.abs(rows) * np.abs(c)[:, None]
     per_batch = contrib.reshape(K, J, -1).sum(axis=1) / J
-    return 2.0 ** -9 * per_batch.max(axis=0)
+    return 2.0 ** -8 * per_batch.max(axis=0)
 
 
 def check_topS_valid(sel, mu_ref, S, tol):
