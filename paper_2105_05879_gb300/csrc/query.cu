@@ -42,6 +42,7 @@ struct QueryArgs {
   float eps, inv_J, sqrt_d;
   uint64_t seed;
   int flags;
+  int a_vec4;  // rows of A are 16-byte aligned and n % 4 == 0
   int nslot;
   uint32_t row_bytes;
   // dynamic shared-memory layout (byte offsets)
@@ -111,10 +112,63 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* to
   return before + x - v;
 }
 
+// 32x32 bit-matrix transpose across a warp: on entry lane L holds row L
+// (bit t = entry (L, t)); on exit lane L holds column L (bit t = entry (t, L)).
+// Recursive exchange of off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+  const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int j = 16 >> i;
+    const uint32_t m = lo_masks[i];
+    const uint32_t t = __shfl_xor_sync(0xffffffffu, v, j);
+    v = (lane & j) ? ((v & ~m) | ((t >> j) & m)) : ((v & m) | ((t & m) << j));
+  }
+  return v;
+}
+
+// c = s_l^T x for a Kerdock sample l = (b, w): sum over p < n of
+// (-1)^{Q_b(p) + w.p} x_p.  Lane L owns p = 32 t + L.  The sign bits of basis b
+// for 32 consecutive words are transposed so that lane L holds, in one
+// register, the bits of its own p for 32 values of t; the Walsh character
+// (-1)^{w.p} splits into a per-lane part (-1)^{(w mod 32).L} and a per-t part
+// (-1)^{(w >> 5).t}, both folded into that register.  x comes from registers
+// (XREG, n <= 1024: xr[t] = x_{32t+L}) or from shared memory.
+template <bool XREG>
+__device__ __forceinline__ float kerdock_coefficient(const uint32_t* __restrict__ srow,
+                                                     int nwords, uint32_t w, int lane,
+                                                     const float (&xr)[32],
+                                                     const float* __restrict__ xs) {
+  const uint32_t whi = w >> 5;
+  const uint32_t pl = __popc(w & 31u & uint32_t(lane)) & 1u;
+  // bit t of wmask = parity(whi & t) for t < 32
+  const uint32_t wmask = __ballot_sync(0xffffffffu, __popc(whi & 31u & uint32_t(lane)) & 1u);
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+  const int groups = (nwords + 31) >> 5;
+  for (int g = 0; g < groups; ++g) {
+    const int t0 = g << 5;
+    const uint32_t word = t0 + lane < nwords ? __ldg(srow + t0 + lane) : 0u;
+    uint32_t F = warp_transpose32(word, lane) ^ wmask;
+    if ((__popc(whi & uint32_t(t0)) & 1u) ^ pl) F = ~F;
+#pragma unroll
+    for (int t = 0; t < 32; t += 4) {
+      const float x0 = XREG ? xr[t] : xs[(t0 + t) * 32 + lane];
+      const float x1 = XREG ? xr[t + 1] : xs[(t0 + t + 1) * 32 + lane];
+      const float x2 = XREG ? xr[t + 2] : xs[(t0 + t + 2) * 32 + lane];
+      const float x3 = XREG ? xr[t + 3] : xs[(t0 + t + 3) * 32 + lane];
+      acc0 += __uint_as_float(__float_as_uint(x0) ^ ((F << (31 - t)) & 0x80000000u));
+      acc1 += __uint_as_float(__float_as_uint(x1) ^ ((F << (30 - t)) & 0x80000000u));
+      acc2 += __uint_as_float(__float_as_uint(x2) ^ ((F << (29 - t)) & 0x80000000u));
+      acc3 += __uint_as_float(__float_as_uint(x3) ^ ((F << (28 - t)) & 0x80000000u));
+    }
+  }
+  return warp_sum((acc0 + acc1) + (acc2 + acc3));
+}
+
 __device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 
-template <typename RT, int GPT>
-__global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
+template <typename RT, int GPT, bool XREG>
+__global__ void __launch_bounds__(kQThreads, 2) query_kernel(const QueryArgs a) {
   using G = Granule<RT>;
   constexpr int GR = G::kElems;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -153,25 +207,38 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
   }
   __syncthreads();
 
-  uint32_t issued = 0;    // loads issued by thread 0 (only meaningful there)
-  uint32_t consumed = 0;  // rows consumed (identical in every thread)
+  // Ring bookkeeping: slot index and phase parity of the next row to issue
+  // (thread 0 only) and of the next row to consume (every thread).
+  uint32_t is_slot = 0, is_phase = 0, is_uses = 0;
+  uint32_t cs_slot = 0, cs_phase = 0;
 
   // Thread 0 only: put the row of sample jj of the current chunk in flight.
   auto issue = [&](int jj) {
-    const uint32_t s = issued % a.nslot, u = issued / a.nslot;
-    if (u > 0 && !mbar_wait_bounded(&empty_bar[s], (u - 1) & 1)) {
+    if (is_uses >= uint32_t(a.nslot) &&
+        !mbar_wait_bounded(&empty_bar[is_slot], is_phase ^ 1u)) {
       set_status(a.status, kStatusTimeout);
       s_abort = 1;
     }
-    mbar_arrive_expect_tx(&full_bar[s], a.row_bytes);
+    mbar_arrive_expect_tx(&full_bar[is_slot], a.row_bytes);
     const int64_t ell = ells[jj];
-    bulk_g2s(ring + size_t(s) * a.row_bytes, R + ell * a.ldr, a.row_bytes, &full_bar[s]);
-    ++issued;
+    bulk_g2s(ring + size_t(is_slot) * a.row_bytes, R + ell * a.ldr, a.row_bytes,
+             &full_bar[is_slot]);
+    ++is_uses;
+    if (++is_slot == uint32_t(a.nslot)) {
+      is_slot = 0;
+      is_phase ^= 1u;
+    }
   };
 
   for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x) {
     // x into shared memory, zero-padded.
     for (int64_t p = tid; p < xpad; p += kQThreads) xs[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
+    __syncthreads();
+    float xr[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < xpad) ? xs[t * 32 + lane] : 0.f;
+    int batch_left = a.J;  // samples left in the current batch
+    int batch_idx = 0;
 
     float acc[GPT][GR];
 #pragma unroll
@@ -202,16 +269,7 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
         if (b == half) {
           c = w < a.n ? a.sqrt_d * xs[w] : 0.f;
         } else {
-          const uint32_t* srow = a.signs + b * a.sign_words;
-          const uint32_t pl = __popc(w & 31u & uint32_t(lane)) & 1u;
-          float sacc = 0.f;
-          for (int t = 0; t < nwords; ++t) {
-            const uint32_t word = __ldg(srow + t);
-            const uint32_t pt = __popc((w >> 5) & uint32_t(t)) & 1u;
-            const uint32_t bit = ((word >> lane) ^ pl ^ pt) & 1u;
-            sacc += flip_sign(xs[t * 32 + lane], bit);
-          }
-          c = warp_sum(sacc);
+          c = kerdock_coefficient<XREG>(a.signs + b * a.sign_words, nwords, w, lane, xr, xs);
         }
         if (lane == 0) {
           coefs[jj] = c;
@@ -221,13 +279,12 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
       __syncthreads();
       // a5: gather-accumulate.
       for (int jj = 0; jj < cnt; ++jj) {
-        const uint32_t s = consumed % a.nslot, u = consumed / a.nslot;
-        if (!mbar_wait_bounded(&full_bar[s], u & 1)) {
+        if (!mbar_wait_bounded(&full_bar[cs_slot], cs_phase)) {
           set_status(a.status, kStatusTimeout);
           s_abort = 1;
         }
         const float c = coefs[jj];
-        const unsigned char* row = ring + size_t(s) * a.row_bytes;
+        const unsigned char* row = ring + size_t(cs_slot) * a.row_bytes;
 #pragma unroll
         for (int u2 = 0; u2 < GPT; ++u2) {
           const int gi = tid + u2 * kQThreads;
@@ -239,11 +296,13 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[s]);
-        ++consumed;
-        const int64_t j = j0 + jj;
-        if ((j + 1) % a.J == 0) {  // batch (j / J) complete
-          float* mrow = means + (j / a.J) * a.ldr;
+        if (lane == 0) mbar_arrive(&empty_bar[cs_slot]);
+        if (++cs_slot == uint32_t(a.nslot)) {
+          cs_slot = 0;
+          cs_phase ^= 1u;
+        }
+        if (--batch_left == 0) {  // batch batch_idx complete
+          float* mrow = means + int64_t(batch_idx) * a.ldr;
 #pragma unroll
           for (int u2 = 0; u2 < GPT; ++u2) {
             const int gi = tid + u2 * kQThreads;
@@ -255,6 +314,8 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
               }
             }
           }
+          batch_left = a.J;
+          ++batch_idx;
         }
         if (tid == 0 && jj >= 1 && jj - 1 + a.nslot < cnt) issue(jj - 1 + a.nslot);
       }
@@ -377,13 +438,40 @@ __global__ void __launch_bounds__(kQThreads) query_kernel(const QueryArgs a) {
     }
     __syncthreads();
 
-    // a8: exact refinement v_i = a_i^T x and the eps-hard threshold.
-    for (int r = warp; r < a.S; r += kQWarps) {
-      const float* arow = a.A + int64_t(sel[r]) * a.lda;
-      float sacc = 0.f;
-      for (int64_t p = lane; p < a.n; p += 32) sacc = fmaf(arow[p], xs[p], sacc);
-      sacc = warp_sum(sacc);
-      if (lane == 0) vals[r] = sacc;
+    // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
+    for (int r0 = warp * 4; r0 < a.S; r0 += kQWarps * 4) {
+      float racc[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* arow[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) arow[u] = a.A + int64_t(sel[r0 + u < a.S ? r0 + u : r0]) * a.lda;
+      if (a.a_vec4) {
+        const float4* xs4 = reinterpret_cast<const float4*>(xs);
+        const int n4 = int(a.n >> 2);
+#pragma unroll 2
+        for (int p4 = lane; p4 < n4; p4 += 32) {
+          const float4 xv = xs4[p4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
+            racc[u] = fmaf(av.x, xv.x, racc[u]);
+            racc[u] = fmaf(av.y, xv.y, racc[u]);
+            racc[u] = fmaf(av.z, xv.z, racc[u]);
+            racc[u] = fmaf(av.w, xv.w, racc[u]);
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int64_t p = lane; p < a.n; p += 32) {
+          const float xv = xs[p];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = warp_sum(racc[u]);
+        if (lane == 0 && r0 + u < a.S) vals[r0 + u] = v;
+      }
     }
     __syncthreads();
     {
@@ -442,9 +530,9 @@ Layout make_layout(const Plan& p) {
   return L;
 }
 
-template <typename RT, int GPT>
+template <typename RT, int GPT, bool XREG>
 int launch_typed(const Plan& p, const Layout& L, QueryArgs& a, void* ws) {
-  auto kern = query_kernel<RT, GPT>;
+  auto kern = query_kernel<RT, GPT, XREG>;
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    int(L.total)));
   int occ = 0;
@@ -496,6 +584,7 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.sqrt_d = float(int64_t(1) << (p.k / 2));
   a.seed = seed;
   a.flags = flags;
+  a.a_vec4 = (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
   a.nslot = L.nslot;
   a.row_bytes = L.row_bytes;
   a.off_xs = uint32_t(L.off_xs);
@@ -511,14 +600,19 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.status = p.status();
   const int64_t granule = 16 / int64_t(p.elem_bytes());
   const int64_t gpt = (p.ldr / granule + kQThreads - 1) / kQThreads;
+  const bool xreg = p.n <= 1024;
   if (p.dtype == KERDOCK_BF16) {
-    if (gpt <= 1) return launch_typed<__nv_bfloat16, 1>(p, L, a, ws);
-    if (gpt <= 2) return launch_typed<__nv_bfloat16, 2>(p, L, a, ws);
-    return launch_typed<__nv_bfloat16, 4>(p, L, a, ws);
+    if (gpt <= 1) return xreg ? launch_typed<__nv_bfloat16, 1, true>(p, L, a, ws)
+                              : launch_typed<__nv_bfloat16, 1, false>(p, L, a, ws);
+    if (gpt <= 2) return xreg ? launch_typed<__nv_bfloat16, 2, true>(p, L, a, ws)
+                              : launch_typed<__nv_bfloat16, 2, false>(p, L, a, ws);
+    return launch_typed<__nv_bfloat16, 4, false>(p, L, a, ws);
   }
-  if (gpt <= 1) return launch_typed<float, 1>(p, L, a, ws);
-  if (gpt <= 2) return launch_typed<float, 2>(p, L, a, ws);
-  return launch_typed<float, 4>(p, L, a, ws);
+  if (gpt <= 1) return xreg ? launch_typed<float, 1, true>(p, L, a, ws)
+                            : launch_typed<float, 1, false>(p, L, a, ws);
+  if (gpt <= 2) return xreg ? launch_typed<float, 2, true>(p, L, a, ws)
+                            : launch_typed<float, 2, false>(p, L, a, ws);
+  return launch_typed<float, 4, false>(p, L, a, ws);
 }
 
 }  // namespace kd
