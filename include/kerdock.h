@@ -157,8 +157,9 @@ int kerdock_apply_debug(kerdock_plan_t plan, const float* X_dev, int64_t q, int6
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);
 
-/* Copy the device sign table to host memory: (d/2) rows of max(1, d/32)
- * uint32 words; bit (p mod 32) of word p/32 of row b is Q_{M_b}(p).
+/* Copy the device sign table to host memory: (d/2) rows of max(4, d/32)
+ * uint32 words (rows padded to 16 bytes); bit (p mod 32) of word p/32 of row
+ * b is Q_{M_b}(p) for p < d, and padding bits are 0.
  * Synchronises the stream. */
 int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_words);
 

@@ -23,7 +23,7 @@ struct Plan {
   int64_t m = 0, n = 0, d = 0, B = 0, L = 0, ldr = 0;
   int k = 0, dtype = KERDOCK_F32, J = 0, K = 0, S = 0;
   int64_t N = 0;
-  int64_t sign_words = 0;  // uint32 words per sign-table row: max(1, d/32)
+  int64_t sign_words = 0;  // uint32 words per sign-table row: max(4, d/32)
   size_t repr_bytes = 0, table_bytes = 0;
   // bound device memory
   void* repr = nullptr;

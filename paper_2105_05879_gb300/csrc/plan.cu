@@ -162,7 +162,7 @@ int kerdock_plan_create(kerdock_plan_t* plan, int64_t m, int64_t n, int32_t dtyp
   p.K = K;
   p.S = int(S < m ? S : m);
   p.N = int64_t(J) * K;
-  p.sign_words = p.d >= 32 ? p.d / 32 : 1;
+  p.sign_words = p.d >= 128 ? p.d / 32 : 4;  // rows padded to 16 bytes (TMA copies)
   p.repr_bytes = size_t(p.B) * size_t(p.d) * size_t(p.ldr) * p.elem_bytes();
   p.table_bytes = kd::kStatusBytes + size_t(p.d / 2) * size_t(p.sign_words) * 4;
   *plan = h;

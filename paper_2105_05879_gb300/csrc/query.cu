@@ -1,43 +1,65 @@
 // query.cu -- the streaming step of Algorithm 1 for a batch of queries.
 //
-// One CTA owns one query at a time (persistent grid, static round robin):
-//   a3  draw l_j = floor(SplitMix64(seed + G(qN + j + 1)) * L / 2^64)
-//   a4  c_j = s_{l_j}^T x: for a Kerdock basis b, sum_p (-1)^{Q_b(p)+w.p} x_p
-//       (one warp per sample, lane = p mod 32, sign bits from the device
-//       table); for the identity basis sqrt(d) x_w (0 when w >= n)
-//   a5  ybar_k = (1/J) sum_{j in batch k} c_j R[l_j][.]: rows of the
-//       representation stream through a shared-memory ring filled by the TMA
-//       engine (cp.async.bulk, one whole row per copy, mbarrier completion);
-//       each thread owns fixed 16-byte column granules, so the sum order is
-//       fixed and the result deterministic
+// Per query x (Algorithm 1, streaming step; Theorem 3; Sec. 4 top-10s):
+//   a3  draw l_j = floor(SplitMix64(seed + G(qN + j + 1)) * L / 2^64), j < N = JK
+//   a4  c_j = s_{l_j}^T x: for a Kerdock basis b, sum_p (-1)^{Q_b(p)+w.p} x_p;
+//       for the identity basis sqrt(d) x_w (0 when w >= n)
+//   a5  ybar_k = (1/J) sum_{j in batch k} c_j R[l_j][.]
 //   a6  mu_i = median_k ybar_{k,i} (mean of the two middle values for even K)
-//   a7  the S indices of largest |mu_i| (radix select on the float bits,
-//       ties to the smaller index), in ascending order
+//   a7  the S indices of largest |mu_i| (ties to the smaller index), ascending
 //   a8  v_i = a_i^T x for the selected rows, keep |v_i| >= eps, compact.
-// Theorem 3 gives the estimator, Algorithm 1 the steps, Sec. 4 the top-10s
-// refinement.
+//
+// Kernel design: a persistent, warp-specialised CTA per SM works through its
+// queries as one continuous stream of samples, so that the representation rows
+// (the HBM stream that bounds the method) never stop flowing:
+//   warp 0        producer: draws l_j (32 lanes at a time) and, per sample,
+//                 issues two TMA bulk copies into a ring slot -- the row
+//                 R[l_j][0..m) and the sign-table row of basis b -- completing
+//                 on the slot's mbarriers; loads x of upcoming queries.
+//   warps 1..3    coefficient warps: c_j from the slot's sign bits and x.
+//   warps 4..11   gather warps: each thread owns fixed 16-byte column granules
+//                 and accumulates c_j R[l_j] in registers in sample order (a
+//                 fixed, deterministic summation order); batch means go to a
+//                 double-buffered means area.
+//   warps 12..15  finalizer warps: median, top-S radix select, exact
+//                 refinement, threshold and output of the previous query while
+//                 the gather warps already stream the next one.
+// All hand-offs are mbarrier phases; every wait is bounded and a timeout sets
+// the plan's status word and ends the CTA.
 #include "kerdock_internal.cuh"
 
 namespace kd {
 namespace {
 
-constexpr int kQThreads = 256;
-constexpr int kQWarps = kQThreads / 32;
-constexpr int kMaxSlots = 32;
-constexpr int kChunk = 1024;           // samples drawn and weighted per round
-constexpr size_t kRingTarget = 64 << 10;  // bytes of representation rows in flight per CTA
-constexpr size_t kMeansSmemMax = 32 << 10;
-constexpr int kMaxCtasPerSm = 2;
+constexpr int kCoefWarps = 3;
+constexpr int kGatherWarps = 8;
+constexpr int kFinalWarps = 4;
+constexpr int kFirstCoefWarp = 1;
+constexpr int kFirstGatherWarp = kFirstCoefWarp + kCoefWarps;
+constexpr int kFirstFinalWarp = kFirstGatherWarp + kGatherWarps;
+constexpr int kWarps = kFirstFinalWarp + kFinalWarps;  // 16
+constexpr int kThreads = kWarps * 32;                   // 512
+constexpr int kGatherThreads = kGatherWarps * 32;
+constexpr int kFinalThreads = kFinalWarps * 32;
+constexpr int kMaxSlots = 64;
+constexpr int kMinSlots = 4;
+constexpr int kXBufs = 3;
+constexpr int kMBufs = 2;
+constexpr int kFinalBarrier = 1;  // named barrier id of the finalizer warps
+constexpr size_t kSmemBudget = 227 * 1024 - 4096;  // dynamic bytes (static ~3 KB)
+constexpr size_t kRingCap = 160 * 1024;
+constexpr size_t kMeansSmemMax = 64 * 1024;
 
 struct QueryArgs {
   const void* R;
   const uint32_t* signs;
-  int64_t sign_words;
+  int64_t sign_stride;  // words per sign-table row
+  uint32_t sign_bytes;  // bytes copied per Kerdock sample: 4 * ceil(n/32) rounded to 16
   const float* A;
   int64_t lda;
   const float* X;
   int64_t ldx;
-  int64_t Q, m, n, d, L, ldr, N;
+  int64_t Q, m, n, d, L, ldr, N, xpad;
   int k, J, K, S;
   float eps, inv_J, sqrt_d;
   uint64_t seed;
@@ -46,7 +68,7 @@ struct QueryArgs {
   int nslot;
   uint32_t row_bytes;
   // dynamic shared-memory layout (byte offsets)
-  uint32_t off_xs, off_ells, off_coefs, off_means;
+  uint32_t off_sgn, off_ell, off_coef, off_x, off_means, off_mu, off_sel, off_vals;
   float* means_gmem;  // non-null when the batch means live in the workspace
   int32_t* out_idx;
   float* out_val;
@@ -85,69 +107,69 @@ struct Granule<__nv_bfloat16> {
   }
 };
 
-// Exclusive prefix sum over the CTA; *total receives the sum of all v.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Exclusive prefix sum over the finalizer warps; *total = sum of all v.
+__device__ __forceinline__ int final_exclusive_scan(int v, int* scratch, int* total) {
+  const int lane = threadIdx.x & 31;
+  const int fw = (threadIdx.x >> 5) - kFirstFinalWarp;
   int x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int s = lane < kQWarps ? scratch[lane] : 0;
+  if (lane == 31) scratch[fw] = x;
+  named_barrier_sync(kFinalBarrier, kFinalThreads);
+  int before = 0, tot = 0;
 #pragma unroll
-    for (int o = 1; o < kQWarps; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < kQWarps) scratch[lane] = s;
+  for (int w = 0; w < kFinalWarps; ++w) {
+    const int s = scratch[w];
+    if (w < fw) before += s;
+    tot += s;
   }
-  __syncthreads();
-  const int before = warp > 0 ? scratch[warp - 1] : 0;
-  *total = scratch[kQWarps - 1];
-  __syncthreads();
+  *total = tot;
+  named_barrier_sync(kFinalBarrier, kFinalThreads);
   return before + x - v;
 }
 
+__device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+
 // 32x32 bit-matrix transpose across a warp: on entry lane L holds row L
 // (bit t = entry (L, t)); on exit lane L holds column L (bit t = entry (t, L)).
-// Recursive exchange of off-diagonal blocks of size 16, 8, 4, 2, 1.
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
   const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const int j = 16 >> i;
-    const uint32_t m = lo_masks[i];
+    const uint32_t msk = lo_masks[i];
     const uint32_t t = __shfl_xor_sync(0xffffffffu, v, j);
-    v = (lane & j) ? ((v & ~m) | ((t >> j) & m)) : ((v & m) | ((t & m) << j));
+    v = (lane & j) ? ((v & ~msk) | ((t >> j) & msk)) : ((v & msk) | ((t & msk) << j));
   }
   return v;
 }
 
 // c = s_l^T x for a Kerdock sample l = (b, w): sum over p < n of
-// (-1)^{Q_b(p) + w.p} x_p.  Lane L owns p = 32 t + L.  The sign bits of basis b
-// for 32 consecutive words are transposed so that lane L holds, in one
+// (-1)^{Q_b(p) + w.p} x_p.  Lane L owns p = 32 t + L.  The sign words of basis
+// b (already in shared memory) are transposed so that lane L holds, in one
 // register, the bits of its own p for 32 values of t; the Walsh character
 // (-1)^{w.p} splits into a per-lane part (-1)^{(w mod 32).L} and a per-t part
 // (-1)^{(w >> 5).t}, both folded into that register.  x comes from registers
 // (XREG, n <= 1024: xr[t] = x_{32t+L}) or from shared memory.
 template <bool XREG>
-__device__ __forceinline__ float kerdock_coefficient(const uint32_t* __restrict__ srow,
-                                                     int nwords, uint32_t w, int lane,
-                                                     const float (&xr)[32],
-                                                     const float* __restrict__ xs) {
+__device__ __forceinline__ float kerdock_coefficient(const uint32_t* srow, int nwords, uint32_t w,
+                                                     int lane, const float (&xr)[32],
+                                                     const float* xs) {
   const uint32_t whi = w >> 5;
   const uint32_t pl = __popc(w & 31u & uint32_t(lane)) & 1u;
-  // bit t of wmask = parity(whi & t) for t < 32
   const uint32_t wmask = __ballot_sync(0xffffffffu, __popc(whi & 31u & uint32_t(lane)) & 1u);
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
   const int groups = (nwords + 31) >> 5;
   for (int g = 0; g < groups; ++g) {
     const int t0 = g << 5;
-    const uint32_t word = t0 + lane < nwords ? __ldg(srow + t0 + lane) : 0u;
+    const uint32_t word = t0 + lane < nwords ? srow[t0 + lane] : 0u;
     uint32_t F = warp_transpose32(word, lane) ^ wmask;
     if ((__popc(whi & uint32_t(t0)) & 1u) ^ pl) F = ~F;
 #pragma unroll
@@ -165,171 +187,248 @@ __device__ __forceinline__ float kerdock_coefficient(const uint32_t* __restrict_
   return warp_sum((acc0 + acc1) + (acc2 + acc3));
 }
 
-__device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+struct Shared {
+  uint64_t row_full[kMaxSlots];
+  uint64_t sgn_full[kMaxSlots];
+  uint64_t coef_full[kMaxSlots];
+  uint64_t slot_empty[kMaxSlots];
+  uint64_t x_full[kXBufs];
+  uint64_t x_empty[kXBufs];
+  uint64_t means_full[kMBufs];
+  uint64_t means_empty[kMBufs];
+  uint32_t hist[256];
+  int scan[kFinalWarps];
+  uint32_t digit, remaining;
+  int abort_flag;
+};
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, Shared& sh,
+                                           uint32_t* status) {
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*reinterpret_cast<volatile int*>(&sh.abort_flag)) return false;
+      if (it > (1u << 22)) {
+        set_status(status, kStatusTimeout);
+        *reinterpret_cast<volatile int*>(&sh.abort_flag) = 1;
+        return false;
+      }
+    }
+  }
+}
 
 template <typename RT, int GPT, bool XREG>
-__global__ void __launch_bounds__(kQThreads, 2) query_kernel(const QueryArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   using G = Granule<RT>;
   constexpr int GR = G::kElems;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kMaxSlots];
-  __shared__ __align__(8) uint64_t empty_bar[kMaxSlots];
-  __shared__ int s_scan[kQWarps];
-  __shared__ uint32_t s_hist[256];
-  __shared__ uint32_t s_digit, s_remaining;
-  __shared__ int s_abort;
+  __shared__ Shared sh;
 
   unsigned char* ring = smem;
-  float* xs = reinterpret_cast<float*>(smem + a.off_xs);
-  int32_t* ells = reinterpret_cast<int32_t*>(smem + a.off_ells);
-  float* coefs = reinterpret_cast<float*>(smem + a.off_coefs);
-  float* means = a.means_gmem != nullptr
-                     ? a.means_gmem + int64_t(blockIdx.x) * a.K * a.ldr
-                     : reinterpret_cast<float*>(smem + a.off_means);
-  // After the gather the ring is reused for mu, the selection and its values.
-  float* mus = reinterpret_cast<float*>(smem);
-  int32_t* sel = reinterpret_cast<int32_t*>(smem + a.ldr * 4);
-  float* vals = reinterpret_cast<float*>(smem + a.ldr * 4 + ((a.S + 3) / 4 * 4) * 4);
+  uint32_t* sgn = reinterpret_cast<uint32_t*>(smem + a.off_sgn);
+  int32_t* ell_s = reinterpret_cast<int32_t*>(smem + a.off_ell);
+  float* coef_s = reinterpret_cast<float*>(smem + a.off_coef);
+  float* xbuf = reinterpret_cast<float*>(smem + a.off_x);
+  float* means_base = a.means_gmem != nullptr
+                          ? a.means_gmem + int64_t(blockIdx.x) * kMBufs * a.K * a.ldr
+                          : reinterpret_cast<float*>(smem + a.off_means);
+  float* mus = reinterpret_cast<float*>(smem + a.off_mu);
+  int32_t* sel = reinterpret_cast<int32_t*>(smem + a.off_sel);
+  float* vals = reinterpret_cast<float*>(smem + a.off_vals);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const RT* R = static_cast<const RT*>(a.R);
-  const int64_t xpad = a.d > 32 ? a.d : 32;
-  const int nwords = int((a.n + 31) / 32);
   const int64_t half = a.d / 2;
+  const uint32_t nslot = uint32_t(a.nslot);
+  const int sign_words_per_slot = int(a.sign_bytes / 4);
 
   if (tid == 0) {
     for (int s = 0; s < a.nslot; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], kQWarps);
+      mbar_init(&sh.row_full[s], 1);
+      mbar_init(&sh.sgn_full[s], 1);
+      mbar_init(&sh.coef_full[s], 1);
+      mbar_init(&sh.slot_empty[s], kGatherWarps);
     }
-    s_abort = 0;
+    for (int b = 0; b < kXBufs; ++b) {
+      mbar_init(&sh.x_full[b], 1);
+      mbar_init(&sh.x_empty[b], kCoefWarps + 1);
+    }
+    for (int b = 0; b < kMBufs; ++b) {
+      mbar_init(&sh.means_full[b], kGatherWarps);
+      mbar_init(&sh.means_empty[b], 1);
+    }
+    sh.abort_flag = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  // Ring bookkeeping: slot index and phase parity of the next row to issue
-  // (thread 0 only) and of the next row to consume (every thread).
-  uint32_t is_slot = 0, is_phase = 0, is_uses = 0;
-  uint32_t cs_slot = 0, cs_phase = 0;
-
-  // Thread 0 only: put the row of sample jj of the current chunk in flight.
-  auto issue = [&](int jj) {
-    if (is_uses >= uint32_t(a.nslot) &&
-        !mbar_wait_bounded(&empty_bar[is_slot], is_phase ^ 1u)) {
-      set_status(a.status, kStatusTimeout);
-      s_abort = 1;
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    uint32_t slot = 0, phase = 0, uses = 0;
+    int qs = 0;
+    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
+      const int xb = qs % kXBufs;
+      if (qs >= kXBufs &&
+          !wait_phase(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, a.status))
+        return;
+      float* xq = xbuf + xb * a.xpad;
+      for (int64_t p = lane; p < a.xpad; p += 32) xq[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.x_full[xb]);
+      for (int64_t j0 = 0; j0 < a.N; j0 += 32) {
+        const int64_t j = j0 + lane;
+        uint64_t ell = 0;
+        if (j < a.N) {
+          ell = sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
+          if (a.ells_out) a.ells_out[q * a.N + j] = int64_t(ell);
+        }
+        const int cnt = int(a.N - j0 < 32 ? a.N - j0 : 32);
+        for (int t = 0; t < cnt; ++t) {
+          const uint32_t e = __shfl_sync(0xffffffffu, uint32_t(ell), t);
+          if (lane == 0) {
+            bool ok = true;
+            if (uses >= nslot) ok = wait_phase(&sh.slot_empty[slot], phase ^ 1u, sh, a.status);
+            if (ok) {
+              ell_s[slot] = int32_t(e);
+              const int64_t b = int64_t(e) >> a.k;
+              if (b < half) {
+                mbar_arrive_expect_tx(&sh.sgn_full[slot], a.sign_bytes);
+                bulk_g2s(sgn + size_t(slot) * sign_words_per_slot, a.signs + b * a.sign_stride,
+                         a.sign_bytes, &sh.sgn_full[slot]);
+              } else {
+                mbar_arrive(&sh.sgn_full[slot]);
+              }
+              mbar_arrive_expect_tx(&sh.row_full[slot], a.row_bytes);
+              bulk_g2s(ring + size_t(slot) * a.row_bytes, R + int64_t(e) * a.ldr, a.row_bytes,
+                       &sh.row_full[slot]);
+            }
+          }
+          if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&sh.abort_flag), 0))
+            return;
+          ++uses;
+          if (++slot == nslot) {
+            slot = 0;
+            phase ^= 1u;
+          }
+        }
+      }
     }
-    mbar_arrive_expect_tx(&full_bar[is_slot], a.row_bytes);
-    const int64_t ell = ells[jj];
-    bulk_g2s(ring + size_t(is_slot) * a.row_bytes, R + ell * a.ldr, a.row_bytes,
-             &full_bar[is_slot]);
-    ++is_uses;
-    if (++is_slot == uint32_t(a.nslot)) {
-      is_slot = 0;
-      is_phase ^= 1u;
-    }
-  };
-
-  for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x) {
-    // x into shared memory, zero-padded.
-    for (int64_t p = tid; p < xpad; p += kQThreads) xs[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
-    __syncthreads();
+  } else if (warp < kFirstGatherWarp) {
+    // ------------------------------------------------------------ coefficients
+    const int cw = warp - kFirstCoefWarp;
+    uint32_t slot = uint32_t(cw), phase = 0;  // nslot >= kMinSlots > kCoefWarps
+    int64_t g_next = cw;                      // global sample counter of this warp
+    const int nwords = int((a.n + 31) / 32);
+    int qs = 0;
     float xr[32];
+    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
+      const int xb = qs % kXBufs;
+      if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, a.status)) return;
+      const float* xq = xbuf + xb * a.xpad;
 #pragma unroll
-    for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < xpad) ? xs[t * 32 + lane] : 0.f;
-    int batch_left = a.J;  // samples left in the current batch
-    int batch_idx = 0;
-
-    float acc[GPT][GR];
-#pragma unroll
-    for (int u = 0; u < GPT; ++u)
-#pragma unroll
-      for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
-
-    for (int64_t j0 = 0; j0 < a.N; j0 += kChunk) {
-      const int cnt = int(a.N - j0 < kChunk ? a.N - j0 : kChunk);
-      // a3: draw this chunk's indices.
-      for (int jj = tid; jj < cnt; jj += kQThreads) {
-        const uint64_t ell = sample_index(a.seed, uint64_t(q) * a.N + j0 + jj, uint64_t(a.L));
-        ells[jj] = int32_t(ell);
-        if (a.ells_out) a.ells_out[q * a.N + j0 + jj] = int64_t(ell);
-      }
-      __syncthreads();
-      // Start the first rows streaming while the coefficients are computed.
-      if (tid == 0) {
-        const int pre = cnt < a.nslot ? cnt : a.nslot;
-        for (int jj = 0; jj < pre; ++jj) issue(jj);
-      }
-      // a4: one warp per sample.
-      for (int jj = warp; jj < cnt; jj += kQWarps) {
-        const int64_t ell = ells[jj];
-        const int64_t b = ell >> a.k;
-        const uint32_t w = uint32_t(ell & (a.d - 1));
+      for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < a.xpad) ? xq[t * 32 + lane] : 0.f;
+      const int64_t g_end = int64_t(qs + 1) * a.N;
+      for (; g_next < g_end; g_next += kCoefWarps) {
+        if (!wait_phase(&sh.sgn_full[slot], phase, sh, a.status)) return;
+        const uint32_t e = uint32_t(ell_s[slot]);
+        const int64_t b = int64_t(e) >> a.k;
+        const uint32_t w = e & uint32_t(a.d - 1);
         float c;
         if (b == half) {
-          c = w < a.n ? a.sqrt_d * xs[w] : 0.f;
+          c = w < a.n ? a.sqrt_d * xq[w] : 0.f;
         } else {
-          c = kerdock_coefficient<XREG>(a.signs + b * a.sign_words, nwords, w, lane, xr, xs);
+          c = kerdock_coefficient<XREG>(sgn + size_t(slot) * sign_words_per_slot, nwords, w, lane,
+                                        xr, xq);
         }
         if (lane == 0) {
-          coefs[jj] = c;
-          if (a.coef_out) a.coef_out[q * a.N + j0 + jj] = c;
+          coef_s[slot] = c;
+          if (a.coef_out) a.coef_out[q * a.N + (g_next - int64_t(qs) * a.N)] = c;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.coef_full[slot]);
+        slot += kCoefWarps;
+        if (slot >= nslot) {
+          slot -= nslot;
+          phase ^= 1u;
         }
       }
-      __syncthreads();
-      // a5: gather-accumulate.
-      for (int jj = 0; jj < cnt; ++jj) {
-        if (!mbar_wait_bounded(&full_bar[cs_slot], cs_phase)) {
-          set_status(a.status, kStatusTimeout);
-          s_abort = 1;
-        }
-        const float c = coefs[jj];
-        const unsigned char* row = ring + size_t(cs_slot) * a.row_bytes;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.x_empty[xb]);
+    }
+  } else if (warp < kFirstFinalWarp) {
+    // ------------------------------------------------------------ gather
+    const int gt = tid - kFirstGatherWarp * 32;
+    uint32_t slot = 0, phase = 0;
+    int qs = 0;
+    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
+      const int mb = qs % kMBufs;
+      float* means = means_base + int64_t(mb) * a.K * a.ldr;
+      float acc[GPT][GR];
 #pragma unroll
-        for (int u2 = 0; u2 < GPT; ++u2) {
-          const int gi = tid + u2 * kQThreads;
+      for (int u = 0; u < GPT; ++u)
+#pragma unroll
+        for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
+      int batch_left = a.J, batch = 0;
+      for (int64_t j = 0; j < a.N; ++j) {
+        if (!wait_phase(&sh.row_full[slot], phase, sh, a.status)) return;
+        if (!wait_phase(&sh.coef_full[slot], phase, sh, a.status)) return;
+        const float c = coef_s[slot];
+        const unsigned char* row = ring + size_t(slot) * a.row_bytes;
+#pragma unroll
+        for (int u = 0; u < GPT; ++u) {
+          const int gi = gt + u * kGatherThreads;
           if (gi * GR < a.ldr) {
             float v[GR];
             G::load(row + size_t(gi) * 16, v);
 #pragma unroll
-            for (int e = 0; e < GR; ++e) acc[u2][e] = fmaf(c, v[e], acc[u2][e]);
+            for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
           }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_bar[cs_slot]);
-        if (++cs_slot == uint32_t(a.nslot)) {
-          cs_slot = 0;
-          cs_phase ^= 1u;
+        if (lane == 0) mbar_arrive(&sh.slot_empty[slot]);
+        if (++slot == nslot) {
+          slot = 0;
+          phase ^= 1u;
         }
-        if (--batch_left == 0) {  // batch batch_idx complete
-          float* mrow = means + int64_t(batch_idx) * a.ldr;
+        if (--batch_left == 0) {
+          if (batch == 0 && qs >= kMBufs &&
+              !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, a.status))
+            return;
+          float* mrow = means + int64_t(batch) * a.ldr;
 #pragma unroll
-          for (int u2 = 0; u2 < GPT; ++u2) {
-            const int gi = tid + u2 * kQThreads;
+          for (int u = 0; u < GPT; ++u) {
+            const int gi = gt + u * kGatherThreads;
             if (gi * GR < a.ldr) {
 #pragma unroll
               for (int e = 0; e < GR; ++e) {
-                mrow[gi * GR + e] = acc[u2][e] * a.inv_J;
-                acc[u2][e] = 0.f;
+                mrow[gi * GR + e] = acc[u][e] * a.inv_J;
+                acc[u][e] = 0.f;
               }
             }
           }
           batch_left = a.J;
-          ++batch_idx;
+          ++batch;
         }
-        if (tid == 0 && jj >= 1 && jj - 1 + a.nslot < cnt) issue(jj - 1 + a.nslot);
       }
-      __syncthreads();
-      if (s_abort) return;
+      if (a.means_gmem != nullptr) __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.means_full[mb]);
     }
-
-    // a6: median over the K batch means (thread-owned columns).
-#pragma unroll
-    for (int u2 = 0; u2 < GPT; ++u2) {
-      const int gi = tid + u2 * kQThreads;
-      for (int e = 0; e < GR; ++e) {
-        const int64_t col = int64_t(gi) * GR + e;
-        if (col >= a.ldr) break;
+  } else {
+    // ------------------------------------------------------------ finalizer
+    const int ft = tid - kFirstFinalWarp * 32;
+    const int fw = warp - kFirstFinalWarp;
+    const int m = int(a.m);
+    int qs = 0;
+    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
+      const int mb = qs % kMBufs, xb = qs % kXBufs;
+      if (!wait_phase(&sh.means_full[mb], uint32_t(qs / kMBufs) & 1u, sh, a.status)) return;
+      if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, a.status)) return;
+      const float* means = means_base + int64_t(mb) * a.K * a.ldr;
+      const float* xq = xbuf + xb * a.xpad;
+      // a6: median over the K batch means.
+      for (int col = ft; col < m; col += kFinalThreads) {
         float med;
         if (a.K == 1) {
           med = means[col];
@@ -354,179 +453,199 @@ __global__ void __launch_bounds__(kQThreads, 2) query_kernel(const QueryArgs a) 
           med = (a.K & 1) ? lo : 0.5f * (lo + hi);
         }
         mus[col] = med;
-        if (a.mu_out && col < a.m) a.mu_out[q * a.m + col] = med;
+        if (a.mu_out) a.mu_out[q * a.m + col] = med;
       }
-    }
-    __syncthreads();
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      if (ft == 0) mbar_arrive(&sh.means_empty[mb]);  // means are consumed
 
-    // a7: top-S by radix select on |mu| (4 digits of 8 bits, high first).
-    const int m = int(a.m);
-    uint32_t prefix = 0, mask = 0;
-    uint32_t remaining = uint32_t(a.S);
-    for (int pass = 0; pass < 4; ++pass) {
-      const int shift = 24 - 8 * pass;
-      s_hist[tid] = 0;
-      __syncthreads();
-      for (int i = tid; i < m; i += kQThreads) {
-        const uint32_t key = abs_key(mus[i]);
-        if ((key & mask) == prefix) atomicAdd(&s_hist[(key >> shift) & 255u], 1u);
-      }
-      __syncthreads();
-      if (warp == 0) {
-        const int base = (31 - lane) * 8;  // lane 0 holds the highest digits
-        uint32_t sum = 0;
-#pragma unroll
-        for (int j2 = 0; j2 < 8; ++j2) sum += s_hist[base + j2];
-        uint32_t incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
+      // a7: top-S by radix select on |mu| (4 digits of 8 bits, high first).
+      uint32_t prefix = 0, mask = 0, remaining = uint32_t(a.S);
+      for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        sh.hist[ft] = 0;
+        sh.hist[ft + kFinalThreads] = 0;
+        named_barrier_sync(kFinalBarrier, kFinalThreads);
+        for (int i = ft; i < m; i += kFinalThreads) {
+          const uint32_t key = abs_key(mus[i]);
+          if ((key & mask) == prefix) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
         }
-        const uint32_t excl = incl - sum;
-        const uint32_t hit = __ballot_sync(0xffffffffu, excl < remaining && remaining <= incl);
-        if (lane == __ffs(hit) - 1) {
-          uint32_t cum = excl;
-          for (int j2 = 7; j2 >= 0; --j2) {
-            const uint32_t h = s_hist[base + j2];
-            if (cum + h >= remaining) {
-              s_digit = uint32_t(base + j2);
-              s_remaining = remaining - cum;
-              break;
+        named_barrier_sync(kFinalBarrier, kFinalThreads);
+        if (fw == 0) {
+          const int base = (31 - lane) * 8;  // lane 0 holds the highest digits
+          uint32_t sum = 0;
+#pragma unroll
+          for (int j2 = 0; j2 < 8; ++j2) sum += sh.hist[base + j2];
+          uint32_t incl = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const uint32_t excl = incl - sum;
+          const uint32_t hit = __ballot_sync(0xffffffffu, excl < remaining && remaining <= incl);
+          if (lane == __ffs(hit) - 1) {
+            uint32_t cum = excl;
+            for (int j2 = 7; j2 >= 0; --j2) {
+              const uint32_t h = sh.hist[base + j2];
+              if (cum + h >= remaining) {
+                sh.digit = uint32_t(base + j2);
+                sh.remaining = remaining - cum;
+                break;
+              }
+              cum += h;
             }
-            cum += h;
           }
         }
+        named_barrier_sync(kFinalBarrier, kFinalThreads);
+        prefix |= sh.digit << shift;
+        mask |= 255u << shift;
+        remaining = sh.remaining;
+        named_barrier_sync(kFinalBarrier, kFinalThreads);
       }
-      __syncthreads();
-      prefix |= s_digit << shift;
-      mask |= 255u << shift;
-      remaining = s_remaining;
-      __syncthreads();
-    }
-    const uint32_t T = prefix;  // the S-th largest key; take `remaining` keys equal to T
-    {
-      const int seg = (m + kQThreads - 1) / kQThreads;
-      const int lo = tid * seg, hi = lo + seg < m ? lo + seg : m;
-      int eq = 0;
-      for (int i = lo; i < hi; ++i) eq += abs_key(mus[i]) == T;
-      int tot;
-      int eq_rank = block_exclusive_scan(eq, s_scan, &tot);
-      int take = 0;
-      for (int i = lo; i < hi; ++i) {
-        const uint32_t key = abs_key(mus[i]);
-        if (key > T) {
-          ++take;
-        } else if (key == T) {
-          take += uint32_t(eq_rank) < remaining;
-          ++eq_rank;
+      const uint32_t T = prefix;  // the S-th largest key; take `remaining` keys equal to T
+      {
+        const int seg = (m + kFinalThreads - 1) / kFinalThreads;
+        const int lo = ft * seg, hi = lo + seg < m ? lo + seg : m;
+        int eq = 0;
+        for (int i = lo; i < hi; ++i) eq += abs_key(mus[i]) == T;
+        int tot;
+        int eq_rank = final_exclusive_scan(eq, sh.scan, &tot);
+        const int eq_rank0 = eq_rank;
+        int take = 0;
+        for (int i = lo; i < hi; ++i) {
+          const uint32_t key = abs_key(mus[i]);
+          if (key > T) {
+            ++take;
+          } else if (key == T) {
+            take += uint32_t(eq_rank) < remaining;
+            ++eq_rank;
+          }
+        }
+        int pos = final_exclusive_scan(take, sh.scan, &tot);
+        eq_rank = eq_rank0;
+        for (int i = lo; i < hi; ++i) {
+          const uint32_t key = abs_key(mus[i]);
+          bool t2 = false;
+          if (key > T) {
+            t2 = true;
+          } else if (key == T) {
+            t2 = uint32_t(eq_rank) < remaining;
+            ++eq_rank;
+          }
+          if (t2) sel[pos++] = i;
         }
       }
-      int pos = block_exclusive_scan(take, s_scan, &tot);
-      eq_rank -= eq;
-      for (int i = lo; i < hi; ++i) {
-        const uint32_t key = abs_key(mus[i]);
-        bool t2 = false;
-        if (key > T) {
-          t2 = true;
-        } else if (key == T) {
-          t2 = uint32_t(eq_rank) < remaining;
-          ++eq_rank;
-        }
-        if (t2) sel[pos++] = i;
-      }
-    }
-    __syncthreads();
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
 
-    // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
-    for (int r0 = warp * 4; r0 < a.S; r0 += kQWarps * 4) {
-      float racc[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* arow[4];
+      // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
+      for (int r0 = fw * 4; r0 < a.S; r0 += kFinalWarps * 4) {
+        float racc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* arow[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) arow[u] = a.A + int64_t(sel[r0 + u < a.S ? r0 + u : r0]) * a.lda;
-      if (a.a_vec4) {
-        const float4* xs4 = reinterpret_cast<const float4*>(xs);
-        const int n4 = int(a.n >> 2);
+        for (int u = 0; u < 4; ++u)
+          arow[u] = a.A + int64_t(sel[r0 + u < a.S ? r0 + u : r0]) * a.lda;
+        if (a.a_vec4) {
+          const float4* xs4 = reinterpret_cast<const float4*>(xq);
+          const int n4 = int(a.n >> 2);
 #pragma unroll 2
-        for (int p4 = lane; p4 < n4; p4 += 32) {
-          const float4 xv = xs4[p4];
+          for (int p4 = lane; p4 < n4; p4 += 32) {
+            const float4 xv = xs4[p4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
-            racc[u] = fmaf(av.x, xv.x, racc[u]);
-            racc[u] = fmaf(av.y, xv.y, racc[u]);
-            racc[u] = fmaf(av.z, xv.z, racc[u]);
-            racc[u] = fmaf(av.w, xv.w, racc[u]);
+            for (int u = 0; u < 4; ++u) {
+              const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
+              racc[u] = fmaf(av.x, xv.x, racc[u]);
+              racc[u] = fmaf(av.y, xv.y, racc[u]);
+              racc[u] = fmaf(av.z, xv.z, racc[u]);
+              racc[u] = fmaf(av.w, xv.w, racc[u]);
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int64_t p = lane; p < a.n; p += 32) {
+            const float xv = xq[p];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
           }
         }
-      } else {
-#pragma unroll 4
-        for (int64_t p = lane; p < a.n; p += 32) {
-          const float xv = xs[p];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
+        for (int u = 0; u < 4; ++u) {
+          const float v = warp_sum(racc[u]);
+          if (lane == 0 && r0 + u < a.S) vals[r0 + u] = v;
         }
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float v = warp_sum(racc[u]);
-        if (lane == 0 && r0 + u < a.S) vals[r0 + u] = v;
-      }
-    }
-    __syncthreads();
-    {
-      const int seg = (a.S + kQThreads - 1) / kQThreads;
-      const int lo = tid * seg, hi = lo + seg < a.S ? lo + seg : a.S;
-      const bool full = a.flags & KERDOCK_FLAG_FULL_OUTPUT;
-      int keep = 0;
-      for (int r = lo; r < hi; ++r) keep += full || fabsf(vals[r]) >= a.eps;
-      int tot;
-      int pos = block_exclusive_scan(keep, s_scan, &tot);
-      const int64_t obase = q * a.S;
-      for (int r = lo; r < hi; ++r) {
-        if (full || fabsf(vals[r]) >= a.eps) {
-          a.out_idx[obase + pos] = sel[r];
-          a.out_val[obase + pos] = vals[r];
-          ++pos;
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      {
+        const int seg = (a.S + kFinalThreads - 1) / kFinalThreads;
+        const int lo = ft * seg, hi = lo + seg < a.S ? lo + seg : a.S;
+        const bool full = a.flags & KERDOCK_FLAG_FULL_OUTPUT;
+        int keep = 0;
+        for (int r = lo; r < hi; ++r) keep += full || fabsf(vals[r]) >= a.eps;
+        int tot;
+        int pos = final_exclusive_scan(keep, sh.scan, &tot);
+        const int64_t obase = q * a.S;
+        for (int r = lo; r < hi; ++r) {
+          if (full || fabsf(vals[r]) >= a.eps) {
+            a.out_idx[obase + pos] = sel[r];
+            a.out_val[obase + pos] = vals[r];
+            ++pos;
+          }
         }
+        if (ft == 0) a.out_count[q] = tot;
       }
-      if (tid == 0) a.out_count[q] = tot;
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      if (ft == 0) mbar_arrive(&sh.x_empty[xb]);  // x of this query no longer needed
     }
-    // The ring area was written through the generic proxy (mu, selection,
-    // values); order those writes before the next query's TMA writes.
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
   }
 }
 
+size_t align_up(size_t v, size_t al) { return (v + al - 1) / al * al; }
+
 struct Layout {
   int nslot;
-  uint32_t row_bytes;
-  size_t ring, off_xs, off_ells, off_coefs, off_means, total;
+  uint32_t row_bytes, sign_bytes;
+  size_t off_sgn, off_ell, off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
   bool means_in_smem;
+  int64_t xpad;
 };
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 Layout make_layout(const Plan& p) {
   Layout L{};
   L.row_bytes = uint32_t(p.ldr * p.elem_bytes());
-  int ns = int(kRingTarget / L.row_bytes);
-  ns = ns < 2 ? 2 : ns > kMaxSlots ? kMaxSlots : ns;
-  L.nslot = ns;
+  const int64_t nwords = (p.n + 31) / 32;
+  L.sign_bytes = uint32_t(align_up(size_t(nwords) * 4, 16));
+  L.xpad = p.d > 32 ? p.d : 32;
   const size_t spad = align_up(size_t(p.S), 4);
-  size_t ring = size_t(ns) * L.row_bytes;
-  const size_t post = size_t(p.ldr) * 4 + 2 * spad * 4;  // mu, sel, vals
-  if (post > ring) ring = post;
-  L.ring = align_up(ring, 128);
-  L.off_xs = L.ring;
-  const size_t xpad = size_t(p.d > 32 ? p.d : 32);
-  L.off_ells = align_up(L.off_xs + xpad * 4, 16);
-  L.off_coefs = L.off_ells + size_t(kChunk) * 4;
-  L.off_means = align_up(L.off_coefs + size_t(kChunk) * 4, 16);
-  const size_t means_bytes = size_t(p.K) * size_t(p.ldr) * 4;
+  const size_t means_bytes = size_t(kMBufs) * size_t(p.K) * size_t(p.ldr) * 4;
   L.means_in_smem = means_bytes <= kMeansSmemMax;
-  L.total = L.off_means + (L.means_in_smem ? means_bytes : 0);
+  // fixed (non-ring) parts, with slack for alignment
+  const size_t fixed = size_t(kXBufs) * size_t(L.xpad) * 4 +
+                       (L.means_in_smem ? means_bytes : 0) + size_t(p.ldr) * 4 +
+                       2 * spad * 4 + 1024;
+  const size_t per_slot = size_t(L.row_bytes) + L.sign_bytes + 8;
+  size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
+  const size_t cap = kRingCap + size_t(kMaxSlots) * (L.sign_bytes + 8);
+  if (avail > cap) avail = cap;
+  int ns = int(avail / per_slot);
+  if (ns > kMaxSlots) ns = kMaxSlots;
+  L.nslot = ns;
+  size_t off = align_up(size_t(ns) * L.row_bytes, 128);
+  L.off_sgn = off;
+  off = align_up(off + size_t(ns) * L.sign_bytes, 16);
+  L.off_ell = off;
+  off = align_up(off + size_t(ns) * 4, 16);
+  L.off_coef = off;
+  off = align_up(off + size_t(ns) * 4, 16);
+  L.off_x = off;
+  off = align_up(off + size_t(kXBufs) * size_t(L.xpad) * 4, 16);
+  L.off_means = off;
+  if (L.means_in_smem) off = align_up(off + means_bytes, 16);
+  L.off_mu = off;
+  off = align_up(off + size_t(p.ldr) * 4, 16);
+  L.off_sel = off;
+  off = align_up(off + spad * 4, 16);
+  L.off_vals = off;
+  off = align_up(off + spad * 4, 16);
+  L.total = off;
   return L;
 }
 
@@ -536,13 +655,12 @@ int launch_typed(const Plan& p, const Layout& L, QueryArgs& a, void* ws) {
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    int(L.total)));
   int occ = 0;
-  KD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kQThreads, L.total));
+  KD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, L.total));
   if (occ < 1) return KERDOCK_ERR_UNSUPPORTED;
-  if (occ > kMaxCtasPerSm) occ = kMaxCtasPerSm;
-  int64_t grid = int64_t(p.num_sms) * occ;
+  int64_t grid = p.num_sms;
   if (grid > a.Q) grid = a.Q;
   a.means_gmem = L.means_in_smem ? nullptr : static_cast<float*>(ws);
-  kern<<<unsigned(grid), kQThreads, L.total, p.stream>>>(a);
+  kern<<<unsigned(grid), kThreads, L.total, p.stream>>>(a);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }
@@ -552,7 +670,8 @@ int launch_typed(const Plan& p, const Layout& L, QueryArgs& a, void* ws) {
 size_t apply_workspace_bytes(const Plan& p, int64_t q) {
   const Layout L = make_layout(p);
   if (L.means_in_smem || q == 0) return 0;
-  return size_t(p.num_sms > 0 ? p.num_sms : 160) * kMaxCtasPerSm * size_t(p.K) * size_t(p.ldr) * 4;
+  const int64_t grid = p.num_sms > 0 ? p.num_sms : 256;
+  return size_t(grid) * kMBufs * size_t(p.K) * size_t(p.ldr) * 4;
 }
 
 int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps, uint64_t seed,
@@ -560,10 +679,12 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
                  size_t ws_bytes, float* mu_out, int64_t* ells_out, float* coef_out) {
   (void)ws_bytes;
   const Layout L = make_layout(p);
+  if (L.nslot < kMinSlots || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
   QueryArgs a{};
   a.R = p.repr;
   a.signs = p.signs();
-  a.sign_words = p.sign_words;
+  a.sign_stride = p.sign_words;
+  a.sign_bytes = L.sign_bytes;
   a.A = p.A;
   a.lda = p.lda;
   a.X = X;
@@ -575,6 +696,7 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.L = p.L;
   a.ldr = p.ldr;
   a.N = p.N;
+  a.xpad = L.xpad;
   a.k = p.k;
   a.J = p.J;
   a.K = p.K;
@@ -584,13 +706,18 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.sqrt_d = float(int64_t(1) << (p.k / 2));
   a.seed = seed;
   a.flags = flags;
-  a.a_vec4 = (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
+  a.a_vec4 =
+      (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
   a.nslot = L.nslot;
   a.row_bytes = L.row_bytes;
-  a.off_xs = uint32_t(L.off_xs);
-  a.off_ells = uint32_t(L.off_ells);
-  a.off_coefs = uint32_t(L.off_coefs);
+  a.off_sgn = uint32_t(L.off_sgn);
+  a.off_ell = uint32_t(L.off_ell);
+  a.off_coef = uint32_t(L.off_coef);
+  a.off_x = uint32_t(L.off_x);
   a.off_means = uint32_t(L.off_means);
+  a.off_mu = uint32_t(L.off_mu);
+  a.off_sel = uint32_t(L.off_sel);
+  a.off_vals = uint32_t(L.off_vals);
   a.out_idx = out_idx;
   a.out_val = out_val;
   a.out_count = out_count;
@@ -599,7 +726,7 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.coef_out = coef_out;
   a.status = p.status();
   const int64_t granule = 16 / int64_t(p.elem_bytes());
-  const int64_t gpt = (p.ldr / granule + kQThreads - 1) / kQThreads;
+  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
   const bool xreg = p.n <= 1024;
   if (p.dtype == KERDOCK_BF16) {
     if (gpt <= 1) return xreg ? launch_typed<__nv_bfloat16, 1, true>(p, L, a, ws)

@@ -150,7 +150,7 @@ def kerdock_sync(plan):
 
 def kerdock_debug_signs(plan):
     info = kerdock_plan_info(plan)
-    words = max(1, info["d"] // 32)
+    words = max(4, info["d"] // 32)
     out = np.zeros((info["d"] // 2, words), dtype=np.uint32)
     _check(load_library().kerdock_debug_signs(
         plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out.size), "kerdock_debug_signs")
