@@ -111,7 +111,9 @@ int kerdock_plan_info(kerdock_plan_t plan, kerdock_plan_info_t* info);
  * bytes, table_dev info.table_bytes bytes; both 256-byte aligned.  Builds the
  * Kerdock sign tables D_b on the device (step (i) of Lemma 6: one bit
  * Q_{M_b}(p) per (b, p), computed from the GF(2^(k-1)) construction of
- * Prop. 5) and clears the device status word, asynchronously on the stream. */
+ * Prop. 5; stored twice, in p order for the preprocessing and transposed by
+ * p mod 32 for the coefficient step) and clears the device status word,
+ * asynchronously on the stream. */
 int kerdock_plan_bind(kerdock_plan_t plan, void* repr_dev, size_t repr_bytes,
                       void* table_dev, size_t table_bytes, void* stream);
 

@@ -24,6 +24,7 @@ struct Plan {
   int k = 0, dtype = KERDOCK_F32, J = 0, K = 0, S = 0;
   int64_t N = 0;
   int64_t sign_words = 0;  // uint32 words per sign-table row: max(4, d/32)
+  int64_t tsign_words = 0;  // words per row of the lane-transposed table: max(32, d/32)
   size_t repr_bytes = 0, table_bytes = 0;
   // bound device memory
   void* repr = nullptr;
@@ -42,6 +43,9 @@ struct Plan {
   uint32_t* signs() const {
     return reinterpret_cast<uint32_t*>(static_cast<char*>(table) + kStatusBytes);
   }
+  // Lane-transposed copy of the sign table for the coefficient step: for basis
+  // b, word [g][L] holds in bit t the sign bit of p = 32 (32 g + t) + L.
+  uint32_t* tsigns() const { return signs() + (d / 2) * sign_words; }
   size_t elem_bytes() const { return dtype == KERDOCK_BF16 ? 2 : 4; }
 };
 

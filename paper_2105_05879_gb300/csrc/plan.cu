@@ -53,7 +53,16 @@ __device__ uint32_t trace_mask(int f, uint32_t poly) {
 // (x,alpha).(y,beta) = tr(xy) + alpha*beta (Prop. 5).  Then Q_{M_b}(p) =
 // sum_{a<c} M_ac p_a p_c = XOR over set bits a of p of parity(U_a & p), where
 // U_a holds the entries of row a above the diagonal.
-__global__ void signs_kernel(uint32_t* __restrict__ signs, int k, int64_t words_per_row) {
+// Q_M(p) = XOR over set bits a of p of parity(U_a & p).
+__device__ __forceinline__ uint32_t quad_form(const uint32_t* upper, int k, uint32_t p) {
+  uint32_t q = 0;
+  for (int a = 0; a < k; ++a)
+    if ((p >> a) & 1u) q ^= __popc(upper[a] & p) & 1u;
+  return q;
+}
+
+__global__ void signs_kernel(uint32_t* __restrict__ signs, uint32_t* __restrict__ tsigns, int k,
+                             int64_t words_per_row, int64_t twords_per_row) {
   const int f = k - 1;
   const uint32_t poly = c_field_poly[f];
   const uint32_t b = blockIdx.x;
@@ -93,12 +102,19 @@ __global__ void signs_kernel(uint32_t* __restrict__ signs, int k, int64_t words_
     for (int j = 0; j < 32; ++j) {
       const int64_t p = w * 32 + j;
       if (p >= d) break;
-      uint32_t q = 0;
-      for (int a = 0; a < k; ++a)
-        if ((p >> a) & 1) q ^= __popc(s_upper[a] & uint32_t(p)) & 1u;
-      bits |= q << j;
+      bits |= quad_form(s_upper, k, uint32_t(p)) << j;
     }
     signs[int64_t(b) * words_per_row + w] = bits;
+  }
+  // Lane-transposed layout: word [g][L], bit t <-> p = 32 (32 g + t) + L.
+  for (int64_t i = threadIdx.x; i < twords_per_row; i += blockDim.x) {
+    const int64_t g = i >> 5, L = i & 31;
+    uint32_t bits = 0;
+    for (int t = 0; t < 32; ++t) {
+      const int64_t p = 32 * (32 * g + t) + L;
+      if (p < d) bits |= quad_form(s_upper, k, uint32_t(p)) << t;
+    }
+    tsigns[int64_t(b) * twords_per_row + i] = bits;
   }
 }
 
@@ -106,7 +122,8 @@ __global__ void signs_kernel(uint32_t* __restrict__ signs, int k, int64_t words_
 
 int launch_signs(const Plan& p) {
   KD_CUDA_TRY(cudaMemsetAsync(p.table, 0, kStatusBytes, p.stream));
-  signs_kernel<<<unsigned(p.d / 2), 128, 0, p.stream>>>(p.signs(), p.k, p.sign_words);
+  signs_kernel<<<unsigned(p.d / 2), 128, 0, p.stream>>>(p.signs(), p.tsigns(), p.k,
+                                                         p.sign_words, p.tsign_words);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }
@@ -164,7 +181,9 @@ int kerdock_plan_create(kerdock_plan_t* plan, int64_t m, int64_t n, int32_t dtyp
   p.N = int64_t(J) * K;
   p.sign_words = p.d >= 128 ? p.d / 32 : 4;  // rows padded to 16 bytes (TMA copies)
   p.repr_bytes = size_t(p.B) * size_t(p.d) * size_t(p.ldr) * p.elem_bytes();
-  p.table_bytes = kd::kStatusBytes + size_t(p.d / 2) * size_t(p.sign_words) * 4;
+  p.tsign_words = p.d >= 1024 ? p.d / 32 : 32;
+  p.table_bytes =
+      kd::kStatusBytes + size_t(p.d / 2) * size_t(p.sign_words + p.tsign_words) * 4;
   *plan = h;
   return KERDOCK_OK;
 }

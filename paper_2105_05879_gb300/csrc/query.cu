@@ -12,11 +12,13 @@
 // Kernel design: a persistent, warp-specialised CTA per SM works through its
 // queries as one continuous stream of samples, so that the representation rows
 // (the HBM stream that bounds the method) never stop flowing:
-//   warp 0        producer: draws l_j (32 lanes at a time) and, per sample,
-//                 issues two TMA bulk copies into a ring slot -- the row
-//                 R[l_j][0..m) and the sign-table row of basis b -- completing
-//                 on the slot's mbarriers; loads x of upcoming queries.
-//   warps 1..3    coefficient warps: c_j from the slot's sign bits and x.
+//   warp 0        producer: each lane draws one l_j and issues the TMA bulk
+//                 copy of the row R[l_j][0..m) into its own ring slot, so one
+//                 warp instruction puts up to 32 rows in flight; it also loads
+//                 x of upcoming queries.
+//   warps 1..3    coefficient warps: draw the same l_j themselves and compute
+//                 c_j for blocks of four samples at a time from the
+//                 lane-transposed sign table and x, ahead of the gather.
 //   warps 4..11   gather warps: each thread owns fixed 16-byte column granules
 //                 and accumulates c_j R[l_j] in registers in sample order (a
 //                 fixed, deterministic summation order); batch means go to a
@@ -52,9 +54,8 @@ constexpr size_t kMeansSmemMax = 64 * 1024;
 
 struct QueryArgs {
   const void* R;
-  const uint32_t* signs;
-  int64_t sign_stride;  // words per sign-table row
-  uint32_t sign_bytes;  // bytes copied per Kerdock sample: 4 * ceil(n/32) rounded to 16
+  const uint32_t* tsigns;  // lane-transposed sign table
+  int64_t tsign_stride;    // words per basis in it
   const float* A;
   int64_t lda;
   const float* X;
@@ -66,9 +67,10 @@ struct QueryArgs {
   int flags;
   int a_vec4;  // rows of A are 16-byte aligned and n % 4 == 0
   int nslot;
+  int pgroup;  // samples the producer issues per warp instruction (<= 32, <= nslot / 2)
   uint32_t row_bytes;
   // dynamic shared-memory layout (byte offsets)
-  uint32_t off_sgn, off_ell, off_coef, off_x, off_means, off_mu, off_sel, off_vals;
+  uint32_t off_coef, off_x, off_means, off_mu, off_sel, off_vals;
   float* means_gmem;  // non-null when the batch means live in the workspace
   int32_t* out_idx;
   float* out_val;
@@ -137,59 +139,61 @@ __device__ __forceinline__ int final_exclusive_scan(int v, int* scratch, int* to
 
 __device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 
-// 32x32 bit-matrix transpose across a warp: on entry lane L holds row L
-// (bit t = entry (L, t)); on exit lane L holds column L (bit t = entry (t, L)).
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
-  const uint32_t lo_masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int j = 16 >> i;
-    const uint32_t msk = lo_masks[i];
-    const uint32_t t = __shfl_xor_sync(0xffffffffu, v, j);
-    v = (lane & j) ? ((v & ~msk) | ((t >> j) & msk)) : ((v & msk) | ((t & msk) << j));
-  }
-  return v;
-}
-
-// c = s_l^T x for a Kerdock sample l = (b, w): sum over p < n of
-// (-1)^{Q_b(p) + w.p} x_p.  Lane L owns p = 32 t + L.  The sign words of basis
-// b (already in shared memory) are transposed so that lane L holds, in one
-// register, the bits of its own p for 32 values of t; the Walsh character
-// (-1)^{w.p} splits into a per-lane part (-1)^{(w mod 32).L} and a per-t part
-// (-1)^{(w >> 5).t}, both folded into that register.  x comes from registers
-// (XREG, n <= 1024: xr[t] = x_{32t+L}) or from shared memory.
+// Coefficients c = s_l^T x of up to four Kerdock samples l = (b, w) at once:
+// c = sum over p < n of (-1)^{Q_b(p) + w.p} x_p.  Lane L owns p = 32 t + L.
+// The lane-transposed table gives lane L, in one word per 1024 values of p,
+// the bits Q_b(32 t + L) for 32 values of t; the Walsh character (-1)^{w.p}
+// splits into a per-lane part (-1)^{(w mod 32).L} and a per-t part
+// (-1)^{(w >> 5).t}, both folded into that word.  Four samples are processed
+// together so that their loads, sums and warp reductions overlap.  x comes
+// from registers (XREG, n <= 1024: xr[t] = x_{32t+L}) or from shared memory.
 template <bool XREG>
-__device__ __forceinline__ float kerdock_coefficient(const uint32_t* srow, int nwords, uint32_t w,
-                                                     int lane, const float (&xr)[32],
-                                                     const float* xs) {
-  const uint32_t whi = w >> 5;
-  const uint32_t pl = __popc(w & 31u & uint32_t(lane)) & 1u;
-  const uint32_t wmask = __ballot_sync(0xffffffffu, __popc(whi & 31u & uint32_t(lane)) & 1u);
-  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-  const int groups = (nwords + 31) >> 5;
-  for (int g = 0; g < groups; ++g) {
-    const int t0 = g << 5;
-    const uint32_t word = t0 + lane < nwords ? srow[t0 + lane] : 0u;
-    uint32_t F = warp_transpose32(word, lane) ^ wmask;
-    if ((__popc(whi & uint32_t(t0)) & 1u) ^ pl) F = ~F;
+__device__ __forceinline__ void kerdock_coefficients4(const uint32_t* __restrict__ tsigns,
+                                                      int64_t tstride, const uint32_t (&ell)[4],
+                                                      int kbits, uint32_t dmask, int groups,
+                                                      int lane, const float (&xr)[32],
+                                                      const float* xs, float (&c)[4]) {
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
+  uint32_t whi[4], pl[4], wmask[4];
+  const uint32_t* rows[4];
 #pragma unroll
-    for (int t = 0; t < 32; t += 4) {
-      const float x0 = XREG ? xr[t] : xs[(t0 + t) * 32 + lane];
-      const float x1 = XREG ? xr[t + 1] : xs[(t0 + t + 1) * 32 + lane];
-      const float x2 = XREG ? xr[t + 2] : xs[(t0 + t + 2) * 32 + lane];
-      const float x3 = XREG ? xr[t + 3] : xs[(t0 + t + 3) * 32 + lane];
-      acc0 += __uint_as_float(__float_as_uint(x0) ^ ((F << (31 - t)) & 0x80000000u));
-      acc1 += __uint_as_float(__float_as_uint(x1) ^ ((F << (30 - t)) & 0x80000000u));
-      acc2 += __uint_as_float(__float_as_uint(x2) ^ ((F << (29 - t)) & 0x80000000u));
-      acc3 += __uint_as_float(__float_as_uint(x3) ^ ((F << (28 - t)) & 0x80000000u));
+  for (int s = 0; s < 4; ++s) {
+    const uint32_t w = ell[s] & dmask;
+    whi[s] = w >> 5;
+    pl[s] = __popc(w & 31u & uint32_t(lane)) & 1u;
+    wmask[s] = __ballot_sync(0xffffffffu, __popc(whi[s] & 31u & uint32_t(lane)) & 1u);
+    // identity-basis samples (b = d/2) read row d/2 - 1; their result is replaced
+    const uint32_t b = ell[s] >> kbits;
+    const uint32_t bmax = (dmask + 1u) / 2u - 1u;
+    rows[s] = tsigns + int64_t(b < bmax ? b : bmax) * tstride;
+  }
+  for (int g = 0; g < groups; ++g) {
+    uint32_t F[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) F[s] = __ldg(rows[s] + (g << 5) + lane);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      F[s] ^= wmask[s];
+      if ((__popc(whi[s] & uint32_t(g << 5)) & 1u) ^ pl[s]) F[s] = ~F[s];
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const float xv = XREG ? xr[t] : xs[((g << 5) + t) * 32 + lane];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        part[s] += __uint_as_float(__float_as_uint(xv) ^ ((F[s] << (31 - t)) & 0x80000000u));
     }
   }
-  return warp_sum((acc0 + acc1) + (acc2 + acc3));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) c[s] = part[s];
 }
 
 struct Shared {
   uint64_t row_full[kMaxSlots];
-  uint64_t sgn_full[kMaxSlots];
   uint64_t coef_full[kMaxSlots];
   uint64_t slot_empty[kMaxSlots];
   uint64_t x_full[kXBufs];
@@ -226,8 +230,6 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   __shared__ Shared sh;
 
   unsigned char* ring = smem;
-  uint32_t* sgn = reinterpret_cast<uint32_t*>(smem + a.off_sgn);
-  int32_t* ell_s = reinterpret_cast<int32_t*>(smem + a.off_ell);
   float* coef_s = reinterpret_cast<float*>(smem + a.off_coef);
   float* xbuf = reinterpret_cast<float*>(smem + a.off_x);
   float* means_base = a.means_gmem != nullptr
@@ -241,12 +243,10 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   const RT* R = static_cast<const RT*>(a.R);
   const int64_t half = a.d / 2;
   const uint32_t nslot = uint32_t(a.nslot);
-  const int sign_words_per_slot = int(a.sign_bytes / 4);
 
   if (tid == 0) {
     for (int s = 0; s < a.nslot; ++s) {
       mbar_init(&sh.row_full[s], 1);
-      mbar_init(&sh.sgn_full[s], 1);
       mbar_init(&sh.coef_full[s], 1);
       mbar_init(&sh.slot_empty[s], kGatherWarps);
     }
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    uint32_t slot = 0, phase = 0, uses = 0;
+    uint64_t uses = 0;  // samples issued so far by this CTA
     int qs = 0;
     for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
       const int xb = qs % kXBufs;
@@ -276,50 +276,35 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
       for (int64_t p = lane; p < a.xpad; p += 32) xq[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.x_full[xb]);
-      for (int64_t j0 = 0; j0 < a.N; j0 += 32) {
-        const int64_t j = j0 + lane;
-        uint64_t ell = 0;
-        if (j < a.N) {
-          ell = sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
+      for (int64_t j0 = 0; j0 < a.N; j0 += a.pgroup) {
+        const int cnt = int(a.N - j0 < a.pgroup ? a.N - j0 : a.pgroup);
+        bool ok = true;
+        if (lane < cnt) {
+          const uint64_t u = uses + uint64_t(lane);
+          const uint32_t slot = uint32_t(u % nslot);
+          const uint32_t ph = uint32_t(u / nslot) & 1u;
+          const int64_t j = j0 + lane;
+          const uint64_t ell =
+              sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
           if (a.ells_out) a.ells_out[q * a.N + j] = int64_t(ell);
-        }
-        const int cnt = int(a.N - j0 < 32 ? a.N - j0 : 32);
-        for (int t = 0; t < cnt; ++t) {
-          const uint32_t e = __shfl_sync(0xffffffffu, uint32_t(ell), t);
-          if (lane == 0) {
-            bool ok = true;
-            if (uses >= nslot) ok = wait_phase(&sh.slot_empty[slot], phase ^ 1u, sh, a.status);
-            if (ok) {
-              ell_s[slot] = int32_t(e);
-              const int64_t b = int64_t(e) >> a.k;
-              if (b < half) {
-                mbar_arrive_expect_tx(&sh.sgn_full[slot], a.sign_bytes);
-                bulk_g2s(sgn + size_t(slot) * sign_words_per_slot, a.signs + b * a.sign_stride,
-                         a.sign_bytes, &sh.sgn_full[slot]);
-              } else {
-                mbar_arrive(&sh.sgn_full[slot]);
-              }
-              mbar_arrive_expect_tx(&sh.row_full[slot], a.row_bytes);
-              bulk_g2s(ring + size_t(slot) * a.row_bytes, R + int64_t(e) * a.ldr, a.row_bytes,
-                       &sh.row_full[slot]);
-            }
-          }
-          if (__shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(&sh.abort_flag), 0))
-            return;
-          ++uses;
-          if (++slot == nslot) {
-            slot = 0;
-            phase ^= 1u;
+          if (u >= nslot) ok = wait_phase(&sh.slot_empty[slot], ph ^ 1u, sh, a.status);
+          if (ok) {
+            mbar_arrive_expect_tx(&sh.row_full[slot], a.row_bytes);
+            bulk_g2s(ring + size_t(slot) * a.row_bytes, R + int64_t(ell) * a.ldr, a.row_bytes,
+                     &sh.row_full[slot]);
           }
         }
+        if (__any_sync(0xffffffffu, !ok)) return;
+        uses += uint64_t(cnt);
       }
     }
   } else if (warp < kFirstGatherWarp) {
     // ------------------------------------------------------------ coefficients
     const int cw = warp - kFirstCoefWarp;
-    uint32_t slot = uint32_t(cw), phase = 0;  // nslot >= kMinSlots > kCoefWarps
-    int64_t g_next = cw;                      // global sample counter of this warp
-    const int nwords = int((a.n + 31) / 32);
+    const int groups = int((a.n + 1023) / 1024);
+    const uint32_t dmask = uint32_t(a.d - 1);
+    const int64_t nblk = (a.N + 3) / 4;
+    int64_t blk_base = 0;  // blocks of four samples handed out before this query
     int qs = 0;
     float xr[32];
     for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
@@ -328,31 +313,39 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
       const float* xq = xbuf + xb * a.xpad;
 #pragma unroll
       for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < a.xpad) ? xq[t * 32 + lane] : 0.f;
-      const int64_t g_end = int64_t(qs + 1) * a.N;
-      for (; g_next < g_end; g_next += kCoefWarps) {
-        if (!wait_phase(&sh.sgn_full[slot], phase, sh, a.status)) return;
-        const uint32_t e = uint32_t(ell_s[slot]);
-        const int64_t b = int64_t(e) >> a.k;
-        const uint32_t w = e & uint32_t(a.d - 1);
-        float c;
-        if (b == half) {
-          c = w < a.n ? a.sqrt_d * xq[w] : 0.f;
-        } else {
-          c = kerdock_coefficient<XREG>(sgn + size_t(slot) * sign_words_per_slot, nwords, w, lane,
-                                        xr, xq);
+      int64_t i = (cw - blk_base % kCoefWarps + kCoefWarps) % kCoefWarps;
+      for (; i < nblk; i += kCoefWarps) {
+        const int64_t j0 = i * 4;
+        const int cnt = int(a.N - j0 < 4 ? a.N - j0 : 4);
+        uint32_t ell[4];
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+          const int64_t j = j0 + (s2 < cnt ? s2 : 0);
+          ell[s2] = uint32_t(
+              sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L)));
         }
-        if (lane == 0) {
-          coef_s[slot] = c;
-          if (a.coef_out) a.coef_out[q * a.N + (g_next - int64_t(qs) * a.N)] = c;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.coef_full[slot]);
-        slot += kCoefWarps;
-        if (slot >= nslot) {
-          slot -= nslot;
-          phase ^= 1u;
+        float c[4];
+        kerdock_coefficients4<XREG>(a.tsigns, a.tsign_stride, ell, a.k, dmask, groups, lane, xr,
+                                    xq, c);
+        const uint64_t u0 = uint64_t(qs) * uint64_t(a.N) + uint64_t(j0);
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+          if (s2 >= cnt) break;
+          const uint32_t w = ell[s2] & dmask;
+          if (int64_t(ell[s2] >> a.k) == half) c[s2] = w < a.n ? a.sqrt_d * xq[w] : 0.f;
+          const uint64_t u = u0 + uint64_t(s2);
+          const uint32_t slot = uint32_t(u % nslot);
+          const uint32_t ph = uint32_t(u / nslot) & 1u;
+          // the gather warps must be done with this slot's previous sample
+          if (u >= nslot && !wait_phase(&sh.slot_empty[slot], ph ^ 1u, sh, a.status)) return;
+          if (lane == 0) {
+            coef_s[slot] = c[s2];
+            if (a.coef_out) a.coef_out[q * a.N + j0 + s2] = c[s2];
+            mbar_arrive(&sh.coef_full[slot]);
+          }
         }
       }
+      blk_base += nblk;
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.x_empty[xb]);
     }
@@ -370,45 +363,61 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 #pragma unroll
         for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
       int batch_left = a.J, batch = 0;
-      for (int64_t j = 0; j < a.N; ++j) {
-        if (!wait_phase(&sh.row_full[slot], phase, sh, a.status)) return;
-        if (!wait_phase(&sh.coef_full[slot], phase, sh, a.status)) return;
-        const float c = coef_s[slot];
-        const unsigned char* row = ring + size_t(slot) * a.row_bytes;
+      for (int64_t j0 = 0; j0 < a.N; j0 += 4) {
+        const int cnt = int(a.N - j0 < 4 ? a.N - j0 : 4);
+        uint32_t slots[4];
 #pragma unroll
-        for (int u = 0; u < GPT; ++u) {
-          const int gi = gt + u * kGatherThreads;
-          if (gi * GR < a.ldr) {
-            float v[GR];
-            G::load(row + size_t(gi) * 16, v);
-#pragma unroll
-            for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
+        for (int s2 = 0; s2 < 4; ++s2) {
+          slots[s2] = slot;
+          if (s2 < cnt) {
+            if (!wait_phase(&sh.row_full[slot], phase, sh, a.status)) return;
+            if (!wait_phase(&sh.coef_full[slot], phase, sh, a.status)) return;
+            if (++slot == nslot) {
+              slot = 0;
+              phase ^= 1u;
+            }
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.slot_empty[slot]);
-        if (++slot == nslot) {
-          slot = 0;
-          phase ^= 1u;
-        }
-        if (--batch_left == 0) {
-          if (batch == 0 && qs >= kMBufs &&
-              !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, a.status))
-            return;
-          float* mrow = means + int64_t(batch) * a.ldr;
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2) {
+          if (s2 >= cnt) break;
+          const float c = coef_s[slots[s2]];
+          const unsigned char* row = ring + size_t(slots[s2]) * a.row_bytes;
 #pragma unroll
           for (int u = 0; u < GPT; ++u) {
             const int gi = gt + u * kGatherThreads;
             if (gi * GR < a.ldr) {
+              float v[GR];
+              G::load(row + size_t(gi) * 16, v);
 #pragma unroll
-              for (int e = 0; e < GR; ++e) {
-                mrow[gi * GR + e] = acc[u][e] * a.inv_J;
-                acc[u][e] = 0.f;
-              }
+              for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
             }
           }
-          batch_left = a.J;
-          ++batch;
+          if (--batch_left == 0) {
+            if (batch == 0 && qs >= kMBufs &&
+                !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, a.status))
+              return;
+            float* mrow = means + int64_t(batch) * a.ldr;
+#pragma unroll
+            for (int u = 0; u < GPT; ++u) {
+              const int gi = gt + u * kGatherThreads;
+              if (gi * GR < a.ldr) {
+#pragma unroll
+                for (int e = 0; e < GR; ++e) {
+                  mrow[gi * GR + e] = acc[u][e] * a.inv_J;
+                  acc[u][e] = 0.f;
+                }
+              }
+            }
+            batch_left = a.J;
+            ++batch;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+          for (int s2 = 0; s2 < 4; ++s2)
+            if (s2 < cnt) mbar_arrive(&sh.slot_empty[slots[s2]]);
         }
       }
       if (a.means_gmem != nullptr) __threadfence_block();
@@ -601,9 +610,9 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 size_t align_up(size_t v, size_t al) { return (v + al - 1) / al * al; }
 
 struct Layout {
-  int nslot;
-  uint32_t row_bytes, sign_bytes;
-  size_t off_sgn, off_ell, off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
+  int nslot, pgroup;
+  uint32_t row_bytes;
+  size_t off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
   bool means_in_smem;
   int64_t xpad;
 };
@@ -611,8 +620,6 @@ struct Layout {
 Layout make_layout(const Plan& p) {
   Layout L{};
   L.row_bytes = uint32_t(p.ldr * p.elem_bytes());
-  const int64_t nwords = (p.n + 31) / 32;
-  L.sign_bytes = uint32_t(align_up(size_t(nwords) * 4, 16));
   L.xpad = p.d > 32 ? p.d : 32;
   const size_t spad = align_up(size_t(p.S), 4);
   const size_t means_bytes = size_t(kMBufs) * size_t(p.K) * size_t(p.ldr) * 4;
@@ -621,18 +628,17 @@ Layout make_layout(const Plan& p) {
   const size_t fixed = size_t(kXBufs) * size_t(L.xpad) * 4 +
                        (L.means_in_smem ? means_bytes : 0) + size_t(p.ldr) * 4 +
                        2 * spad * 4 + 1024;
-  const size_t per_slot = size_t(L.row_bytes) + L.sign_bytes + 8;
+  const size_t per_slot = size_t(L.row_bytes) + 4;
   size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
-  const size_t cap = kRingCap + size_t(kMaxSlots) * (L.sign_bytes + 8);
+  const size_t cap = kRingCap + size_t(kMaxSlots) * 4;
   if (avail > cap) avail = cap;
   int ns = int(avail / per_slot);
   if (ns > kMaxSlots) ns = kMaxSlots;
   L.nslot = ns;
+  int g = 1;
+  while (g * 2 <= 32 && g * 4 <= ns) g *= 2;  // pgroup <= nslot / 2
+  L.pgroup = g;
   size_t off = align_up(size_t(ns) * L.row_bytes, 128);
-  L.off_sgn = off;
-  off = align_up(off + size_t(ns) * L.sign_bytes, 16);
-  L.off_ell = off;
-  off = align_up(off + size_t(ns) * 4, 16);
   L.off_coef = off;
   off = align_up(off + size_t(ns) * 4, 16);
   L.off_x = off;
@@ -682,9 +688,8 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   if (L.nslot < kMinSlots || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
   QueryArgs a{};
   a.R = p.repr;
-  a.signs = p.signs();
-  a.sign_stride = p.sign_words;
-  a.sign_bytes = L.sign_bytes;
+  a.tsigns = p.tsigns();
+  a.tsign_stride = p.tsign_words;
   a.A = p.A;
   a.lda = p.lda;
   a.X = X;
@@ -709,9 +714,8 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.a_vec4 =
       (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
   a.nslot = L.nslot;
+  a.pgroup = L.pgroup;
   a.row_bytes = L.row_bytes;
-  a.off_sgn = uint32_t(L.off_sgn);
-  a.off_ell = uint32_t(L.off_ell);
   a.off_coef = uint32_t(L.off_coef);
   a.off_x = uint32_t(L.off_x);
   a.off_means = uint32_t(L.off_means);
