@@ -43,8 +43,9 @@ constexpr int kWarps = kFirstFinalWarp + kFinalWarps;  // 16
 constexpr int kThreads = kWarps * 32;                   // 512
 constexpr int kGatherThreads = kGatherWarps * 32;
 constexpr int kFinalThreads = kFinalWarps * 32;
-constexpr int kMaxSlots = 64;
-constexpr int kMinSlots = 4;
+constexpr int kMaxSlots = 64;  // ring rows
+constexpr int kMaxChunks = 64;
+constexpr int kMinChunks = 4;  // > kCoefWarps: each coefficient warp steps kCoefWarps chunks
 constexpr int kXBufs = 3;
 constexpr int kMBufs = 2;
 constexpr int kFinalBarrier = 1;  // named barrier id of the finalizer warps
@@ -66,8 +67,9 @@ struct QueryArgs {
   uint64_t seed;
   int flags;
   int a_vec4;  // rows of A are 16-byte aligned and n % 4 == 0
-  int nslot;
-  int pgroup;  // samples the producer issues per warp instruction (<= 32, <= nslot / 2)
+  int nchunk;   // ring chunks; each holds chunk_rows consecutive samples of one query
+  int crows;    // rows per chunk (1, 2 or 4)
+  int pgroup;   // chunks the producer fills per warp instruction (pgroup * crows <= 32)
   uint32_t row_bytes;
   // dynamic shared-memory layout (byte offsets)
   uint32_t off_coef, off_x, off_means, off_mu, off_sel, off_vals;
@@ -193,9 +195,9 @@ __device__ __forceinline__ void kerdock_coefficients4(const uint32_t* __restrict
 }
 
 struct Shared {
-  uint64_t row_full[kMaxSlots];
-  uint64_t coef_full[kMaxSlots];
-  uint64_t slot_empty[kMaxSlots];
+  uint64_t row_full[kMaxChunks];
+  uint64_t coef_full[kMaxChunks];
+  uint64_t slot_empty[kMaxChunks];
   uint64_t x_full[kXBufs];
   uint64_t x_empty[kXBufs];
   uint64_t means_full[kMBufs];
@@ -242,11 +244,13 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const RT* R = static_cast<const RT*>(a.R);
   const int64_t half = a.d / 2;
-  const uint32_t nslot = uint32_t(a.nslot);
+  const uint32_t nchunk = uint32_t(a.nchunk);
+  const int CR = a.crows;
+  const int64_t qchunks = (a.N + CR - 1) / CR;  // chunks per query
 
   if (tid == 0) {
-    for (int s = 0; s < a.nslot; ++s) {
-      mbar_init(&sh.row_full[s], 1);
+    for (int s = 0; s < a.nchunk; ++s) {
+      mbar_init(&sh.row_full[s], uint32_t(CR));
       mbar_init(&sh.coef_full[s], 1);
       mbar_init(&sh.slot_empty[s], kGatherWarps);
     }
@@ -265,7 +269,9 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    uint64_t uses = 0;  // samples issued so far by this CTA
+    uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
+    uint64_t filled = 0;             // chunks filled so far
+    const int ci = lane / CR, r = lane % CR;
     int qs = 0;
     for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
       const int xb = qs % kXBufs;
@@ -276,26 +282,36 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
       for (int64_t p = lane; p < a.xpad; p += 32) xq[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.x_full[xb]);
-      for (int64_t j0 = 0; j0 < a.N; j0 += a.pgroup) {
-        const int cnt = int(a.N - j0 < a.pgroup ? a.N - j0 : a.pgroup);
+      for (int64_t c0 = 0; c0 < qchunks; c0 += a.pgroup) {
+        const int cnt = int(qchunks - c0 < a.pgroup ? qchunks - c0 : a.pgroup);
         bool ok = true;
-        if (lane < cnt) {
-          const uint64_t u = uses + uint64_t(lane);
-          const uint32_t slot = uint32_t(u % nslot);
-          const uint32_t ph = uint32_t(u / nslot) & 1u;
-          const int64_t j = j0 + lane;
-          const uint64_t ell =
-              sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
-          if (a.ells_out) a.ells_out[q * a.N + j] = int64_t(ell);
-          if (u >= nslot) ok = wait_phase(&sh.slot_empty[slot], ph ^ 1u, sh, a.status);
-          if (ok) {
-            mbar_arrive_expect_tx(&sh.row_full[slot], a.row_bytes);
-            bulk_g2s(ring + size_t(slot) * a.row_bytes, R + int64_t(ell) * a.ldr, a.row_bytes,
-                     &sh.row_full[slot]);
+        if (ci < cnt) {
+          uint32_t cs = cslot + uint32_t(ci), ph = cphase;
+          if (cs >= nchunk) {
+            cs -= nchunk;
+            ph ^= 1u;
+          }
+          if (filled + uint64_t(ci) >= nchunk)
+            ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, a.status);
+          const int64_t j = (c0 + ci) * CR + r;
+          if (ok && j < a.N) {
+            const uint64_t ell =
+                sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
+            if (a.ells_out) a.ells_out[q * a.N + j] = int64_t(ell);
+            mbar_arrive_expect_tx(&sh.row_full[cs], a.row_bytes);
+            bulk_g2s(ring + (size_t(cs) * CR + r) * a.row_bytes, R + int64_t(ell) * a.ldr,
+                     a.row_bytes, &sh.row_full[cs]);
+          } else if (ok) {
+            mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
           }
         }
         if (__any_sync(0xffffffffu, !ok)) return;
-        uses += uint64_t(cnt);
+        filled += uint64_t(cnt);
+        cslot += uint32_t(cnt);
+        if (cslot >= nchunk) {
+          cslot -= nchunk;
+          cphase ^= 1u;
+        }
       }
     }
   } else if (warp < kFirstGatherWarp) {
@@ -303,8 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
     const int cw = warp - kFirstCoefWarp;
     const int groups = int((a.n + 1023) / 1024);
     const uint32_t dmask = uint32_t(a.d - 1);
-    const int64_t nblk = (a.N + 3) / 4;
-    int64_t blk_base = 0;  // blocks of four samples handed out before this query
+    uint32_t cs = uint32_t(cw), ph = 0;  // this warp handles chunks cw, cw + 3, ...
+    uint64_t cc = uint64_t(cw);          // global chunk counter of this warp
     int qs = 0;
     float xr[32];
     for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
@@ -313,46 +329,48 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
       const float* xq = xbuf + xb * a.xpad;
 #pragma unroll
       for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < a.xpad) ? xq[t * 32 + lane] : 0.f;
-      int64_t i = (cw - blk_base % kCoefWarps + kCoefWarps) % kCoefWarps;
-      for (; i < nblk; i += kCoefWarps) {
-        const int64_t j0 = i * 4;
-        const int cnt = int(a.N - j0 < 4 ? a.N - j0 : 4);
+      const uint64_t cend = uint64_t(qs + 1) * uint64_t(qchunks);
+      for (; cc < cend; cc += kCoefWarps) {
+        const int64_t j0 = int64_t(cc - uint64_t(qs) * uint64_t(qchunks)) * CR;
+        const int cnt = int(a.N - j0 < CR ? a.N - j0 : CR);
+        // lanes 0..cnt-1 draw the chunk's indices; everyone gets all four
+        uint32_t my_ell = 0;
+        if (lane < cnt)
+          my_ell = uint32_t(sample_index(
+              a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j0 + lane), uint64_t(a.L)));
         uint32_t ell[4];
 #pragma unroll
-        for (int s2 = 0; s2 < 4; ++s2) {
-          const int64_t j = j0 + (s2 < cnt ? s2 : 0);
-          ell[s2] = uint32_t(
-              sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L)));
-        }
+        for (int s2 = 0; s2 < 4; ++s2) ell[s2] = __shfl_sync(0xffffffffu, my_ell, s2 < cnt ? s2 : 0);
         float c[4];
         kerdock_coefficients4<XREG>(a.tsigns, a.tsign_stride, ell, a.k, dmask, groups, lane, xr,
                                     xq, c);
-        const uint64_t u0 = uint64_t(qs) * uint64_t(a.N) + uint64_t(j0);
+        // the gather warps must be done with this chunk's previous samples
+        if (cc >= nchunk && !wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, a.status)) return;
+        if (lane == 0) {
 #pragma unroll
-        for (int s2 = 0; s2 < 4; ++s2) {
-          if (s2 >= cnt) break;
-          const uint32_t w = ell[s2] & dmask;
-          if (int64_t(ell[s2] >> a.k) == half) c[s2] = w < a.n ? a.sqrt_d * xq[w] : 0.f;
-          const uint64_t u = u0 + uint64_t(s2);
-          const uint32_t slot = uint32_t(u % nslot);
-          const uint32_t ph = uint32_t(u / nslot) & 1u;
-          // the gather warps must be done with this slot's previous sample
-          if (u >= nslot && !wait_phase(&sh.slot_empty[slot], ph ^ 1u, sh, a.status)) return;
-          if (lane == 0) {
-            coef_s[slot] = c[s2];
-            if (a.coef_out) a.coef_out[q * a.N + j0 + s2] = c[s2];
-            mbar_arrive(&sh.coef_full[slot]);
+          for (int s2 = 0; s2 < 4; ++s2) {
+            if (s2 >= cnt) break;
+            const uint32_t w = ell[s2] & dmask;
+            float cv = c[s2];
+            if (int64_t(ell[s2] >> a.k) == half) cv = w < a.n ? a.sqrt_d * xq[w] : 0.f;
+            coef_s[cs * CR + s2] = cv;
+            if (a.coef_out) a.coef_out[q * a.N + j0 + s2] = cv;
           }
+          mbar_arrive(&sh.coef_full[cs]);
+        }
+        cs += kCoefWarps;
+        if (cs >= nchunk) {
+          cs -= nchunk;
+          ph ^= 1u;
         }
       }
-      blk_base += nblk;
       __syncwarp();
       if (lane == 0) mbar_arrive(&sh.x_empty[xb]);
     }
   } else if (warp < kFirstFinalWarp) {
     // ------------------------------------------------------------ gather
     const int gt = tid - kFirstGatherWarp * 32;
-    uint32_t slot = 0, phase = 0;
+    uint32_t cs = 0, ph = 0;
     int qs = 0;
     for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
       const int mb = qs % kMBufs;
@@ -363,26 +381,15 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 #pragma unroll
         for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
       int batch_left = a.J, batch = 0;
-      for (int64_t j0 = 0; j0 < a.N; j0 += 4) {
-        const int cnt = int(a.N - j0 < 4 ? a.N - j0 : 4);
-        uint32_t slots[4];
-#pragma unroll
-        for (int s2 = 0; s2 < 4; ++s2) {
-          slots[s2] = slot;
-          if (s2 < cnt) {
-            if (!wait_phase(&sh.row_full[slot], phase, sh, a.status)) return;
-            if (!wait_phase(&sh.coef_full[slot], phase, sh, a.status)) return;
-            if (++slot == nslot) {
-              slot = 0;
-              phase ^= 1u;
-            }
-          }
-        }
+      for (int64_t j0 = 0; j0 < a.N; j0 += CR) {
+        const int cnt = int(a.N - j0 < CR ? a.N - j0 : CR);
+        if (!wait_phase(&sh.row_full[cs], ph, sh, a.status)) return;
+        if (!wait_phase(&sh.coef_full[cs], ph, sh, a.status)) return;
 #pragma unroll
         for (int s2 = 0; s2 < 4; ++s2) {
           if (s2 >= cnt) break;
-          const float c = coef_s[slots[s2]];
-          const unsigned char* row = ring + size_t(slots[s2]) * a.row_bytes;
+          const float c = coef_s[cs * CR + s2];
+          const unsigned char* row = ring + (size_t(cs) * CR + s2) * a.row_bytes;
 #pragma unroll
           for (int u = 0; u < GPT; ++u) {
             const int gi = gt + u * kGatherThreads;
@@ -414,10 +421,10 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
           }
         }
         __syncwarp();
-        if (lane == 0) {
-#pragma unroll
-          for (int s2 = 0; s2 < 4; ++s2)
-            if (s2 < cnt) mbar_arrive(&sh.slot_empty[slots[s2]]);
+        if (lane == 0) mbar_arrive(&sh.slot_empty[cs]);
+        if (++cs == nchunk) {
+          cs = 0;
+          ph ^= 1u;
         }
       }
       if (a.means_gmem != nullptr) __threadfence_block();
@@ -610,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
 size_t align_up(size_t v, size_t al) { return (v + al - 1) / al * al; }
 
 struct Layout {
-  int nslot, pgroup;
+  int nchunk, crows, pgroup;
   uint32_t row_bytes;
   size_t off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
   bool means_in_smem;
@@ -634,9 +641,12 @@ Layout make_layout(const Plan& p) {
   if (avail > cap) avail = cap;
   int ns = int(avail / per_slot);
   if (ns > kMaxSlots) ns = kMaxSlots;
-  L.nslot = ns;
-  int g = 1;
-  while (g * 2 <= 32 && g * 4 <= ns) g *= 2;  // pgroup <= nslot / 2
+  // rows per chunk: four when the ring still holds at least 8 chunks
+  L.crows = ns >= 32 ? 4 : ns >= 8 ? 2 : 1;
+  L.nchunk = ns / L.crows;
+  ns = L.nchunk * L.crows;
+  int g = 1;  // chunks per producer step: g * crows <= 32 lanes, g <= nchunk / 2
+  while (2 * g * L.crows <= 32 && 4 * g <= L.nchunk) g *= 2;
   L.pgroup = g;
   size_t off = align_up(size_t(ns) * L.row_bytes, 128);
   L.off_coef = off;
@@ -685,7 +695,7 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
                  size_t ws_bytes, float* mu_out, int64_t* ells_out, float* coef_out) {
   (void)ws_bytes;
   const Layout L = make_layout(p);
-  if (L.nslot < kMinSlots || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
+  if (L.nchunk < kMinChunks || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
   QueryArgs a{};
   a.R = p.repr;
   a.tsigns = p.tsigns();
@@ -713,7 +723,8 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   a.flags = flags;
   a.a_vec4 =
       (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
-  a.nslot = L.nslot;
+  a.nchunk = L.nchunk;
+  a.crows = L.crows;
   a.pgroup = L.pgroup;
   a.row_bytes = L.row_bytes;
   a.off_coef = uint32_t(L.off_coef);
