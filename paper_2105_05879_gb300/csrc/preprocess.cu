@@ -8,12 +8,14 @@
 //
 // Kernel design (d <= 1024): a CTA owns a tile of 32 rows of A, kept in
 // shared memory across all the bases it processes, so A is read from HBM once.
-// For each basis a warp g holds, per lane (= row), RG = d/NW consecutive p in
-// registers: sign flip from the bit table, log2(RG) butterfly stages in
-// registers; one shared-memory exchange then moves the NW warp-owned chunks
-// into registers for the remaining log2(NW) stages and, at the same time,
-// transposes the tile so that each store instruction of a warp writes 32
-// consecutive i of one output row R[b][w][.] (128 B for float32).
+// Per basis the sign bits become float sign masks in shared memory (one XOR
+// per element).  Phase 1: a warp g holds, per lane (= row), RG = d/NW
+// consecutive p in registers as float pairs and runs log2(RG) butterfly
+// stages (packed add/sub.f32x2).  One shared-memory exchange then moves the
+// NW warp-owned chunks so that each thread holds two rows x two adjacent w
+// for the remaining log2(NW) stages (packed across the two rows), and stores
+// 8-byte row pairs: a warp store writes two 128-byte runs of consecutive i of
+// output rows R[b][w][.] (float32).
 #include "kerdock_internal.cuh"
 
 namespace kd {
@@ -21,43 +23,85 @@ namespace {
 
 constexpr int kTileRows = 32;
 
-template <typename T>
-__device__ __forceinline__ T to_out(float v);
-template <>
-__device__ __forceinline__ float to_out<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) {
-  return __float2bfloat16_rn(v);
+// Packed-pair helpers: two float lanes in one 64-bit register (add/sub.f32x2).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
 }
 
-// In-register unnormalised FWHT of length RG (bit h of the register index).
-template <int RG>
-__device__ __forceinline__ void fwht_regs(float (&v)[RG]) {
+// Unnormalised FWHT of length 2*NP held as NP float2 pairs (element 2i and
+// 2i+1 in pair i): the stride-1 stage is done inside each pair, the other
+// stages on whole pairs with packed adds.
+template <int NP>
+__device__ __forceinline__ void fwht_pairs(float2 (&v)[NP]) {
 #pragma unroll
-  for (int h = 1; h < RG; h <<= 1) {
+  for (int i = 0; i < NP; ++i) v[i] = make_float2(v[i].x + v[i].y, v[i].x - v[i].y);
 #pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      if (!(r & h)) {
-        const float a = v[r], c = v[r + h];
-        v[r] = a + c;
-        v[r + h] = a - c;
+  for (int h = 1; h < NP; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      if (!(i & h)) {
+        const float2 a = v[i], c = v[i + h];
+        v[i] = add2(a, c);
+        v[i + h] = sub2(a, c);
       }
     }
   }
+}
+
+// Unnormalised FWHT of length NH over an array of float2, each pair carrying
+// two independent transforms (two rows).
+template <int NH>
+__device__ __forceinline__ void fwht_across(float2 (&v)[NH]) {
+#pragma unroll
+  for (int h = 1; h < NH; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      if (!(i & h)) {
+        const float2 a = v[i], c = v[i + h];
+        v[i] = add2(a, c);
+        v[i + h] = sub2(a, c);
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(T* dst, float2 v);
+template <>
+__device__ __forceinline__ void store_pair<float>(float* dst, float2 v) {
+  *reinterpret_cast<float2*>(dst) = v;
+}
+template <>
+__device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* dst, float2 v) {
+  *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v.x, v.y);
 }
 
 template <int LOG_D>
 struct PreCfg {
   static constexpr int D = 1 << LOG_D;
   static constexpr int NW = LOG_D <= 2 ? 1 : LOG_D <= 4 ? 2 : LOG_D <= 6 ? 4 : 8;
-  static constexpr int RG = D / NW;              // register values per thread in phase 1
+  static constexpr int RG = D / NW;                // phase-1 values per thread
   static constexpr int EXP = LOG_D >= 10 ? 2 : 1;  // exchange rounds (bounds shared memory)
-  static constexpr int RGP = RG / EXP;           // registers exchanged per round
-  static constexpr int AST = D + 4;              // A-tile row stride (floats): conflict-free LDS.128
+  static constexpr int RGP = RG / EXP;             // values exchanged per round
+  static constexpr int WPAIRS = RGP / 2 / (2 * NW);  // phase-2 w pairs per thread per round
+  static constexpr int AST = D + 4;                // A-tile row stride (floats): conflict-free LDS.128
   static constexpr int THREADS = NW * 32;
-  static constexpr size_t SMEM =
-      size_t(kTileRows) * AST * 4 + size_t(RGP) * NW * 32 * 4;
-  static_assert(RGP >= NW, "phase 2 needs at least one w_lo per warp");
+  static constexpr size_t SMEM = size_t(kTileRows) * AST * 4 + size_t(RGP) * NW * 32 * 4 +
+                                 size_t(D > 32 ? D : 32) * 4;
+  static_assert(WPAIRS >= 1, "phase 2 needs at least one w pair per thread");
   static_assert(RG >= 4, "vector loads need 4 registers");
 };
 
@@ -79,11 +123,14 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 1)
   constexpr int D = C::D, NW = C::NW, RG = C::RG, RGP = C::RGP, AST = C::AST;
   constexpr int64_t B = D / 2 + 1;
   extern __shared__ __align__(16) float smem[];
-  float* At = smem;                           // [32][AST]
-  float* X = smem + size_t(kTileRows) * AST;  // [RGP * NW][32]
+  float* At = smem;                                         // [32][AST]
+  float2* X2 = reinterpret_cast<float2*>(smem + size_t(kTileRows) * AST);  // [RGP*NW/2][32]
+  uint32_t* Msk = reinterpret_cast<uint32_t*>(smem + size_t(kTileRows) * AST +
+                                              size_t(RGP) * NW * 32);     // [D] sign masks
   OutT* R = static_cast<OutT*>(a.R);
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x >> 5;
+  const int rp = lane & 15, wsel = lane >> 4;  // phase-2 roles: row pair, w-pair selector
   const float sqrt_d = float(1 << (LOG_D / 2));
 
   const int64_t per = a.items / gridDim.x, rem = a.items % gridDim.x;
@@ -95,70 +142,77 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 1)
     const int64_t t = item / B;
     const int b = int(item - t * B);
     const int64_t i0 = t * kTileRows;
+    const bool ident = b == D / 2;
+    __syncthreads();  // everyone is done with the previous item (tile, masks, exchange)
     if (t != cur_tile) {
-      __syncthreads();  // everyone is done with the previous tile
       for (int idx = threadIdx.x; idx < kTileRows * D; idx += C::THREADS) {
         const int i = idx / D, p = idx % D;
         float v = 0.f;
         if (i0 + i < a.m && p < a.n) v = a.A[(i0 + i) * a.lda + p];
         At[i * AST + p] = v;
       }
-      __syncthreads();
       cur_tile = t;
     }
-    const bool ident = b == D / 2;
+    if (!ident) {  // step (i) of Lemma 6 as float sign masks for this basis
+      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words;
+      for (int p = threadIdx.x; p < D; p += C::THREADS)
+        Msk[p] = ((__ldg(srow + (p >> 5)) >> (p & 31)) & 1u) << 31;
+    }
+    __syncthreads();
 
-    // Phase 1: lane = row i, registers = p in [g*RG, (g+1)*RG).
-    float v[RG];
+    // Phase 1: lane = row i, registers = p in [g*RG, (g+1)*RG) as pairs.
+    float2 v[RG / 2];
 #pragma unroll
     for (int r = 0; r < RG; r += 4) {
-      const float4 q = *reinterpret_cast<const float4*>(&At[lane * AST + g * RG + r]);
-      v[r] = q.x;
-      v[r + 1] = q.y;
-      v[r + 2] = q.z;
-      v[r + 3] = q.w;
-    }
-    if (!ident) {
-      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words;
-      if constexpr (RG >= 32) {
-#pragma unroll
-        for (int r0 = 0; r0 < RG; r0 += 32) {
-          const uint32_t word = __ldg(srow + (g * RG + r0) / 32);
-#pragma unroll
-          for (int r = 0; r < 32; ++r) v[r0 + r] = flip_sign(v[r0 + r], (word >> r) & 1u);
-        }
-      } else {
-        const uint32_t word = __ldg(srow + (g * RG) / 32) >> ((g * RG) & 31);
-#pragma unroll
-        for (int r = 0; r < RG; ++r) v[r] = flip_sign(v[r], (word >> r) & 1u);
+      float4 q = *reinterpret_cast<const float4*>(&At[lane * AST + g * RG + r]);
+      if (!ident) {
+        const uint4 mk = *reinterpret_cast<const uint4*>(&Msk[g * RG + r]);
+        q.x = __uint_as_float(__float_as_uint(q.x) ^ mk.x);
+        q.y = __uint_as_float(__float_as_uint(q.y) ^ mk.y);
+        q.z = __uint_as_float(__float_as_uint(q.z) ^ mk.z);
+        q.w = __uint_as_float(__float_as_uint(q.w) ^ mk.w);
       }
-      fwht_regs<RG>(v);
+      v[r / 2] = make_float2(q.x, q.y);
+      v[r / 2 + 1] = make_float2(q.z, q.w);
     }
+    if (!ident) fwht_pairs<RG / 2>(v);
 
-    // Exchange + phase 2, in EXP rounds over the top register bit(s).
+    // Exchange + phase 2, in EXP rounds over the top register bit(s).  The
+    // exchange layout is [w/2][row][2] so that phase 1 writes 8 bytes per
+    // value pair and phase 2 reads 16 bytes = two rows x two adjacent w.
 #pragma unroll
     for (int part = 0; part < C::EXP; ++part) {
-      __syncthreads();  // X is free
+      if (part > 0) __syncthreads();  // X is free
 #pragma unroll
-      for (int r = 0; r < RGP; ++r) X[(g * RGP + r) * 32 + lane] = v[part * RGP + r];
+      for (int r2 = 0; r2 < RGP / 2; ++r2) X2[(g * (RGP / 2) + r2) * 32 + lane] = v[part * (RGP / 2) + r2];
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < RGP / NW; ++u) {
-        const int wl = g * (RGP / NW) + u;
-        float y[NW];
+      for (int u = 0; u < C::WPAIRS; ++u) {
+        const int wp = (g * 2 + wsel) * C::WPAIRS + u;  // w pair index within the round
+        float2 ye[NW], yo[NW];  // (row 2rp, row 2rp+1) for w_lo = 2wp and 2wp+1
 #pragma unroll
-        for (int h = 0; h < NW; ++h) y[h] = X[(h * RGP + wl) * 32 + lane];
+        for (int h = 0; h < NW; ++h) {
+          const float4 f = *reinterpret_cast<const float4*>(&X2[(h * (RGP / 2) + wp) * 32 + 2 * rp]);
+          ye[h] = make_float2(f.x, f.z);
+          yo[h] = make_float2(f.y, f.w);
+        }
         if (!ident) {
-          fwht_regs<NW>(y);
+          fwht_across<NW>(ye);
+          fwht_across<NW>(yo);
         } else {
 #pragma unroll
-          for (int h = 0; h < NW; ++h) y[h] *= sqrt_d;
+          for (int h = 0; h < NW; ++h) {
+            ye[h] = make_float2(ye[h].x * sqrt_d, ye[h].y * sqrt_d);
+            yo[h] = make_float2(yo[h].x * sqrt_d, yo[h].y * sqrt_d);
+          }
         }
-        if (i0 + lane < a.ldr) {
+        const int64_t row = i0 + 2 * rp;
+        if (row < a.ldr) {
 #pragma unroll
           for (int h = 0; h < NW; ++h) {
-            const int64_t w = int64_t(h) * RG + part * RGP + wl;
-            R[(int64_t(b) * D + w) * a.ldr + i0 + lane] = to_out<OutT>(y[h]);
+            const int64_t w = int64_t(h) * RG + part * RGP + 2 * wp;
+            store_pair<OutT>(R + (int64_t(b) * D + w) * a.ldr + row, ye[h]);
+            store_pair<OutT>(R + (int64_t(b) * D + w + 1) * a.ldr + row, yo[h]);
           }
         }
       }
