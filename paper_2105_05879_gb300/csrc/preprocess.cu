@@ -21,7 +21,7 @@
 namespace kd {
 namespace {
 
-constexpr int kTileRows = 32;
+constexpr int kTileRows = 16;
 
 // Packed-pair helpers: two float lanes in one 64-bit register (add/sub.f32x2).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) {
@@ -89,19 +89,25 @@ __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* dst, fl
   *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v.x, v.y);
 }
 
+// Per-size configuration.  A CTA owns TI = 16 rows; D = NW * 2^LH * RG with
+// NW warps, 2^LH lane halves and RG phase-1 registers per thread; SRC = D/RG
+// sources are combined in phase 2; EXP exchange rounds bound shared memory.
 template <int LOG_D>
 struct PreCfg {
   static constexpr int D = 1 << LOG_D;
-  static constexpr int NW = LOG_D <= 2 ? 1 : LOG_D <= 4 ? 2 : LOG_D <= 6 ? 4 : 8;
-  static constexpr int RG = D / NW;                // phase-1 values per thread
-  static constexpr int EXP = LOG_D >= 10 ? 2 : 1;  // exchange rounds (bounds shared memory)
-  static constexpr int RGP = RG / EXP;             // values exchanged per round
-  static constexpr int WPAIRS = RGP / 2 / (2 * NW);  // phase-2 w pairs per thread per round
-  static constexpr int AST = D + 4;                // A-tile row stride (floats): conflict-free LDS.128
+  static constexpr int NW = LOG_D >= 10 ? 8 : LOG_D >= 8 ? 4 : LOG_D >= 6 ? 2 : 1;
+  static constexpr int LH = LOG_D >= 4 ? 1 : 0;
+  static constexpr int RG = D / (NW << LH);
+  static constexpr int SRC = D / RG;
+  static constexpr int EXP = LOG_D >= 10 ? 2 : 1;
+  static constexpr int RGP = RG / EXP;
+  static constexpr int WPS = RGP / (4 * NW);  // phase-2 w per thread per round
+  static constexpr int AST = D + 4;            // A-tile row stride (floats): conflict-free LDS.128
+  static constexpr int XST = RGP * kTileRows + 16;  // floats per source in X (bank shift 16)
   static constexpr int THREADS = NW * 32;
-  static constexpr size_t SMEM = size_t(kTileRows) * AST * 4 + size_t(RGP) * NW * 32 * 4 +
-                                 size_t(D > 32 ? D : 32) * 4;
-  static_assert(WPAIRS >= 1, "phase 2 needs at least one w pair per thread");
+  static constexpr size_t SMEM = size_t(kTileRows) * AST * 4 + size_t(SRC) * XST * 4 +
+                                 2 * size_t(D > 32 ? D : 32) * 4;
+  static_assert(WPS >= 1, "phase 2 needs at least one w per thread");
   static_assert(RG >= 4, "vector loads need 4 registers");
 };
 
@@ -117,20 +123,25 @@ struct PreArgs {
 };
 
 template <int LOG_D, typename OutT>
-__global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 1)
+__global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
     preprocess_small_kernel(const PreArgs a) {
   using C = PreCfg<LOG_D>;
-  constexpr int D = C::D, NW = C::NW, RG = C::RG, RGP = C::RGP, AST = C::AST;
+  constexpr int D = C::D, RG = C::RG, RGP = C::RGP, AST = C::AST, SRC = C::SRC;
+  constexpr int XST = C::XST;
+  constexpr int MPT = (D + C::THREADS - 1) / C::THREADS;  // sign masks per thread
   constexpr int64_t B = D / 2 + 1;
   extern __shared__ __align__(16) float smem[];
-  float* At = smem;                                         // [32][AST]
-  float2* X2 = reinterpret_cast<float2*>(smem + size_t(kTileRows) * AST);  // [RGP*NW/2][32]
-  uint32_t* Msk = reinterpret_cast<uint32_t*>(smem + size_t(kTileRows) * AST +
-                                              size_t(RGP) * NW * 32);     // [D] sign masks
+  float* At = smem;                                 // [16][AST]
+  float* X = smem + size_t(kTileRows) * AST;        // [SRC][XST]: [w][row] per source
+  uint32_t* Msk = reinterpret_cast<uint32_t*>(X + size_t(SRC) * XST);  // [2][max(D,32)]
+  constexpr int MSTRIDE = D > 32 ? D : 32;
   OutT* R = static_cast<OutT*>(a.R);
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x >> 5;
-  const int rp = lane & 15, wsel = lane >> 4;  // phase-2 roles: row pair, w-pair selector
+  const int row = lane & 15, hb = lane >> 4;             // phase 1: row, lane half
+  const int src = (g << C::LH) + hb;                     // phase-1 source index
+  const bool p1 = C::LH == 1 || hb == 0;                 // lane takes part in phase 1
+  const int rp = lane & 7, wsel = lane >> 3;             // phase 2: row pair, w selector
   const float sqrt_d = float(1 << (LOG_D / 2));
 
   const int64_t per = a.items / gridDim.x, rem = a.items % gridDim.x;
@@ -138,12 +149,25 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 1)
   const int64_t end = beg + per + (blockIdx.x < rem ? 1 : 0);
   int64_t cur_tile = -1;
 
+  // Sign words of the first item's basis; later ones are prefetched one item ahead.
+  uint32_t words[MPT];
+  {
+    const int b0 = int(beg % B);
+    const uint32_t* srow = a.signs + int64_t(b0 < D / 2 ? b0 : 0) * a.sign_words;
+#pragma unroll
+    for (int c = 0; c < MPT; ++c) {
+      const int p = threadIdx.x + c * C::THREADS;
+      words[c] = p < D ? __ldg(srow + (p >> 5)) : 0u;
+    }
+  }
+
   for (int64_t item = beg; item < end; ++item) {
     const int64_t t = item / B;
     const int b = int(item - t * B);
     const int64_t i0 = t * kTileRows;
     const bool ident = b == D / 2;
-    __syncthreads();  // everyone is done with the previous item (tile, masks, exchange)
+    uint32_t* mk = Msk + (item & 1) * MSTRIDE;
+    __syncthreads();  // everyone is done with the previous item's tile, exchange and masks
     if (t != cur_tile) {
       for (int idx = threadIdx.x; idx < kTileRows * D; idx += C::THREADS) {
         const int i = idx / D, p = idx % D;
@@ -153,66 +177,73 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 1)
       }
       cur_tile = t;
     }
-    if (!ident) {  // step (i) of Lemma 6 as float sign masks for this basis
-      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words;
-      for (int p = threadIdx.x; p < D; p += C::THREADS)
-        Msk[p] = ((__ldg(srow + (p >> 5)) >> (p & 31)) & 1u) << 31;
+#pragma unroll
+    for (int c = 0; c < MPT; ++c) {  // step (i) of Lemma 6 as float sign masks
+      const int p = threadIdx.x + c * C::THREADS;
+      if (p < D) mk[p] = ((words[c] >> (p & 31)) & 1u) << 31;
+    }
+    if (item + 1 < end) {  // prefetch the next item's sign words
+      const int bn = int((item + 1) % B);
+      const uint32_t* srow = a.signs + int64_t(bn < D / 2 ? bn : 0) * a.sign_words;
+#pragma unroll
+      for (int c = 0; c < MPT; ++c) {
+        const int p = threadIdx.x + c * C::THREADS;
+        words[c] = p < D ? __ldg(srow + (p >> 5)) : 0u;
+      }
     }
     __syncthreads();
 
-    // Phase 1: lane = row i, registers = p in [g*RG, (g+1)*RG) as pairs.
+    // Phase 1: lane = (row, half), registers = p in [src*RG, (src+1)*RG) as pairs.
     float2 v[RG / 2];
+    if (p1) {
 #pragma unroll
-    for (int r = 0; r < RG; r += 4) {
-      float4 q = *reinterpret_cast<const float4*>(&At[lane * AST + g * RG + r]);
-      if (!ident) {
-        const uint4 mk = *reinterpret_cast<const uint4*>(&Msk[g * RG + r]);
-        q.x = __uint_as_float(__float_as_uint(q.x) ^ mk.x);
-        q.y = __uint_as_float(__float_as_uint(q.y) ^ mk.y);
-        q.z = __uint_as_float(__float_as_uint(q.z) ^ mk.z);
-        q.w = __uint_as_float(__float_as_uint(q.w) ^ mk.w);
+      for (int r = 0; r < RG; r += 4) {
+        float4 q = *reinterpret_cast<const float4*>(&At[row * AST + src * RG + r]);
+        if (!ident) {
+          const uint4 m4 = *reinterpret_cast<const uint4*>(&mk[src * RG + r]);
+          q.x = __uint_as_float(__float_as_uint(q.x) ^ m4.x);
+          q.y = __uint_as_float(__float_as_uint(q.y) ^ m4.y);
+          q.z = __uint_as_float(__float_as_uint(q.z) ^ m4.z);
+          q.w = __uint_as_float(__float_as_uint(q.w) ^ m4.w);
+        }
+        v[r / 2] = make_float2(q.x, q.y);
+        v[r / 2 + 1] = make_float2(q.z, q.w);
       }
-      v[r / 2] = make_float2(q.x, q.y);
-      v[r / 2 + 1] = make_float2(q.z, q.w);
+      if (!ident) fwht_pairs<RG / 2>(v);
     }
-    if (!ident) fwht_pairs<RG / 2>(v);
 
-    // Exchange + phase 2, in EXP rounds over the top register bit(s).  The
-    // exchange layout is [w/2][row][2] so that phase 1 writes 8 bytes per
-    // value pair and phase 2 reads 16 bytes = two rows x two adjacent w.
+    // Exchange ([source][w][row]) + phase 2 in EXP rounds over the top register bit(s).
 #pragma unroll
     for (int part = 0; part < C::EXP; ++part) {
       if (part > 0) __syncthreads();  // X is free
+      if (p1) {
 #pragma unroll
-      for (int r2 = 0; r2 < RGP / 2; ++r2) X2[(g * (RGP / 2) + r2) * 32 + lane] = v[part * (RGP / 2) + r2];
+        for (int r2 = 0; r2 < RGP / 2; ++r2) {
+          const float2 val = v[part * (RGP / 2) + r2];
+          X[src * XST + (2 * r2) * kTileRows + row] = val.x;
+          X[src * XST + (2 * r2 + 1) * kTileRows + row] = val.y;
+        }
+      }
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < C::WPAIRS; ++u) {
-        const int wp = (g * 2 + wsel) * C::WPAIRS + u;  // w pair index within the round
-        float2 ye[NW], yo[NW];  // (row 2rp, row 2rp+1) for w_lo = 2wp and 2wp+1
+      for (int u = 0; u < C::WPS; ++u) {
+        const int wl = (g * 4 + wsel) * C::WPS + u;  // w within the round's block
+        float2 y[SRC];  // (row 2rp, row 2rp+1)
 #pragma unroll
-        for (int h = 0; h < NW; ++h) {
-          const float4 f = *reinterpret_cast<const float4*>(&X2[(h * (RGP / 2) + wp) * 32 + 2 * rp]);
-          ye[h] = make_float2(f.x, f.z);
-          yo[h] = make_float2(f.y, f.w);
-        }
+        for (int h = 0; h < SRC; ++h)
+          y[h] = *reinterpret_cast<const float2*>(&X[h * XST + wl * kTileRows + 2 * rp]);
         if (!ident) {
-          fwht_across<NW>(ye);
-          fwht_across<NW>(yo);
+          fwht_across<SRC>(y);
         } else {
 #pragma unroll
-          for (int h = 0; h < NW; ++h) {
-            ye[h] = make_float2(ye[h].x * sqrt_d, ye[h].y * sqrt_d);
-            yo[h] = make_float2(yo[h].x * sqrt_d, yo[h].y * sqrt_d);
-          }
+          for (int h = 0; h < SRC; ++h) y[h] = make_float2(y[h].x * sqrt_d, y[h].y * sqrt_d);
         }
-        const int64_t row = i0 + 2 * rp;
-        if (row < a.ldr) {
+        const int64_t orow = i0 + 2 * rp;
+        if (orow < a.ldr) {
 #pragma unroll
-          for (int h = 0; h < NW; ++h) {
-            const int64_t w = int64_t(h) * RG + part * RGP + 2 * wp;
-            store_pair<OutT>(R + (int64_t(b) * D + w) * a.ldr + row, ye[h]);
-            store_pair<OutT>(R + (int64_t(b) * D + w + 1) * a.ldr + row, yo[h]);
+          for (int h = 0; h < SRC; ++h) {
+            const int64_t w = int64_t(h) * RG + part * RGP + wl;
+            store_pair<OutT>(R + (int64_t(b) * D + w) * a.ldr + orow, y[h]);
           }
         }
       }
