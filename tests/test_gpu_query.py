@@ -190,3 +190,23 @@ def test_query_apply_before_preprocess_fails(K):
         plan.apply(X, 0.1, 0)
     assert e.value.code == -4
     plan.close()
+
+
+def test_query_large_K_uses_workspace(K):
+    # 2 * K * m * 4 bytes of batch means exceed the kernel's shared-memory
+    # budget, so they live in the caller's workspace (K = 16, m = 1024).
+    torch = torch_cuda()
+    n = 1024
+    A = workloads.random_orthogonal(n, 41).astype(np.float32)
+    Z = workloads.sparse_codes(n, 5, 8, 0.35, 42)
+    X = workloads.queries_from_codes(f32(A), Z).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    J, Kb, S = 24, 16, 64
+    plan = K.KerdockPlan(n, n, J=J, K=Kb, S=S)
+    assert K.kerdock_apply_workspace_bytes(plan.handle, X.shape[0]) > 0
+    plan.preprocess(torch.from_numpy(A).cuda())
+    res = plan.apply(torch.from_numpy(X).cuda(), 0.1, 5, flags=1, debug=True)
+    plan.sync()
+    res = tuple(t.cpu().numpy() for t in res)
+    check_query(A64, None, X64, plan, res, 0.1, 5, J, Kb, S, 10, lazy=True, full=True)
+    plan.close()
