@@ -16,6 +16,8 @@
 // for the remaining log2(NW) stages (packed across the two rows), and stores
 // 8-byte row pairs: a warp store writes two 128-byte runs of consecutive i of
 // output rows R[b][w][.] (float32).
+#include <cooperative_groups.h>
+
 #include "kerdock_internal.cuh"
 
 namespace kd {
@@ -251,6 +253,170 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// d = 4096: a cluster of four CTAs shares one tile of 32 rows.  CTA c holds the
+// quarter p in [1024 c, 1024 (c+1)) of those rows in shared memory and runs the
+// first ten butterfly stages there (7 in registers, 3 across its 8 warps via
+// its exchange buffer); the last five stages combine the 32 sources (8 warps x
+// 4 CTAs) per output, read from the four exchange buffers over distributed
+// shared memory.  Each CTA then stores a quarter of the w of the round.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+struct Big {
+  static constexpr int D = 4096, Q = 1024, TI = 32, NW = 8, RG = 128, EXP = 2, RGP = RG / EXP;
+  static constexpr int CL = 4;                 // CTAs per cluster
+  static constexpr int SRC = NW * CL;          // 32 sources in phase 2
+  static constexpr int WPC = RGP / CL;         // w per CTA per round: 16
+  static constexpr int AST = Q + 4;            // A-tile row stride (floats)
+  static constexpr int XST = RGP * TI;         // floats per source: [w][row]
+  static constexpr int THREADS = NW * 32;
+  static constexpr size_t SMEM = size_t(TI) * AST * 4 + size_t(NW) * XST * 4 + size_t(Q) * 4;
+};
+
+template <typename OutT>
+__global__ void __launch_bounds__(Big::THREADS, 1)
+    preprocess_d4096_kernel(const PreArgs a) {
+  using C = Big;
+  constexpr int64_t B = C::D / 2 + 1;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = int(cluster.block_rank());
+  extern __shared__ __align__(16) float smem[];
+  float* At = smem;                                 // [32][AST]: this CTA's quarter
+  float* X = smem + size_t(C::TI) * C::AST;         // [8 sources][RGP w][32 rows]
+  uint32_t* Msk = reinterpret_cast<uint32_t*>(X + size_t(C::NW) * C::XST);  // [1024]
+  const float* Xc[C::CL];
+#pragma unroll
+  for (int c = 0; c < C::CL; ++c) Xc[c] = cluster.map_shared_rank(X, c);
+  OutT* R = static_cast<OutT*>(a.R);
+  const int lane = threadIdx.x & 31;
+  const int g = threadIdx.x >> 5;
+  const int rp = lane & 15, wsel = lane >> 4;
+  const float sqrt_d = 64.f;
+
+  const int64_t ncl = gridDim.x / C::CL, cid = blockIdx.x / C::CL;
+  const int64_t per = a.items / ncl, rem = a.items % ncl;
+  const int64_t beg = cid * per + (cid < rem ? cid : rem);
+  const int64_t end = beg + per + (cid < rem ? 1 : 0);
+  int64_t cur_tile = -1;
+
+  for (int64_t item = beg; item < end; ++item) {
+    const int64_t t = item / B;
+    const int b = int(item - t * B);
+    const int64_t i0 = t * C::TI;
+    const bool ident = b == C::D / 2;
+    cluster.sync();  // every CTA of the cluster is done reading the exchange buffers
+    if (t != cur_tile) {
+      for (int idx = threadIdx.x; idx < C::TI * C::Q; idx += C::THREADS) {
+        const int i = idx / C::Q, p = idx % C::Q;
+        const int64_t gp = int64_t(crank) * C::Q + p;
+        float v = 0.f;
+        if (i0 + i < a.m && gp < a.n) v = a.A[(i0 + i) * a.lda + gp];
+        At[i * C::AST + p] = v;
+      }
+      cur_tile = t;
+    }
+    if (!ident) {  // step (i) of Lemma 6 for this quarter as float sign masks
+      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words + crank * (C::Q / 32);
+      for (int p = threadIdx.x; p < C::Q; p += C::THREADS)
+        Msk[p] = ((__ldg(srow + (p >> 5)) >> (p & 31)) & 1u) << 31;
+    }
+    __syncthreads();
+
+    // Phase 1: lane = row, registers = p in [g*RG, (g+1)*RG) of this quarter.
+    float2 v[C::RG / 2];
+#pragma unroll
+    for (int r = 0; r < C::RG; r += 4) {
+      float4 q = *reinterpret_cast<const float4*>(&At[lane * C::AST + g * C::RG + r]);
+      if (!ident) {
+        const uint4 m4 = *reinterpret_cast<const uint4*>(&Msk[g * C::RG + r]);
+        q.x = __uint_as_float(__float_as_uint(q.x) ^ m4.x);
+        q.y = __uint_as_float(__float_as_uint(q.y) ^ m4.y);
+        q.z = __uint_as_float(__float_as_uint(q.z) ^ m4.z);
+        q.w = __uint_as_float(__float_as_uint(q.w) ^ m4.w);
+      }
+      v[r / 2] = make_float2(q.x, q.y);
+      v[r / 2 + 1] = make_float2(q.z, q.w);
+    }
+    if (!ident) fwht_pairs<C::RG / 2>(v);
+
+#pragma unroll
+    for (int part = 0; part < C::EXP; ++part) {
+      if (part > 0) cluster.sync();  // the previous round's remote reads are done
+#pragma unroll
+      for (int r2 = 0; r2 < C::RGP / 2; ++r2) {
+        const float2 val = v[part * (C::RGP / 2) + r2];
+        X[g * C::XST + (2 * r2) * C::TI + lane] = val.x;
+        X[g * C::XST + (2 * r2 + 1) * C::TI + lane] = val.y;
+      }
+      cluster.sync();  // all four exchange buffers hold this round
+      const int wl = crank * C::WPC + g * 2 + wsel;  // w within the round
+      float2 y[C::SRC];  // source s = 8 * cta + warp <-> p bits 7..11
+#pragma unroll
+      for (int c = 0; c < C::CL; ++c) {
+#pragma unroll
+        for (int h = 0; h < C::NW; ++h)
+          y[c * C::NW + h] =
+              *reinterpret_cast<const float2*>(&Xc[c][h * C::XST + wl * C::TI + 2 * rp]);
+      }
+      if (!ident) {
+        fwht_across<C::SRC>(y);
+      } else {
+#pragma unroll
+        for (int h = 0; h < C::SRC; ++h) y[h] = make_float2(y[h].x * sqrt_d, y[h].y * sqrt_d);
+      }
+      const int64_t orow = i0 + 2 * rp;
+      if (orow < a.ldr) {
+#pragma unroll
+        for (int h = 0; h < C::SRC; ++h) {
+          const int64_t w = int64_t(h) * C::RG + part * C::RGP + wl;
+          store_pair<OutT>(R + (int64_t(b) * C::D + w) * a.ldr + orow, y[h]);
+        }
+      }
+    }
+  }
+  cluster.sync();  // keep this CTA's shared memory alive until the others are done
+}
+
+template <typename OutT>
+int launch_d4096(const Plan& p) {
+  using C = Big;
+  auto kern = preprocess_d4096_kernel<OutT>;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(C::SMEM)));
+  PreArgs a;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.m = p.m;
+  a.n = p.n;
+  a.signs = p.signs();
+  a.sign_words = p.sign_words;
+  a.R = p.repr;
+  a.ldr = p.ldr;
+  a.num_tiles = (p.ldr + C::TI - 1) / C::TI;
+  a.items = a.num_tiles * p.B;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C::CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(C::THREADS);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = p.stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(C::CL);
+  int clusters = 0;
+  KD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
+  if (clusters < 1) return KERDOCK_ERR_UNSUPPORTED;
+  int64_t ncl = clusters;
+  if (ncl > a.items) ncl = a.items;
+  cfg.gridDim = dim3(unsigned(ncl * C::CL));
+  KD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+  return KERDOCK_OK;
+}
+
 template <int LOG_D, typename OutT>
 int launch_small(const Plan& p) {
   using C = PreCfg<LOG_D>;
@@ -286,6 +452,7 @@ int launch_typed(const Plan& p) {
     case 6: return launch_small<6, OutT>(p);
     case 8: return launch_small<8, OutT>(p);
     case 10: return launch_small<10, OutT>(p);
+    case 12: return launch_d4096<OutT>(p);
     default: return KERDOCK_ERR_UNSUPPORTED;
   }
 }

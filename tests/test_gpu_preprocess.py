@@ -93,3 +93,30 @@ def test_preprocess_n1024_sampled_bases(K):
         Rg = representation_slice(plan, b)
         assert np.abs(Rg - Rref[t]).max() <= 1e-4 * np.abs(Rref[t]).max(), b
     plan.close()
+
+
+@pytest.mark.parametrize("m,n,dtype", [(40, 4096, "f32"), (33, 3000, "f32"), (70, 2048, "bf16")])
+def test_preprocess_d4096_parity(K, m, n, dtype):
+    # d = 4096 (k = 12): the four-CTA cluster kernel; the oracle checks a
+    # spread of bases, including the identity basis d/2 = 2048.
+    torch = torch_cuda()
+    rng = np.random.default_rng(m * 31 + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    plan = K.KerdockPlan(m, n, J=1, K=1, S=1, dtype=dtype)
+    assert plan.info["d"] == 4096
+    plan.preprocess(torch.from_numpy(A).cuda())
+    plan.sync()
+    ldr = plan.info["ldr"]
+    Rdev = plan.representation()
+    bases = [0, 1, 2, 5, 100, 1023, 1024, 1500, 2046, 2047, 2048]
+    Rref = okd.representation_lemma6(f32(A), 12, bases=bases)
+    for t_, b in enumerate(bases):
+        Rg = Rdev[b].float().cpu().numpy().astype(np.float64)
+        assert not np.any(Rg[:, m:ldr]), "padding entries must be zero"
+        Rg = Rg[:, :m]
+        scale = np.abs(Rref[t_]).max()
+        if dtype == "f32":
+            assert np.abs(Rg - Rref[t_]).max() <= 1e-4 * scale, b
+        else:
+            assert (np.abs(Rg - Rref[t_]) <= 2.0 ** -8 * np.abs(Rref[t_]) + 1e-6 * scale).all(), b
+    plan.close()

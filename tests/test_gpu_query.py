@@ -210,3 +210,21 @@ def test_query_large_K_uses_workspace(K):
     res = tuple(t.cpu().numpy() for t in res)
     check_query(A64, None, X64, plan, res, 0.1, 5, J, Kb, S, 10, lazy=True, full=True)
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_query_d4096(K, dtype):
+    # n = 4096 (x from shared memory, four sign words per lane), m = 256 rows
+    # with orthonormal rows so that Ax = z for x = A^T z.
+    torch = torch_cuda()
+    m, n = 256, 4096
+    Q, _ = np.linalg.qr(np.random.default_rng(51).standard_normal((n, m)))
+    A = Q.T.astype(np.float32)
+    Z = workloads.sparse_codes(m, 4, 8, 0.35, 52)
+    X = (Z @ f32(A)).astype(np.float32)
+    A64, X64 = f32(A), f32(X)
+    J, Kb, S = 160, 2, 48
+    plan, *res = run_case(K, A, X, J, Kb, S, 0.15, 9, dtype=dtype, flags=1)
+    check_query(A64, None, X64, plan, res, 0.15, 9, J, Kb, S, 12, dtype=dtype, lazy=True,
+                full=True)
+    plan.close()
