@@ -155,6 +155,30 @@ int kerdock_apply_debug(kerdock_plan_t plan, const float* X_dev, int64_t q, int6
                         float* out_val, int32_t* out_count, void* ws_dev, size_t ws_bytes,
                         float* mu_out, int64_t* ells_out, float* coef_out);
 
+/* Allocation-free variant of kerdock_apply (the paper has no counterpart:
+ * this is an integration aid).  It is for callers that cannot allocate
+ * device memory -- code running while a stream is captured into a CUDA
+ * graph, real-time or embedded hosts with a device-memory budget fixed at
+ * start-up, plugin hosts that own the allocator -- and so cannot provide the
+ * workspace kerdock_apply may need.  Same arguments, results and ordering
+ * as kerdock_apply without the workspace; the batch-mean scratch lives in a
+ * 16 MiB array inside the library instead, which every GPU that loads the
+ * library keeps until the process exits.
+ *   - Limit: 8 * K * ldr * min(q, number of SMs) bytes must not exceed
+ *     16 MiB; larger calls return KERDOCK_ERR_CAPACITY and launch nothing
+ *     (e.g. with K = 2 and m = 4096 on a 152-SM GPU it fits; K = 16 with
+ *     m = 1024 does not unless q <= 128).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other plans) race with each other.  Nothing in it needs to
+ *     be cleared between calls.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
+int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                          float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
+                          float* out_val, int32_t* out_count);
+
 /* Synchronise the plan's stream and report the first error any kernel of
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);

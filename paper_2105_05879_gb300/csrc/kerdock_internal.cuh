@@ -57,6 +57,10 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
                  int32_t* out_count, void* ws, size_t ws_bytes, float* mu_out,
                  int64_t* ells_out, float* coef_out);
 size_t apply_workspace_bytes(const Plan& p, int64_t q);
+int launch_apply_noalloc(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps,
+                         uint64_t seed, int flags, int32_t* out_idx, float* out_val,
+                         int32_t* out_count);
+size_t noalloc_scratch_bytes();
 
 // ---------------------------------------------------------------------------
 // Device helpers

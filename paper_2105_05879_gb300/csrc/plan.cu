@@ -291,6 +291,23 @@ int kerdock_apply_debug(kerdock_plan_t plan, const float* X_dev, int64_t q, int6
                       ws_bytes, mu_out, ells_out, coef_out);
 }
 
+int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                          float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
+                          float* out_val, int32_t* out_count) {
+  if (plan == nullptr || q < 0) return KERDOCK_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
+  if (!p.preprocessed) return KERDOCK_ERR_NOT_PREPROCESSED;
+  if (q == 0) return KERDOCK_OK;
+  if (X_dev == nullptr || out_idx == nullptr || out_val == nullptr || out_count == nullptr)
+    return KERDOCK_ERR_INVALID_ARG;
+  if (ldx < p.n || flags < 0 || flags > KERDOCK_FLAG_FULL_OUTPUT) return KERDOCK_ERR_INVALID_ARG;
+  if (!(flags & KERDOCK_FLAG_FULL_OUTPUT) && !(eps > 0.0f)) return KERDOCK_ERR_INVALID_ARG;
+  if (q > (int64_t(1) << 31) / (p.S > 0 ? p.S : 1)) return KERDOCK_ERR_UNSUPPORTED;
+  return kd::launch_apply_noalloc(p, X_dev, q, ldx, eps, seed, flags, out_idx, out_val,
+                                  out_count);
+}
+
 int kerdock_sync(kerdock_plan_t plan) {
   if (plan == nullptr) return KERDOCK_ERR_INVALID_ARG;
   Plan& p = plan->p;

@@ -28,6 +28,8 @@
 //                 the gather warps already stream the next one.
 // All hand-offs are mbarrier phases; every wait is bounded and a timeout sets
 // the plan's status word and ends the CTA.
+#include <mutex>
+
 #include "kerdock_internal.cuh"
 
 namespace kd {
@@ -755,6 +757,165 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   if (gpt <= 2) return xreg ? launch_typed<float, 2, true>(p, L, a, ws)
                             : launch_typed<float, 2, false>(p, L, a, ws);
   return launch_typed<float, 4, false>(p, L, a, ws);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply.  Some callers cannot allocate device memory: code
+// that runs while a stream is being captured into a CUDA graph, real-time or
+// embedded hosts that fix their device-memory budget at start-up, or plugin
+// hosts that own the allocator.  For them kerdock_apply_noalloc runs the same
+// query kernel with its batch-mean scratch (normally the caller's workspace
+// or shared memory) in this file-scope device array instead.  Every GPU that
+// loads the library keeps the array until the process exits.  All calls share
+// it, so calls that overlap on the GPU race with each other; nothing in it
+// needs clearing, because each batch mean is written before it is read.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, never a device pointer).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  KD_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return KERDOCK_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    KD_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    if (ptr == nullptr) return KERDOCK_ERR_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KERDOCK_OK;
+}
+
+// The kernel's shared-memory layout with the batch means always in global
+// scratch (so the whole shared-memory budget goes to the row ring).
+Layout make_layout_noalloc(const Plan& p) {
+  Layout L{};
+  L.row_bytes = uint32_t(p.ldr * p.elem_bytes());
+  L.xpad = p.d > 32 ? p.d : 32;
+  const size_t spad = align_up(size_t(p.S), 4);
+  L.means_in_smem = false;
+  const size_t fixed = size_t(kXBufs) * size_t(L.xpad) * 4 + size_t(p.ldr) * 4 + 2 * spad * 4 + 1024;
+  const size_t per_slot = size_t(L.row_bytes) + 4;
+  size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
+  const size_t cap = kRingCap + size_t(kMaxSlots) * 4;
+  if (avail > cap) avail = cap;
+  int ns = int(avail / per_slot);
+  if (ns > kMaxSlots) ns = kMaxSlots;
+  L.crows = ns >= 32 ? 4 : ns >= 8 ? 2 : 1;
+  L.nchunk = ns / L.crows;
+  ns = L.nchunk * L.crows;
+  int g = 1;
+  while (2 * g * L.crows <= 32 && 4 * g <= L.nchunk) g *= 2;
+  L.pgroup = g;
+  size_t off = align_up(size_t(ns) * L.row_bytes, 128);
+  L.off_coef = off;
+  off = align_up(off + size_t(ns) * 4, 16);
+  L.off_x = off;
+  off = align_up(off + size_t(kXBufs) * size_t(L.xpad) * 4, 16);
+  L.off_means = off;
+  L.off_mu = off;
+  off = align_up(off + size_t(p.ldr) * 4, 16);
+  L.off_sel = off;
+  off = align_up(off + spad * 4, 16);
+  L.off_vals = off;
+  off = align_up(off + spad * 4, 16);
+  L.total = off;
+  return L;
+}
+
+template <typename RT, int GPT, bool XREG>
+int launch_noalloc_typed(const Layout& L, QueryArgs& a, int64_t grid, cudaStream_t stream) {
+  auto kern = query_kernel<RT, GPT, XREG>;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(L.total)));
+  kern<<<unsigned(grid), kThreads, L.total, stream>>>(a);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+}  // namespace
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+int launch_apply_noalloc(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps,
+                         uint64_t seed, int flags, int32_t* out_idx, float* out_val,
+                         int32_t* out_count) {
+  const Layout L = make_layout_noalloc(p);
+  if (L.nchunk < kMinChunks || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
+  int64_t grid = p.num_sms;
+  if (grid > q) grid = q;
+  const size_t need = size_t(grid) * kMBufs * size_t(p.K) * size_t(p.ldr) * sizeof(float);
+  if (need > kNoAllocScratchBytes) return KERDOCK_ERR_CAPACITY;  // beyond the fixed scratch
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc != KERDOCK_OK) return rc;
+  QueryArgs a{};
+  a.R = p.repr;
+  a.tsigns = p.tsigns();
+  a.tsign_stride = p.tsign_words;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.X = X;
+  a.ldx = ldx;
+  a.Q = q;
+  a.m = p.m;
+  a.n = p.n;
+  a.d = p.d;
+  a.L = p.L;
+  a.ldr = p.ldr;
+  a.N = p.N;
+  a.xpad = L.xpad;
+  a.k = p.k;
+  a.J = p.J;
+  a.K = p.K;
+  a.S = p.S;
+  a.eps = eps;
+  a.inv_J = 1.0f / float(p.J);
+  a.sqrt_d = float(int64_t(1) << (p.k / 2));
+  a.seed = seed;
+  a.flags = flags;
+  a.a_vec4 =
+      (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
+  a.nchunk = L.nchunk;
+  a.crows = L.crows;
+  a.pgroup = L.pgroup;
+  a.row_bytes = L.row_bytes;
+  a.off_coef = uint32_t(L.off_coef);
+  a.off_x = uint32_t(L.off_x);
+  a.off_means = uint32_t(L.off_means);
+  a.off_mu = uint32_t(L.off_mu);
+  a.off_sel = uint32_t(L.off_sel);
+  a.off_vals = uint32_t(L.off_vals);
+  a.means_gmem = static_cast<float*>(scratch);
+  a.out_idx = out_idx;
+  a.out_val = out_val;
+  a.out_count = out_count;
+  a.status = p.status();
+  const int64_t granule = 16 / int64_t(p.elem_bytes());
+  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
+  const bool xreg = p.n <= 1024;
+  if (p.dtype == KERDOCK_BF16) {
+    if (gpt <= 1) return xreg ? launch_noalloc_typed<__nv_bfloat16, 1, true>(L, a, grid, p.stream)
+                              : launch_noalloc_typed<__nv_bfloat16, 1, false>(L, a, grid, p.stream);
+    if (gpt <= 2) return xreg ? launch_noalloc_typed<__nv_bfloat16, 2, true>(L, a, grid, p.stream)
+                              : launch_noalloc_typed<__nv_bfloat16, 2, false>(L, a, grid, p.stream);
+    return launch_noalloc_typed<__nv_bfloat16, 4, false>(L, a, grid, p.stream);
+  }
+  if (gpt <= 1) return xreg ? launch_noalloc_typed<float, 1, true>(L, a, grid, p.stream)
+                            : launch_noalloc_typed<float, 1, false>(L, a, grid, p.stream);
+  if (gpt <= 2) return xreg ? launch_noalloc_typed<float, 2, true>(L, a, grid, p.stream)
+                            : launch_noalloc_typed<float, 2, false>(L, a, grid, p.stream);
+  return launch_noalloc_typed<float, 4, false>(L, a, grid, p.stream);
 }
 
 }  // namespace kd

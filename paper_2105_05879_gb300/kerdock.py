@@ -31,7 +31,7 @@ EXPORTED = [
     "kerdock_plan_create", "kerdock_plan_info", "kerdock_plan_bind", "kerdock_set_stream",
     "kerdock_preprocess", "kerdock_apply_workspace_bytes", "kerdock_apply",
     "kerdock_apply_debug", "kerdock_sync", "kerdock_debug_signs", "kerdock_plan_destroy",
-    "kerdock_strerror", "kerdock_version",
+    "kerdock_strerror", "kerdock_version", "kerdock_apply_noalloc",
 ]
 
 
@@ -81,6 +81,8 @@ def load_library(path=None):
         "kerdock_apply_debug": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float,
                                                ctypes.c_uint64, c_i32, c_vp, c_vp, c_vp, c_vp,
                                                c_sz, c_vp, c_vp, c_vp]),
+        "kerdock_apply_noalloc": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float,
+                                                 ctypes.c_uint64, c_i32, c_vp, c_vp, c_vp]),
         "kerdock_sync": (ctypes.c_int, [P]),
         "kerdock_debug_signs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32), c_sz]),
         "kerdock_plan_destroy": (ctypes.c_int, [P]),
@@ -142,6 +144,13 @@ def kerdock_apply_debug(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr,
     _check(load_library().kerdock_apply_debug(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
                                               val_ptr, cnt_ptr, ws_ptr, ws_bytes, mu_ptr,
                                               ells_ptr, coef_ptr), "kerdock_apply_debug")
+
+
+def kerdock_apply_noalloc(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr, cnt_ptr):
+    """kerdock_apply without a workspace: for callers that cannot allocate device
+    memory; the scratch is a fixed array inside the library (see kerdock.h)."""
+    _check(load_library().kerdock_apply_noalloc(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
+                                                val_ptr, cnt_ptr), "kerdock_apply_noalloc")
 
 
 def kerdock_sync(plan):
