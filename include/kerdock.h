@@ -179,6 +179,70 @@ int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, in
                           float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
                           float* out_val, int32_t* out_count);
 
+/* ------------------------------------------------------------------------
+ * Batches: queries over any mix of plans (sizes, representation types,
+ * sparsities) answered by one persistent launch, optionally replayed from a
+ * captured CUDA graph.  (Serving form of Algorithm 1's streaming step.)
+ * ------------------------------------------------------------------------ */
+#define KERDOCK_BATCH_GRAPH 1 /* capture the launch into a CUDA graph (needs a non-NULL stream) */
+
+typedef struct {
+  kerdock_plan_t plan;  /* a bound, preprocessed plan on the current device */
+  const float* x;       /* device pointer to this query's n floats */
+  int32_t J, K;         /* batch size and number of batches of the median of means (K <= 16) */
+  int32_t S;            /* candidate-set size, 1 <= S <= m (Sec. 4 uses S = 10 s) */
+  int32_t flags;        /* KERDOCK_FLAG_FULL_OUTPUT or 0 */
+  float eps;            /* threshold (> 0 unless full output) */
+  int32_t reserved;
+  uint64_t seed;        /* sampling seed */
+  int64_t index;        /* the q of the sampling convention (sample j uses counter index*J*K + j) */
+  int32_t* out_idx;     /* device, S int32: kept indices, ascending */
+  float* out_val;       /* device, S float32: their values */
+  int32_t* out_count;   /* device, one int32: how many were kept */
+} kerdock_query_t;
+
+typedef struct kerdock_batch_s* kerdock_batch_t;
+
+/* Device workspace bytes kerdock_batch_create needs for this list (0 on
+ * invalid input). */
+size_t kerdock_batch_workspace_bytes(const kerdock_query_t* queries, int64_t count);
+
+/* Validate the queries, deal them to the CTAs by estimated cost (longest
+ * first onto the least-loaded CTA), upload descriptors and schedule into
+ * ws_dev (256-byte aligned, caller-owned, kept alive with the batch), and --
+ * with KERDOCK_BATCH_GRAPH -- capture the launch into a CUDA graph.
+ * Synchronises the stream once (the upload).  Every plan must stay bound and
+ * preprocessed while the batch exists; x and the outputs are read/written at
+ * every launch. */
+int kerdock_batch_create(kerdock_batch_t* batch, const kerdock_query_t* queries, int64_t count,
+                         void* ws_dev, size_t ws_bytes, void* stream, int32_t options);
+
+/* Run the batch (graph replay or plain launch), asynchronously. */
+int kerdock_batch_launch(kerdock_batch_t batch);
+
+/* Set the query kernel's ring geometry for this batch: ring_kb KiB of shared
+ * memory for representation rows and crows rows per ring chunk (1, 2 or 4;
+ * 0 = default for either); re-captures the graph. */
+int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t crows);
+
+/* Autotuner: time reps launches of every candidate geometry (ring 64/96/128/
+ * 160 KiB x 1/2/4 rows per chunk), keep the fastest and report it. */
+int kerdock_batch_tune(kerdock_batch_t batch, int32_t reps, int32_t* ring_kb, int32_t* crows,
+                       float* best_ms);
+
+/* Synchronise the batch's stream and report a recorded device error. */
+int kerdock_batch_sync(kerdock_batch_t batch);
+
+int kerdock_batch_destroy(kerdock_batch_t batch);
+
+/* Ring geometry of a plan's kerdock_apply (0 = default); and the autotuner
+ * that times kerdock_apply with each candidate and keeps the fastest. */
+int kerdock_plan_set_tuning(kerdock_plan_t plan, int32_t ring_kb, int32_t crows);
+int kerdock_plan_tune(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx, float eps,
+                      uint64_t seed, int32_t* out_idx, float* out_val, int32_t* out_count,
+                      void* ws_dev, size_t ws_bytes, int32_t reps, int32_t* ring_kb,
+                      int32_t* crows, float* best_ms);
+
 /* Synchronise the plan's stream and report the first error any kernel of
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);

@@ -19,6 +19,12 @@ constexpr size_t kStatusBytes = 256;  // status word area at the start of the ta
 // Device status word codes (first error wins).
 enum : uint32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadIndex = 2 };
 
+// Tunable geometry of the query kernel's row ring (0 = library default).
+struct Tuning {
+  int ring_kb = 0;  // KiB of shared memory for the row ring
+  int crows = 0;    // rows per ring chunk (1, 2 or 4)
+};
+
 struct Plan {
   int64_t m = 0, n = 0, d = 0, B = 0, L = 0, ldr = 0;
   int k = 0, dtype = KERDOCK_F32, J = 0, K = 0, S = 0;
@@ -38,6 +44,7 @@ struct Plan {
   // device properties
   int device = -1;
   int num_sms = 0;
+  Tuning tuning;
 
   uint32_t* status() const { return reinterpret_cast<uint32_t*>(table); }
   uint32_t* signs() const {
@@ -48,6 +55,60 @@ struct Plan {
   uint32_t* tsigns() const { return signs() + (d / 2) * sign_words; }
   size_t elem_bytes() const { return dtype == KERDOCK_BF16 ? 2 : 4; }
 };
+
+// Layout of one launch (shared by all its queries): ring geometry and the
+// byte offsets of the dynamic shared-memory regions.
+struct LaunchCfg {
+  int nchunk;            // ring chunks; a chunk holds crows consecutive samples of one query
+  int crows;             // rows per chunk (1, 2 or 4)
+  int pgroup;            // chunks the producer fills per warp instruction (pgroup * crows <= 32)
+  uint32_t slot_bytes;   // ring slot stride: the largest row of the launch
+  int64_t xpad;          // floats per x buffer
+  int64_t mstride;       // floats per batch-means buffer (K * ldr of the largest query)
+  uint32_t off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
+  float* means_gmem;     // per-CTA batch means in global memory when non-null
+  uint32_t* status;
+};
+
+// Everything one query needs, with pointers already offset to that query.
+struct QueryDesc {
+  const void* R;            // representation of the query's plan
+  const uint32_t* tsigns;   // lane-transposed sign table of the plan
+  const float* A;           // rows of A for the refinement
+  const float* x;           // the query vector (n floats)
+  int32_t* out_idx;         // S kept indices
+  float* out_val;           // S kept values
+  int32_t* out_count;       // one count
+  float* mu_out;            // m floats (debug) or null
+  int64_t* ells_out;        // N indices (debug) or null
+  float* coef_out;          // N coefficients (debug) or null
+  int64_t tstride, lda, m, n, d, L, ldr, N, ctr_base;
+  uint64_t seed;
+  int32_t k, J, K, S, dtype, flags, a_vec4;
+  uint32_t row_bytes;
+  float eps, inv_J, sqrt_d;
+};
+
+// Largest sizes over the queries of one launch.
+struct Dims {
+  uint32_t row_bytes = 0;  // bytes of one representation row
+  int64_t xpad = 32;       // x buffer floats: max(d, 32)
+  int64_t ldr = 0;         // representation row stride (elements)
+  int64_t S = 0;           // candidate-set size
+  int64_t KL = 0;          // K * ldr
+};
+
+size_t align_up(size_t v, size_t al);
+void dims_add(Dims& dm, const Plan& p, int64_t K, int64_t S);
+bool means_fit_smem(const Dims& dm);
+bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c);
+QueryDesc plan_desc(const Plan& p);
+void set_query_params(QueryDesc& d, int64_t J, int64_t K, int64_t S, float eps, uint64_t seed,
+                      int flags);
+int prepare_batch_kernel(const LaunchCfg& cfg);  // kernel attributes; call outside capture
+int launch_batch(const LaunchCfg& cfg, const QueryDesc* descs, const int32_t* order,
+                 const int64_t* cta_start, int grid, cudaStream_t stream);
+constexpr int kQueryThreads = 512;
 
 // Launchers (return KERDOCK_OK or a negative error code).
 int launch_signs(const Plan& p);
@@ -148,6 +209,10 @@ __device__ __forceinline__ float flip_sign(float v, uint32_t bit) {
 }
 
 }  // namespace kd
+
+struct kerdock_plan_s {
+  kd::Plan p;
+};
 
 #define KD_CUDA_TRY(expr)                           \
   do {                                              \

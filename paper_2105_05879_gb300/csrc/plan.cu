@@ -132,10 +132,6 @@ int launch_signs(const Plan& p) {
 
 using kd::Plan;
 
-struct kerdock_plan_s {
-  Plan p;
-};
-
 extern "C" {
 
 int kerdock_version(void) { return 100; }

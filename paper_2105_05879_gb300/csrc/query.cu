@@ -55,36 +55,6 @@ constexpr size_t kSmemBudget = 227 * 1024 - 4096;  // dynamic bytes (static ~3 K
 constexpr size_t kRingCap = 160 * 1024;
 constexpr size_t kMeansSmemMax = 64 * 1024;
 
-struct QueryArgs {
-  const void* R;
-  const uint32_t* tsigns;  // lane-transposed sign table
-  int64_t tsign_stride;    // words per basis in it
-  const float* A;
-  int64_t lda;
-  const float* X;
-  int64_t ldx;
-  int64_t Q, m, n, d, L, ldr, N, xpad;
-  int k, J, K, S;
-  float eps, inv_J, sqrt_d;
-  uint64_t seed;
-  int flags;
-  int a_vec4;  // rows of A are 16-byte aligned and n % 4 == 0
-  int nchunk;   // ring chunks; each holds chunk_rows consecutive samples of one query
-  int crows;    // rows per chunk (1, 2 or 4)
-  int pgroup;   // chunks the producer fills per warp instruction (pgroup * crows <= 32)
-  uint32_t row_bytes;
-  // dynamic shared-memory layout (byte offsets)
-  uint32_t off_coef, off_x, off_means, off_mu, off_sel, off_vals;
-  float* means_gmem;  // non-null when the batch means live in the workspace
-  int32_t* out_idx;
-  float* out_val;
-  int32_t* out_count;
-  float* mu_out;
-  int64_t* ells_out;
-  float* coef_out;
-  uint32_t* status;
-};
-
 template <typename RT>
 struct Granule;
 template <>
@@ -226,33 +196,75 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, Share
   }
 }
 
-template <typename RT, int GPT, bool XREG>
-__global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
-  using G = Granule<RT>;
-  constexpr int GR = G::kElems;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ Shared sh;
+// Single-plan launch: the plan-wide descriptor plus the query batch shape.
+struct QueryArgs {
+  LaunchCfg cfg;
+  QueryDesc base;  // x, outputs and debug pointers point at query 0
+  int64_t Q, ldx;
+};
 
-  unsigned char* ring = smem;
-  float* coef_s = reinterpret_cast<float*>(smem + a.off_coef);
-  float* xbuf = reinterpret_cast<float*>(smem + a.off_x);
-  float* means_base = a.means_gmem != nullptr
-                          ? a.means_gmem + int64_t(blockIdx.x) * kMBufs * a.K * a.ldr
-                          : reinterpret_cast<float*>(smem + a.off_means);
-  float* mus = reinterpret_cast<float*>(smem + a.off_mu);
-  int32_t* sel = reinterpret_cast<int32_t*>(smem + a.off_sel);
-  float* vals = reinterpret_cast<float*>(smem + a.off_vals);
+// Batch launch: descriptors, their order and each CTA's range in it.
+struct BatchArgs {
+  LaunchCfg cfg;
+  const QueryDesc* descs;
+  const int32_t* order;
+  const int64_t* cta_start;  // gridDim.x + 1 entries
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const RT* R = static_cast<const RT*>(a.R);
-  const int64_t half = a.d / 2;
-  const uint32_t nchunk = uint32_t(a.nchunk);
-  const int CR = a.crows;
-  const int64_t qchunks = (a.N + CR - 1) / CR;  // chunks per query
+struct SingleSeq {
+  const QueryArgs& a;
+  __device__ int64_t size() const {
+    return blockIdx.x < a.Q ? (a.Q - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  }
+  __device__ QueryDesc get(int64_t i) const {
+    const int64_t q = blockIdx.x + i * gridDim.x;
+    QueryDesc d = a.base;
+    d.x = a.base.x + q * a.ldx;
+    d.out_idx = a.base.out_idx + q * a.base.S;
+    d.out_val = a.base.out_val + q * a.base.S;
+    d.out_count = a.base.out_count + q;
+    if (d.mu_out) d.mu_out += q * a.base.m;
+    if (d.ells_out) d.ells_out += q * a.base.N;
+    if (d.coef_out) d.coef_out += q * a.base.N;
+    d.ctr_base = q * a.base.N;
+    return d;
+  }
+};
 
-  if (tid == 0) {
-    for (int s = 0; s < a.nchunk; ++s) {
-      mbar_init(&sh.row_full[s], uint32_t(CR));
+struct BatchSeq {
+  const BatchArgs& a;
+  __device__ int64_t size() const { return a.cta_start[blockIdx.x + 1] - a.cta_start[blockIdx.x]; }
+  __device__ QueryDesc get(int64_t i) const { return a.descs[a.order[a.cta_start[blockIdx.x] + i]]; }
+};
+
+// Shared-memory regions of a launch.
+struct Regions {
+  unsigned char* ring;
+  float* coef_s;
+  float* xbuf;
+  float* means_base;
+  float* mus;
+  int32_t* sel;
+  float* vals;
+};
+
+__device__ __forceinline__ Regions regions(unsigned char* smem, const LaunchCfg& c) {
+  Regions r;
+  r.ring = smem;
+  r.coef_s = reinterpret_cast<float*>(smem + c.off_coef);
+  r.xbuf = reinterpret_cast<float*>(smem + c.off_x);
+  r.means_base = c.means_gmem != nullptr ? c.means_gmem + int64_t(blockIdx.x) * kMBufs * c.mstride
+                                         : reinterpret_cast<float*>(smem + c.off_means);
+  r.mus = reinterpret_cast<float*>(smem + c.off_mu);
+  r.sel = reinterpret_cast<int32_t*>(smem + c.off_sel);
+  r.vals = reinterpret_cast<float*>(smem + c.off_vals);
+  return r;
+}
+
+__device__ __forceinline__ void init_barriers(Shared& sh, const LaunchCfg& c) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < c.nchunk; ++s) {
+      mbar_init(&sh.row_full[s], uint32_t(c.crows));
       mbar_init(&sh.coef_full[s], 1);
       mbar_init(&sh.slot_empty[s], kGatherWarps);
     }
@@ -268,496 +280,631 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
     fence_mbar_init();
   }
   __syncthreads();
+}
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
-    uint64_t filled = 0;             // chunks filled so far
-    const int ci = lane / CR, r = lane % CR;
-    int qs = 0;
-    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
-      const int xb = qs % kXBufs;
-      if (qs >= kXBufs &&
-          !wait_phase(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, a.status))
-        return;
-      float* xq = xbuf + xb * a.xpad;
-      for (int64_t p = lane; p < a.xpad; p += 32) xq[p] = p < a.n ? a.X[q * a.ldx + p] : 0.f;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.x_full[xb]);
-      for (int64_t c0 = 0; c0 < qchunks; c0 += a.pgroup) {
-        const int cnt = int(qchunks - c0 < a.pgroup ? qchunks - c0 : a.pgroup);
-        bool ok = true;
-        if (ci < cnt) {
-          uint32_t cs = cslot + uint32_t(ci), ph = cphase;
-          if (cs >= nchunk) {
-            cs -= nchunk;
-            ph ^= 1u;
-          }
-          if (filled + uint64_t(ci) >= nchunk)
-            ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, a.status);
-          const int64_t j = (c0 + ci) * CR + r;
-          if (ok && j < a.N) {
-            const uint64_t ell =
-                sample_index(a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j), uint64_t(a.L));
-            if (a.ells_out) a.ells_out[q * a.N + j] = int64_t(ell);
-            mbar_arrive_expect_tx(&sh.row_full[cs], a.row_bytes);
-            bulk_g2s(ring + (size_t(cs) * CR + r) * a.row_bytes, R + int64_t(ell) * a.ldr,
-                     a.row_bytes, &sh.row_full[cs]);
-          } else if (ok) {
-            mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
-          }
-        }
-        if (__any_sync(0xffffffffu, !ok)) return;
-        filled += uint64_t(cnt);
-        cslot += uint32_t(cnt);
-        if (cslot >= nchunk) {
-          cslot -= nchunk;
-          cphase ^= 1u;
-        }
-      }
-    }
-  } else if (warp < kFirstGatherWarp) {
-    // ------------------------------------------------------------ coefficients
-    const int cw = warp - kFirstCoefWarp;
-    const int groups = int((a.n + 1023) / 1024);
-    const uint32_t dmask = uint32_t(a.d - 1);
-    uint32_t cs = uint32_t(cw), ph = 0;  // this warp handles chunks cw, cw + 3, ...
-    uint64_t cc = uint64_t(cw);          // global chunk counter of this warp
-    int qs = 0;
-    float xr[32];
-    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
-      const int xb = qs % kXBufs;
-      if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, a.status)) return;
-      const float* xq = xbuf + xb * a.xpad;
-#pragma unroll
-      for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < a.xpad) ? xq[t * 32 + lane] : 0.f;
-      const uint64_t cend = uint64_t(qs + 1) * uint64_t(qchunks);
-      for (; cc < cend; cc += kCoefWarps) {
-        const int64_t j0 = int64_t(cc - uint64_t(qs) * uint64_t(qchunks)) * CR;
-        const int cnt = int(a.N - j0 < CR ? a.N - j0 : CR);
-        // lanes 0..cnt-1 draw the chunk's indices; everyone gets all four
-        uint32_t my_ell = 0;
-        if (lane < cnt)
-          my_ell = uint32_t(sample_index(
-              a.seed, uint64_t(q) * uint64_t(a.N) + uint64_t(j0 + lane), uint64_t(a.L)));
-        uint32_t ell[4];
-#pragma unroll
-        for (int s2 = 0; s2 < 4; ++s2) ell[s2] = __shfl_sync(0xffffffffu, my_ell, s2 < cnt ? s2 : 0);
-        float c[4];
-        kerdock_coefficients4<XREG>(a.tsigns, a.tsign_stride, ell, a.k, dmask, groups, lane, xr,
-                                    xq, c);
-        // the gather warps must be done with this chunk's previous samples
-        if (cc >= nchunk && !wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, a.status)) return;
-        if (lane == 0) {
-#pragma unroll
-          for (int s2 = 0; s2 < 4; ++s2) {
-            if (s2 >= cnt) break;
-            const uint32_t w = ell[s2] & dmask;
-            float cv = c[s2];
-            if (int64_t(ell[s2] >> a.k) == half) cv = w < a.n ? a.sqrt_d * xq[w] : 0.f;
-            coef_s[cs * CR + s2] = cv;
-            if (a.coef_out) a.coef_out[q * a.N + j0 + s2] = cv;
-          }
-          mbar_arrive(&sh.coef_full[cs]);
-        }
-        cs += kCoefWarps;
+// ---------------------------------------------------------------- producer
+template <class Seq>
+__device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
+  const int lane = threadIdx.x & 31;
+  const int CR = cfg.crows;
+  const uint32_t nchunk = uint32_t(cfg.nchunk);
+  uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
+  uint64_t filled = 0;             // chunks filled so far
+  const int ci = lane / CR, r = lane % CR;
+  const int64_t nq = seq.size();
+  for (int64_t qs = 0; qs < nq; ++qs) {
+    const QueryDesc qd = seq.get(qs);
+    const int xb = int(qs % kXBufs);
+    if (qs >= kXBufs &&
+        !wait_phase(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, cfg.status))
+      return;
+    float* xq = rg.xbuf + xb * cfg.xpad;
+    for (int64_t p = lane; p < cfg.xpad; p += 32) xq[p] = p < qd.n ? qd.x[p] : 0.f;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.x_full[xb]);
+    const int64_t qchunks = (qd.N + CR - 1) / CR;
+    const unsigned char* R = static_cast<const unsigned char*>(qd.R);
+    for (int64_t c0 = 0; c0 < qchunks; c0 += cfg.pgroup) {
+      const int cnt = int(qchunks - c0 < cfg.pgroup ? qchunks - c0 : cfg.pgroup);
+      bool ok = true;
+      if (ci < cnt) {
+        uint32_t cs = cslot + uint32_t(ci), ph = cphase;
         if (cs >= nchunk) {
           cs -= nchunk;
           ph ^= 1u;
         }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.x_empty[xb]);
-    }
-  } else if (warp < kFirstFinalWarp) {
-    // ------------------------------------------------------------ gather
-    const int gt = tid - kFirstGatherWarp * 32;
-    uint32_t cs = 0, ph = 0;
-    int qs = 0;
-    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
-      const int mb = qs % kMBufs;
-      float* means = means_base + int64_t(mb) * a.K * a.ldr;
-      float acc[GPT][GR];
-#pragma unroll
-      for (int u = 0; u < GPT; ++u)
-#pragma unroll
-        for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
-      int batch_left = a.J, batch = 0;
-      for (int64_t j0 = 0; j0 < a.N; j0 += CR) {
-        const int cnt = int(a.N - j0 < CR ? a.N - j0 : CR);
-        if (!wait_phase(&sh.row_full[cs], ph, sh, a.status)) return;
-        if (!wait_phase(&sh.coef_full[cs], ph, sh, a.status)) return;
-#pragma unroll
-        for (int s2 = 0; s2 < 4; ++s2) {
-          if (s2 >= cnt) break;
-          const float c = coef_s[cs * CR + s2];
-          const unsigned char* row = ring + (size_t(cs) * CR + s2) * a.row_bytes;
-#pragma unroll
-          for (int u = 0; u < GPT; ++u) {
-            const int gi = gt + u * kGatherThreads;
-            if (gi * GR < a.ldr) {
-              float v[GR];
-              G::load(row + size_t(gi) * 16, v);
-#pragma unroll
-              for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
-            }
-          }
-          if (--batch_left == 0) {
-            if (batch == 0 && qs >= kMBufs &&
-                !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, a.status))
-              return;
-            float* mrow = means + int64_t(batch) * a.ldr;
-#pragma unroll
-            for (int u = 0; u < GPT; ++u) {
-              const int gi = gt + u * kGatherThreads;
-              if (gi * GR < a.ldr) {
-#pragma unroll
-                for (int e = 0; e < GR; ++e) {
-                  mrow[gi * GR + e] = acc[u][e] * a.inv_J;
-                  acc[u][e] = 0.f;
-                }
-              }
-            }
-            batch_left = a.J;
-            ++batch;
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.slot_empty[cs]);
-        if (++cs == nchunk) {
-          cs = 0;
-          ph ^= 1u;
+        if (filled + uint64_t(ci) >= nchunk)
+          ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, cfg.status);
+        const int64_t j = (c0 + ci) * CR + r;
+        if (ok && j < qd.N) {
+          const uint64_t ell =
+              sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j), uint64_t(qd.L));
+          if (qd.ells_out) qd.ells_out[j] = int64_t(ell);
+          mbar_arrive_expect_tx(&sh.row_full[cs], qd.row_bytes);
+          bulk_g2s(rg.ring + (size_t(cs) * CR + r) * cfg.slot_bytes,
+                   R + int64_t(ell) * qd.row_bytes, qd.row_bytes, &sh.row_full[cs]);
+        } else if (ok) {
+          mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
         }
       }
-      if (a.means_gmem != nullptr) __threadfence_block();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.means_full[mb]);
-    }
-  } else {
-    // ------------------------------------------------------------ finalizer
-    const int ft = tid - kFirstFinalWarp * 32;
-    const int fw = warp - kFirstFinalWarp;
-    const int m = int(a.m);
-    int qs = 0;
-    for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x, ++qs) {
-      const int mb = qs % kMBufs, xb = qs % kXBufs;
-      if (!wait_phase(&sh.means_full[mb], uint32_t(qs / kMBufs) & 1u, sh, a.status)) return;
-      if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, a.status)) return;
-      const float* means = means_base + int64_t(mb) * a.K * a.ldr;
-      const float* xq = xbuf + xb * a.xpad;
-      // a6: median over the K batch means.
-      for (int col = ft; col < m; col += kFinalThreads) {
-        float med;
-        if (a.K == 1) {
-          med = means[col];
-        } else if (a.K == 2) {
-          med = 0.5f * (means[col] + means[a.ldr + col]);
-        } else {
-          float v[kMaxK];
-#pragma unroll
-          for (int kk = 0; kk < kMaxK; ++kk) v[kk] = kk < a.K ? means[kk * a.ldr + col] : 0.f;
-          const int r_lo = (a.K - 1) / 2, r_hi = a.K / 2;
-          float lo = 0.f, hi = 0.f;
-#pragma unroll
-          for (int i = 0; i < kMaxK; ++i) {
-            if (i >= a.K) break;
-            int rank = 0;
-#pragma unroll
-            for (int j = 0; j < kMaxK; ++j)
-              if (j < a.K && (v[j] < v[i] || (v[j] == v[i] && j < i))) ++rank;
-            if (rank == r_lo) lo = v[i];
-            if (rank == r_hi) hi = v[i];
-          }
-          med = (a.K & 1) ? lo : 0.5f * (lo + hi);
-        }
-        mus[col] = med;
-        if (a.mu_out) a.mu_out[q * a.m + col] = med;
+      if (__any_sync(0xffffffffu, !ok)) return;
+      filled += uint64_t(cnt);
+      cslot += uint32_t(cnt);
+      if (cslot >= nchunk) {
+        cslot -= nchunk;
+        cphase ^= 1u;
       }
-      named_barrier_sync(kFinalBarrier, kFinalThreads);
-      if (ft == 0) mbar_arrive(&sh.means_empty[mb]);  // means are consumed
-
-      // a7: top-S by radix select on |mu| (4 digits of 8 bits, high first).
-      uint32_t prefix = 0, mask = 0, remaining = uint32_t(a.S);
-      for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        sh.hist[ft] = 0;
-        sh.hist[ft + kFinalThreads] = 0;
-        named_barrier_sync(kFinalBarrier, kFinalThreads);
-        for (int i = ft; i < m; i += kFinalThreads) {
-          const uint32_t key = abs_key(mus[i]);
-          if ((key & mask) == prefix) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
-        }
-        named_barrier_sync(kFinalBarrier, kFinalThreads);
-        if (fw == 0) {
-          const int base = (31 - lane) * 8;  // lane 0 holds the highest digits
-          uint32_t sum = 0;
-#pragma unroll
-          for (int j2 = 0; j2 < 8; ++j2) sum += sh.hist[base + j2];
-          uint32_t incl = sum;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const uint32_t excl = incl - sum;
-          const uint32_t hit = __ballot_sync(0xffffffffu, excl < remaining && remaining <= incl);
-          if (lane == __ffs(hit) - 1) {
-            uint32_t cum = excl;
-            for (int j2 = 7; j2 >= 0; --j2) {
-              const uint32_t h = sh.hist[base + j2];
-              if (cum + h >= remaining) {
-                sh.digit = uint32_t(base + j2);
-                sh.remaining = remaining - cum;
-                break;
-              }
-              cum += h;
-            }
-          }
-        }
-        named_barrier_sync(kFinalBarrier, kFinalThreads);
-        prefix |= sh.digit << shift;
-        mask |= 255u << shift;
-        remaining = sh.remaining;
-        named_barrier_sync(kFinalBarrier, kFinalThreads);
-      }
-      const uint32_t T = prefix;  // the S-th largest key; take `remaining` keys equal to T
-      {
-        const int seg = (m + kFinalThreads - 1) / kFinalThreads;
-        const int lo = ft * seg, hi = lo + seg < m ? lo + seg : m;
-        int eq = 0;
-        for (int i = lo; i < hi; ++i) eq += abs_key(mus[i]) == T;
-        int tot;
-        int eq_rank = final_exclusive_scan(eq, sh.scan, &tot);
-        const int eq_rank0 = eq_rank;
-        int take = 0;
-        for (int i = lo; i < hi; ++i) {
-          const uint32_t key = abs_key(mus[i]);
-          if (key > T) {
-            ++take;
-          } else if (key == T) {
-            take += uint32_t(eq_rank) < remaining;
-            ++eq_rank;
-          }
-        }
-        int pos = final_exclusive_scan(take, sh.scan, &tot);
-        eq_rank = eq_rank0;
-        for (int i = lo; i < hi; ++i) {
-          const uint32_t key = abs_key(mus[i]);
-          bool t2 = false;
-          if (key > T) {
-            t2 = true;
-          } else if (key == T) {
-            t2 = uint32_t(eq_rank) < remaining;
-            ++eq_rank;
-          }
-          if (t2) sel[pos++] = i;
-        }
-      }
-      named_barrier_sync(kFinalBarrier, kFinalThreads);
-
-      // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
-      for (int r0 = fw * 4; r0 < a.S; r0 += kFinalWarps * 4) {
-        float racc[4] = {0.f, 0.f, 0.f, 0.f};
-        const float* arow[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          arow[u] = a.A + int64_t(sel[r0 + u < a.S ? r0 + u : r0]) * a.lda;
-        if (a.a_vec4) {
-          const float4* xs4 = reinterpret_cast<const float4*>(xq);
-          const int n4 = int(a.n >> 2);
-#pragma unroll 2
-          for (int p4 = lane; p4 < n4; p4 += 32) {
-            const float4 xv = xs4[p4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
-              racc[u] = fmaf(av.x, xv.x, racc[u]);
-              racc[u] = fmaf(av.y, xv.y, racc[u]);
-              racc[u] = fmaf(av.z, xv.z, racc[u]);
-              racc[u] = fmaf(av.w, xv.w, racc[u]);
-            }
-          }
-        } else {
-#pragma unroll 4
-          for (int64_t p = lane; p < a.n; p += 32) {
-            const float xv = xq[p];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float v = warp_sum(racc[u]);
-          if (lane == 0 && r0 + u < a.S) vals[r0 + u] = v;
-        }
-      }
-      named_barrier_sync(kFinalBarrier, kFinalThreads);
-      {
-        const int seg = (a.S + kFinalThreads - 1) / kFinalThreads;
-        const int lo = ft * seg, hi = lo + seg < a.S ? lo + seg : a.S;
-        const bool full = a.flags & KERDOCK_FLAG_FULL_OUTPUT;
-        int keep = 0;
-        for (int r = lo; r < hi; ++r) keep += full || fabsf(vals[r]) >= a.eps;
-        int tot;
-        int pos = final_exclusive_scan(keep, sh.scan, &tot);
-        const int64_t obase = q * a.S;
-        for (int r = lo; r < hi; ++r) {
-          if (full || fabsf(vals[r]) >= a.eps) {
-            a.out_idx[obase + pos] = sel[r];
-            a.out_val[obase + pos] = vals[r];
-            ++pos;
-          }
-        }
-        if (ft == 0) a.out_count[q] = tot;
-      }
-      named_barrier_sync(kFinalBarrier, kFinalThreads);
-      if (ft == 0) mbar_arrive(&sh.x_empty[xb]);  // x of this query no longer needed
     }
   }
 }
 
-size_t align_up(size_t v, size_t al) { return (v + al - 1) / al * al; }
-
-struct Layout {
-  int nchunk, crows, pgroup;
-  uint32_t row_bytes;
-  size_t off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
-  bool means_in_smem;
-  int64_t xpad;
+// ---------------------------------------------------------------- coefficients
+struct CoefState {
+  uint32_t cs, ph;  // ring chunk and phase of this warp's next chunk
+  uint64_t cc;      // global chunk counter of this warp's next chunk
+  uint64_t cbase;   // global chunk counter of the current query's first chunk
 };
 
-Layout make_layout(const Plan& p) {
-  Layout L{};
-  L.row_bytes = uint32_t(p.ldr * p.elem_bytes());
-  L.xpad = p.d > 32 ? p.d : 32;
-  const size_t spad = align_up(size_t(p.S), 4);
-  const size_t means_bytes = size_t(kMBufs) * size_t(p.K) * size_t(p.ldr) * 4;
-  L.means_in_smem = means_bytes <= kMeansSmemMax;
-  // fixed (non-ring) parts, with slack for alignment
-  const size_t fixed = size_t(kXBufs) * size_t(L.xpad) * 4 +
-                       (L.means_in_smem ? means_bytes : 0) + size_t(p.ldr) * 4 +
-                       2 * spad * 4 + 1024;
-  const size_t per_slot = size_t(L.row_bytes) + 4;
-  size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
-  const size_t cap = kRingCap + size_t(kMaxSlots) * 4;
-  if (avail > cap) avail = cap;
-  int ns = int(avail / per_slot);
-  if (ns > kMaxSlots) ns = kMaxSlots;
-  // rows per chunk: four when the ring still holds at least 8 chunks
-  L.crows = ns >= 32 ? 4 : ns >= 8 ? 2 : 1;
-  L.nchunk = ns / L.crows;
-  ns = L.nchunk * L.crows;
-  int g = 1;  // chunks per producer step: g * crows <= 32 lanes, g <= nchunk / 2
-  while (2 * g * L.crows <= 32 && 4 * g <= L.nchunk) g *= 2;
-  L.pgroup = g;
-  size_t off = align_up(size_t(ns) * L.row_bytes, 128);
-  L.off_coef = off;
-  off = align_up(off + size_t(ns) * 4, 16);
-  L.off_x = off;
-  off = align_up(off + size_t(kXBufs) * size_t(L.xpad) * 4, 16);
-  L.off_means = off;
-  if (L.means_in_smem) off = align_up(off + means_bytes, 16);
-  L.off_mu = off;
-  off = align_up(off + size_t(p.ldr) * 4, 16);
-  L.off_sel = off;
-  off = align_up(off + spad * 4, 16);
-  L.off_vals = off;
-  off = align_up(off + spad * 4, 16);
-  L.total = off;
-  return L;
+template <bool XREG>
+__device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const LaunchCfg& cfg,
+                           const Regions& rg, Shared& sh, const float* xq) {
+  const int lane = threadIdx.x & 31;
+  const int CR = cfg.crows;
+  const uint32_t nchunk = uint32_t(cfg.nchunk);
+  const int groups = int((qd.n + 1023) / 1024);
+  const uint32_t dmask = uint32_t(qd.d - 1);
+  const int64_t half = qd.d / 2;
+  float xr[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < cfg.xpad) ? xq[t * 32 + lane] : 0.f;
+  const uint64_t cend = st.cbase + uint64_t((qd.N + CR - 1) / CR);
+  for (; st.cc < cend; st.cc += kCoefWarps) {
+    const int64_t j0 = int64_t(st.cc - st.cbase) * CR;
+    const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
+    // lanes 0..cnt-1 draw the chunk's indices; every lane gets all four
+    uint32_t my_ell = 0;
+    if (lane < cnt)
+      my_ell = uint32_t(
+          sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j0 + lane), uint64_t(qd.L)));
+    uint32_t ell[4];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) ell[s2] = __shfl_sync(0xffffffffu, my_ell, s2 < cnt ? s2 : 0);
+    float c[4];
+    kerdock_coefficients4<XREG>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
+    // the gather warps must be done with this chunk's previous samples
+    if (st.cc >= nchunk && !wait_phase(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg.status))
+      return false;
+    if (lane == 0) {
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2) {
+        if (s2 >= cnt) break;
+        const uint32_t w = ell[s2] & dmask;
+        float cv = c[s2];
+        if (int64_t(ell[s2] >> qd.k) == half) cv = w < qd.n ? qd.sqrt_d * xq[w] : 0.f;
+        rg.coef_s[st.cs * CR + s2] = cv;
+        if (qd.coef_out) qd.coef_out[j0 + s2] = cv;
+      }
+      mbar_arrive(&sh.coef_full[st.cs]);
+    }
+    st.cs += kCoefWarps;
+    if (st.cs >= nchunk) {
+      st.cs -= nchunk;
+      st.ph ^= 1u;
+    }
+  }
+  st.cbase = cend;
+  return true;
 }
 
+// XMODE: 0 = x in registers (n <= 1024), 1 = x in shared memory, 2 = per query.
+template <class Seq, int XMODE>
+__device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
+  const int lane = threadIdx.x & 31;
+  const int cw = (threadIdx.x >> 5) - kFirstCoefWarp;
+  CoefState st{uint32_t(cw), 0u, uint64_t(cw), 0};  // nchunk >= kMinChunks > kCoefWarps
+  const int64_t nq = seq.size();
+  for (int64_t qs = 0; qs < nq; ++qs) {
+    const QueryDesc qd = seq.get(qs);
+    const int xb = int(qs % kXBufs);
+    if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg.status)) return;
+    const float* xq = rg.xbuf + xb * cfg.xpad;
+    bool ok;
+    if (XMODE == 0) {
+      ok = coef_query<true>(qd, qs, st, cfg, rg, sh, xq);
+    } else if (XMODE == 1) {
+      ok = coef_query<false>(qd, qs, st, cfg, rg, sh, xq);
+    } else {
+      ok = qd.n <= 1024 ? coef_query<true>(qd, qs, st, cfg, rg, sh, xq)
+                        : coef_query<false>(qd, qs, st, cfg, rg, sh, xq);
+    }
+    if (!ok) return;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.x_empty[xb]);
+  }
+}
+
+// ---------------------------------------------------------------- gather
+template <typename RT, int GPT>
+__device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint32_t& ph,
+                             const LaunchCfg& cfg, const Regions& rg, Shared& sh, float* means) {
+  using G = Granule<RT>;
+  constexpr int GR = G::kElems;
+  const int lane = threadIdx.x & 31;
+  const int gt = threadIdx.x - kFirstGatherWarp * 32;
+  const int CR = cfg.crows;
+  const uint32_t nchunk = uint32_t(cfg.nchunk);
+  const int mb = int(qs % kMBufs);
+  float acc[GPT][GR];
+#pragma unroll
+  for (int u = 0; u < GPT; ++u)
+#pragma unroll
+    for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
+  int batch_left = qd.J, batch = 0;
+  for (int64_t j0 = 0; j0 < qd.N; j0 += CR) {
+    const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
+    if (!wait_phase(&sh.row_full[cs], ph, sh, cfg.status)) return false;
+    if (!wait_phase(&sh.coef_full[cs], ph, sh, cfg.status)) return false;
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) {
+      if (s2 >= cnt) break;
+      const float c = rg.coef_s[cs * CR + s2];
+      const unsigned char* row = rg.ring + (size_t(cs) * CR + s2) * cfg.slot_bytes;
+#pragma unroll
+      for (int u = 0; u < GPT; ++u) {
+        const int gi = gt + u * kGatherThreads;
+        if (gi * GR < qd.ldr) {
+          float v[GR];
+          G::load(row + size_t(gi) * 16, v);
+#pragma unroll
+          for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
+        }
+      }
+      if (--batch_left == 0) {
+        if (batch == 0 && qs >= kMBufs &&
+            !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg.status))
+          return false;
+        float* mrow = means + int64_t(batch) * qd.ldr;
+#pragma unroll
+        for (int u = 0; u < GPT; ++u) {
+          const int gi = gt + u * kGatherThreads;
+          if (gi * GR < qd.ldr) {
+#pragma unroll
+            for (int e = 0; e < GR; ++e) {
+              mrow[gi * GR + e] = acc[u][e] * qd.inv_J;
+              acc[u][e] = 0.f;
+            }
+          }
+        }
+        batch_left = qd.J;
+        ++batch;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.slot_empty[cs]);
+    if (++cs == nchunk) {
+      cs = 0;
+      ph ^= 1u;
+    }
+  }
+  return true;
+}
+
+// DYN: the representation type is chosen per query (batches of mixed plans).
+template <class Seq, typename RT, int GPT, bool DYN>
+__device__ void gather_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
+  const int lane = threadIdx.x & 31;
+  uint32_t cs = 0, ph = 0;
+  const int64_t nq = seq.size();
+  for (int64_t qs = 0; qs < nq; ++qs) {
+    const QueryDesc qd = seq.get(qs);
+    float* means = rg.means_base + (qs % kMBufs) * cfg.mstride;
+    bool ok;
+    if (DYN) {
+      ok = qd.dtype == KERDOCK_BF16
+               ? gather_query<__nv_bfloat16, GPT>(qd, qs, cs, ph, cfg, rg, sh, means)
+               : gather_query<float, GPT>(qd, qs, cs, ph, cfg, rg, sh, means);
+    } else {
+      ok = gather_query<RT, GPT>(qd, qs, cs, ph, cfg, rg, sh, means);
+    }
+    if (!ok) return;
+    if (cfg.means_gmem != nullptr) __threadfence_block();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.means_full[qs % kMBufs]);
+  }
+}
+
+// ---------------------------------------------------------------- finalizer
+template <class Seq>
+__device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ft = tid - kFirstFinalWarp * 32;
+  const int fw = warp - kFirstFinalWarp;
+  float* mus = rg.mus;
+  int32_t* sel = rg.sel;
+  float* vals = rg.vals;
+  const int64_t nq = seq.size();
+  for (int64_t qs = 0; qs < nq; ++qs) {
+    const QueryDesc qd = seq.get(qs);
+    const int m = int(qd.m);
+    const int mb = int(qs % kMBufs), xb = int(qs % kXBufs);
+    if (!wait_phase(&sh.means_full[mb], uint32_t(qs / kMBufs) & 1u, sh, cfg.status)) return;
+    if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg.status)) return;
+    const float* means = rg.means_base + int64_t(mb) * cfg.mstride;
+    const float* xq = rg.xbuf + xb * cfg.xpad;
+    // a6: median over the K batch means.
+    for (int col = ft; col < m; col += kFinalThreads) {
+      float med;
+      if (qd.K == 1) {
+        med = means[col];
+      } else if (qd.K == 2) {
+        med = 0.5f * (means[col] + means[qd.ldr + col]);
+      } else {
+        float v[kMaxK];
+#pragma unroll
+        for (int kk = 0; kk < kMaxK; ++kk) v[kk] = kk < qd.K ? means[kk * qd.ldr + col] : 0.f;
+        const int r_lo = (qd.K - 1) / 2, r_hi = qd.K / 2;
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int i = 0; i < kMaxK; ++i) {
+          if (i >= qd.K) break;
+          int rank = 0;
+#pragma unroll
+          for (int j = 0; j < kMaxK; ++j)
+            if (j < qd.K && (v[j] < v[i] || (v[j] == v[i] && j < i))) ++rank;
+          if (rank == r_lo) lo = v[i];
+          if (rank == r_hi) hi = v[i];
+        }
+        med = (qd.K & 1) ? lo : 0.5f * (lo + hi);
+      }
+      mus[col] = med;
+      if (qd.mu_out) qd.mu_out[col] = med;
+    }
+    named_barrier_sync(kFinalBarrier, kFinalThreads);
+    if (ft == 0) mbar_arrive(&sh.means_empty[mb]);  // the means are consumed
+
+    // a7: top-S by radix select on |mu| (4 digits of 8 bits, high first).
+    uint32_t prefix = 0, mask = 0, remaining = uint32_t(qd.S);
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 24 - 8 * pass;
+      sh.hist[ft] = 0;
+      sh.hist[ft + kFinalThreads] = 0;
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      for (int i = ft; i < m; i += kFinalThreads) {
+        const uint32_t key = abs_key(mus[i]);
+        if ((key & mask) == prefix) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
+      }
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      if (fw == 0) {
+        const int base = (31 - lane) * 8;  // lane 0 holds the highest digits
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j2 = 0; j2 < 8; ++j2) sum += sh.hist[base + j2];
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - sum;
+        const uint32_t hit = __ballot_sync(0xffffffffu, excl < remaining && remaining <= incl);
+        if (lane == __ffs(hit) - 1) {
+          uint32_t cum = excl;
+          for (int j2 = 7; j2 >= 0; --j2) {
+            const uint32_t h = sh.hist[base + j2];
+            if (cum + h >= remaining) {
+              sh.digit = uint32_t(base + j2);
+              sh.remaining = remaining - cum;
+              break;
+            }
+            cum += h;
+          }
+        }
+      }
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      prefix |= sh.digit << shift;
+      mask |= 255u << shift;
+      remaining = sh.remaining;
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+    }
+    const uint32_t T = prefix;  // the S-th largest key; take `remaining` keys equal to T
+    {
+      const int seg = (m + kFinalThreads - 1) / kFinalThreads;
+      const int lo = ft * seg, hi = lo + seg < m ? lo + seg : m;
+      int eq = 0;
+      for (int i = lo; i < hi; ++i) eq += abs_key(mus[i]) == T;
+      int tot;
+      int eq_rank = final_exclusive_scan(eq, sh.scan, &tot);
+      const int eq_rank0 = eq_rank;
+      int take = 0;
+      for (int i = lo; i < hi; ++i) {
+        const uint32_t key = abs_key(mus[i]);
+        if (key > T) {
+          ++take;
+        } else if (key == T) {
+          take += uint32_t(eq_rank) < remaining;
+          ++eq_rank;
+        }
+      }
+      int pos = final_exclusive_scan(take, sh.scan, &tot);
+      eq_rank = eq_rank0;
+      for (int i = lo; i < hi; ++i) {
+        const uint32_t key = abs_key(mus[i]);
+        bool t2 = false;
+        if (key > T) {
+          t2 = true;
+        } else if (key == T) {
+          t2 = uint32_t(eq_rank) < remaining;
+          ++eq_rank;
+        }
+        if (t2) sel[pos++] = i;
+      }
+    }
+    named_barrier_sync(kFinalBarrier, kFinalThreads);
+
+    // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
+    for (int r0 = fw * 4; r0 < qd.S; r0 += kFinalWarps * 4) {
+      float racc[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* arow[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        arow[u] = qd.A + int64_t(sel[r0 + u < qd.S ? r0 + u : r0]) * qd.lda;
+      if (qd.a_vec4) {
+        const float4* xs4 = reinterpret_cast<const float4*>(xq);
+        const int n4 = int(qd.n >> 2);
+#pragma unroll 2
+        for (int p4 = lane; p4 < n4; p4 += 32) {
+          const float4 xv = xs4[p4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
+            racc[u] = fmaf(av.x, xv.x, racc[u]);
+            racc[u] = fmaf(av.y, xv.y, racc[u]);
+            racc[u] = fmaf(av.z, xv.z, racc[u]);
+            racc[u] = fmaf(av.w, xv.w, racc[u]);
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int64_t p = lane; p < qd.n; p += 32) {
+          const float xv = xq[p];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = warp_sum(racc[u]);
+        if (lane == 0 && r0 + u < qd.S) vals[r0 + u] = v;
+      }
+    }
+    named_barrier_sync(kFinalBarrier, kFinalThreads);
+    {
+      const int seg = (qd.S + kFinalThreads - 1) / kFinalThreads;
+      const int lo = ft * seg, hi = lo + seg < qd.S ? lo + seg : qd.S;
+      const bool full = qd.flags & KERDOCK_FLAG_FULL_OUTPUT;
+      int keep = 0;
+      for (int r = lo; r < hi; ++r) keep += full || fabsf(vals[r]) >= qd.eps;
+      int tot;
+      int pos = final_exclusive_scan(keep, sh.scan, &tot);
+      for (int r = lo; r < hi; ++r) {
+        if (full || fabsf(vals[r]) >= qd.eps) {
+          qd.out_idx[pos] = sel[r];
+          qd.out_val[pos] = vals[r];
+          ++pos;
+        }
+      }
+      if (ft == 0) *qd.out_count = tot;
+    }
+    named_barrier_sync(kFinalBarrier, kFinalThreads);
+    if (ft == 0) mbar_arrive(&sh.x_empty[xb]);  // x of this query is no longer needed
+  }
+}
+
+template <class Seq, typename RT, int GPT, bool DYN, int XMODE>
+__device__ __forceinline__ void run_roles(const Seq& seq, const LaunchCfg& cfg, Shared& sh,
+                                          unsigned char* smem) {
+  const Regions rg = regions(smem, cfg);
+  init_barriers(sh, cfg);
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    producer_role(seq, cfg, rg, sh);
+  } else if (warp < kFirstGatherWarp) {
+    coef_role<Seq, XMODE>(seq, cfg, rg, sh);
+  } else if (warp < kFirstFinalWarp) {
+    gather_role<Seq, RT, GPT, DYN>(seq, cfg, rg, sh);
+  } else {
+    final_role(seq, cfg, rg, sh);
+  }
+}
+
+// Single-plan kernel: the representation type, granules per gather thread and
+// the x placement are compile-time.
 template <typename RT, int GPT, bool XREG>
-int launch_typed(const Plan& p, const Layout& L, QueryArgs& a, void* ws) {
-  auto kern = query_kernel<RT, GPT, XREG>;
-  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(L.total)));
-  int occ = 0;
-  KD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, L.total));
-  if (occ < 1) return KERDOCK_ERR_UNSUPPORTED;
-  int64_t grid = p.num_sms;
-  if (grid > a.Q) grid = a.Q;
-  a.means_gmem = L.means_in_smem ? nullptr : static_cast<float*>(ws);
-  kern<<<unsigned(grid), kThreads, L.total, p.stream>>>(a);
-  KD_CUDA_TRY(cudaGetLastError());
-  return KERDOCK_OK;
+__global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ Shared sh;
+  SingleSeq seq{a};
+  run_roles<SingleSeq, RT, GPT, false, XREG ? 0 : 1>(seq, a.cfg, sh, smem);
+}
+
+// Batch kernel: any mix of plans (types and sizes), one descriptor per query.
+__global__ void __launch_bounds__(kThreads, 1) query_batch_kernel(const BatchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ Shared sh;
+  BatchSeq seq{a};
+  run_roles<BatchSeq, float, 4, true, 2>(seq, a.cfg, sh, smem);
 }
 
 }  // namespace
 
+size_t align_up(size_t v, size_t al) { return (v + al - 1) / al * al; }
+
+void dims_add(Dims& dm, const Plan& p, int64_t K, int64_t S) {
+  const uint32_t rb = uint32_t(p.ldr * p.elem_bytes());
+  if (rb > dm.row_bytes) dm.row_bytes = rb;
+  const int64_t xp = p.d > 32 ? p.d : 32;
+  if (xp > dm.xpad) dm.xpad = xp;
+  if (p.ldr > dm.ldr) dm.ldr = p.ldr;
+  if (S > dm.S) dm.S = S;
+  if (K * p.ldr > dm.KL) dm.KL = K * p.ldr;
+}
+
+bool means_fit_smem(const Dims& dm) {
+  return size_t(kMBufs) * size_t(dm.KL) * 4 <= kMeansSmemMax;
+}
+
+// Shared-memory layout for a launch.  ring_kb caps the row ring (0 = default
+// 160 KiB), crows forces the rows per chunk (0 = four when the ring holds at
+// least eight such chunks, else two, else one).  Returns false when the ring
+// cannot hold kMinChunks chunks.
+bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c) {
+  c = LaunchCfg{};
+  c.slot_bytes = dm.row_bytes;
+  c.xpad = dm.xpad;
+  c.mstride = dm.KL;
+  const size_t spad = align_up(size_t(dm.S), 4);
+  const size_t means_bytes = size_t(kMBufs) * size_t(dm.KL) * 4;
+  const size_t fixed = size_t(kXBufs) * size_t(dm.xpad) * 4 + (means_in_smem ? means_bytes : 0) +
+                       size_t(dm.ldr) * 4 + 2 * spad * 4 + 1024;
+  const size_t per_slot = size_t(dm.row_bytes) + 4;
+  size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
+  const size_t ring_cap = (tu.ring_kb > 0 ? size_t(tu.ring_kb) << 10 : kRingCap);
+  const size_t cap = ring_cap + size_t(kMaxSlots) * 4;
+  if (avail > cap) avail = cap;
+  int ns = int(avail / per_slot);
+  if (ns > kMaxSlots) ns = kMaxSlots;
+  int cr = tu.crows > 0 ? tu.crows : (ns >= 32 ? 4 : ns >= 8 ? 2 : 1);
+  if (cr != 1 && cr != 2 && cr != 4) return false;
+  c.crows = cr;
+  c.nchunk = ns / cr;
+  if (c.nchunk < kMinChunks) return false;
+  if (c.nchunk > kMaxChunks) c.nchunk = kMaxChunks;
+  ns = c.nchunk * cr;
+  int g = 1;  // chunks per producer step: g * crows <= 32 lanes, g <= nchunk / 2
+  while (2 * g * cr <= 32 && 4 * g <= c.nchunk) g *= 2;
+  c.pgroup = g;
+  size_t off = align_up(size_t(ns) * dm.row_bytes, 128);
+  c.off_coef = uint32_t(off);
+  off = align_up(off + size_t(ns) * 4, 16);
+  c.off_x = uint32_t(off);
+  off = align_up(off + size_t(kXBufs) * size_t(dm.xpad) * 4, 16);
+  c.off_means = uint32_t(off);
+  if (means_in_smem) off = align_up(off + means_bytes, 16);
+  c.off_mu = uint32_t(off);
+  off = align_up(off + size_t(dm.ldr) * 4, 16);
+  c.off_sel = uint32_t(off);
+  off = align_up(off + spad * 4, 16);
+  c.off_vals = uint32_t(off);
+  off = align_up(off + spad * 4, 16);
+  c.total = uint32_t(off);
+  return off <= kSmemBudget;
+}
+
+// Descriptor fields that come from the plan alone.
+QueryDesc plan_desc(const Plan& p) {
+  QueryDesc d{};
+  d.R = p.repr;
+  d.tsigns = p.tsigns();
+  d.A = p.A;
+  d.tstride = p.tsign_words;
+  d.lda = p.lda;
+  d.m = p.m;
+  d.n = p.n;
+  d.d = p.d;
+  d.L = p.L;
+  d.ldr = p.ldr;
+  d.k = p.k;
+  d.dtype = p.dtype;
+  d.a_vec4 =
+      (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
+  d.row_bytes = uint32_t(p.ldr * p.elem_bytes());
+  d.sqrt_d = float(int64_t(1) << (p.k / 2));
+  return d;
+}
+
+void set_query_params(QueryDesc& d, int64_t J, int64_t K, int64_t S, float eps, uint64_t seed,
+                      int flags) {
+  d.J = int32_t(J);
+  d.K = int32_t(K);
+  d.N = J * K;
+  d.S = int32_t(S);
+  d.eps = eps;
+  d.inv_J = 1.0f / float(J);
+  d.seed = seed;
+  d.flags = flags;
+}
+
+namespace {
+
+template <typename RT, int GPT, bool XREG>
+int launch_single(const QueryArgs& a, int64_t grid, cudaStream_t stream) {
+  auto kern = query_kernel<RT, GPT, XREG>;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(a.cfg.total)));
+  kern<<<unsigned(grid), kThreads, a.cfg.total, stream>>>(a);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
+  const int64_t granule = 16 / int64_t(p.elem_bytes());
+  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
+  const bool xreg = p.n <= 1024;
+  if (p.dtype == KERDOCK_BF16) {
+    if (gpt <= 1) return xreg ? launch_single<__nv_bfloat16, 1, true>(a, grid, p.stream)
+                              : launch_single<__nv_bfloat16, 1, false>(a, grid, p.stream);
+    if (gpt <= 2) return xreg ? launch_single<__nv_bfloat16, 2, true>(a, grid, p.stream)
+                              : launch_single<__nv_bfloat16, 2, false>(a, grid, p.stream);
+    return launch_single<__nv_bfloat16, 4, false>(a, grid, p.stream);
+  }
+  if (gpt <= 1) return xreg ? launch_single<float, 1, true>(a, grid, p.stream)
+                            : launch_single<float, 1, false>(a, grid, p.stream);
+  if (gpt <= 2) return xreg ? launch_single<float, 2, true>(a, grid, p.stream)
+                            : launch_single<float, 2, false>(a, grid, p.stream);
+  return launch_single<float, 4, false>(a, grid, p.stream);
+}
+
+}  // namespace
+
+Dims plan_dims(const Plan& p) {
+  Dims dm;
+  dims_add(dm, p, p.K, p.S);
+  return dm;
+}
+
 size_t apply_workspace_bytes(const Plan& p, int64_t q) {
-  const Layout L = make_layout(p);
-  if (L.means_in_smem || q == 0) return 0;
+  const Dims dm = plan_dims(p);
+  if (means_fit_smem(dm) || q == 0) return 0;
   const int64_t grid = p.num_sms > 0 ? p.num_sms : 256;
-  return size_t(grid) * kMBufs * size_t(p.K) * size_t(p.ldr) * 4;
+  return size_t(grid) * kMBufs * size_t(dm.KL) * 4;
 }
 
 int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps, uint64_t seed,
                  int flags, int32_t* out_idx, float* out_val, int32_t* out_count, void* ws,
                  size_t ws_bytes, float* mu_out, int64_t* ells_out, float* coef_out) {
   (void)ws_bytes;
-  const Layout L = make_layout(p);
-  if (L.nchunk < kMinChunks || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
+  const Dims dm = plan_dims(p);
+  const bool smem_means = means_fit_smem(dm);
   QueryArgs a{};
-  a.R = p.repr;
-  a.tsigns = p.tsigns();
-  a.tsign_stride = p.tsign_words;
-  a.A = p.A;
-  a.lda = p.lda;
-  a.X = X;
-  a.ldx = ldx;
+  if (!make_cfg(dm, p.tuning, smem_means, a.cfg)) return KERDOCK_ERR_UNSUPPORTED;
+  a.cfg.means_gmem = smem_means ? nullptr : static_cast<float*>(ws);
+  a.cfg.status = p.status();
+  a.base = plan_desc(p);
+  set_query_params(a.base, p.J, p.K, p.S, eps, seed, flags);
+  a.base.x = X;
+  a.base.out_idx = out_idx;
+  a.base.out_val = out_val;
+  a.base.out_count = out_count;
+  a.base.mu_out = mu_out;
+  a.base.ells_out = ells_out;
+  a.base.coef_out = coef_out;
   a.Q = q;
-  a.m = p.m;
-  a.n = p.n;
-  a.d = p.d;
-  a.L = p.L;
-  a.ldr = p.ldr;
-  a.N = p.N;
-  a.xpad = L.xpad;
-  a.k = p.k;
-  a.J = p.J;
-  a.K = p.K;
-  a.S = p.S;
-  a.eps = eps;
-  a.inv_J = 1.0f / float(p.J);
-  a.sqrt_d = float(int64_t(1) << (p.k / 2));
-  a.seed = seed;
-  a.flags = flags;
-  a.a_vec4 =
-      (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
-  a.nchunk = L.nchunk;
-  a.crows = L.crows;
-  a.pgroup = L.pgroup;
-  a.row_bytes = L.row_bytes;
-  a.off_coef = uint32_t(L.off_coef);
-  a.off_x = uint32_t(L.off_x);
-  a.off_means = uint32_t(L.off_means);
-  a.off_mu = uint32_t(L.off_mu);
-  a.off_sel = uint32_t(L.off_sel);
-  a.off_vals = uint32_t(L.off_vals);
-  a.out_idx = out_idx;
-  a.out_val = out_val;
-  a.out_count = out_count;
-  a.mu_out = mu_out;
-  a.ells_out = ells_out;
-  a.coef_out = coef_out;
-  a.status = p.status();
-  const int64_t granule = 16 / int64_t(p.elem_bytes());
-  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
-  const bool xreg = p.n <= 1024;
-  if (p.dtype == KERDOCK_BF16) {
-    if (gpt <= 1) return xreg ? launch_typed<__nv_bfloat16, 1, true>(p, L, a, ws)
-                              : launch_typed<__nv_bfloat16, 1, false>(p, L, a, ws);
-    if (gpt <= 2) return xreg ? launch_typed<__nv_bfloat16, 2, true>(p, L, a, ws)
-                              : launch_typed<__nv_bfloat16, 2, false>(p, L, a, ws);
-    return launch_typed<__nv_bfloat16, 4, false>(p, L, a, ws);
-  }
-  if (gpt <= 1) return xreg ? launch_typed<float, 1, true>(p, L, a, ws)
-                            : launch_typed<float, 1, false>(p, L, a, ws);
-  if (gpt <= 2) return xreg ? launch_typed<float, 2, true>(p, L, a, ws)
-                            : launch_typed<float, 2, false>(p, L, a, ws);
-  return launch_typed<float, 4, false>(p, L, a, ws);
+  a.ldx = ldx;
+  int64_t grid = p.num_sms;
+  if (grid > q) grid = q;
+  return dispatch_single(p, a, grid);
 }
+
 
 // ---------------------------------------------------------------------------
 // Allocation-free apply.  Some callers cannot allocate device memory: code
@@ -796,53 +943,6 @@ int noalloc_scratch(void** out) {
   return KERDOCK_OK;
 }
 
-// The kernel's shared-memory layout with the batch means always in global
-// scratch (so the whole shared-memory budget goes to the row ring).
-Layout make_layout_noalloc(const Plan& p) {
-  Layout L{};
-  L.row_bytes = uint32_t(p.ldr * p.elem_bytes());
-  L.xpad = p.d > 32 ? p.d : 32;
-  const size_t spad = align_up(size_t(p.S), 4);
-  L.means_in_smem = false;
-  const size_t fixed = size_t(kXBufs) * size_t(L.xpad) * 4 + size_t(p.ldr) * 4 + 2 * spad * 4 + 1024;
-  const size_t per_slot = size_t(L.row_bytes) + 4;
-  size_t avail = kSmemBudget > fixed ? kSmemBudget - fixed : 0;
-  const size_t cap = kRingCap + size_t(kMaxSlots) * 4;
-  if (avail > cap) avail = cap;
-  int ns = int(avail / per_slot);
-  if (ns > kMaxSlots) ns = kMaxSlots;
-  L.crows = ns >= 32 ? 4 : ns >= 8 ? 2 : 1;
-  L.nchunk = ns / L.crows;
-  ns = L.nchunk * L.crows;
-  int g = 1;
-  while (2 * g * L.crows <= 32 && 4 * g <= L.nchunk) g *= 2;
-  L.pgroup = g;
-  size_t off = align_up(size_t(ns) * L.row_bytes, 128);
-  L.off_coef = off;
-  off = align_up(off + size_t(ns) * 4, 16);
-  L.off_x = off;
-  off = align_up(off + size_t(kXBufs) * size_t(L.xpad) * 4, 16);
-  L.off_means = off;
-  L.off_mu = off;
-  off = align_up(off + size_t(p.ldr) * 4, 16);
-  L.off_sel = off;
-  off = align_up(off + spad * 4, 16);
-  L.off_vals = off;
-  off = align_up(off + spad * 4, 16);
-  L.total = off;
-  return L;
-}
-
-template <typename RT, int GPT, bool XREG>
-int launch_noalloc_typed(const Layout& L, QueryArgs& a, int64_t grid, cudaStream_t stream) {
-  auto kern = query_kernel<RT, GPT, XREG>;
-  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(L.total)));
-  kern<<<unsigned(grid), kThreads, L.total, stream>>>(a);
-  KD_CUDA_TRY(cudaGetLastError());
-  return KERDOCK_OK;
-}
-
 }  // namespace
 
 size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
@@ -850,72 +950,50 @@ size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
 int launch_apply_noalloc(const Plan& p, const float* X, int64_t q, int64_t ldx, float eps,
                          uint64_t seed, int flags, int32_t* out_idx, float* out_val,
                          int32_t* out_count) {
-  const Layout L = make_layout_noalloc(p);
-  if (L.nchunk < kMinChunks || L.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
+  const Dims dm = plan_dims(p);
+  QueryArgs a{};
+  // the batch means always go to the scratch array, so the whole shared-memory
+  // budget goes to the row ring
+  if (!make_cfg(dm, p.tuning, false, a.cfg)) return KERDOCK_ERR_UNSUPPORTED;
   int64_t grid = p.num_sms;
   if (grid > q) grid = q;
-  const size_t need = size_t(grid) * kMBufs * size_t(p.K) * size_t(p.ldr) * sizeof(float);
+  const size_t need = size_t(grid) * kMBufs * size_t(dm.KL) * sizeof(float);
   if (need > kNoAllocScratchBytes) return KERDOCK_ERR_CAPACITY;  // beyond the fixed scratch
   void* scratch = nullptr;
   const int rc = noalloc_scratch(&scratch);
   if (rc != KERDOCK_OK) return rc;
-  QueryArgs a{};
-  a.R = p.repr;
-  a.tsigns = p.tsigns();
-  a.tsign_stride = p.tsign_words;
-  a.A = p.A;
-  a.lda = p.lda;
-  a.X = X;
-  a.ldx = ldx;
+  a.cfg.means_gmem = static_cast<float*>(scratch);
+  a.cfg.status = p.status();
+  a.base = plan_desc(p);
+  set_query_params(a.base, p.J, p.K, p.S, eps, seed, flags);
+  a.base.x = X;
+  a.base.out_idx = out_idx;
+  a.base.out_val = out_val;
+  a.base.out_count = out_count;
   a.Q = q;
-  a.m = p.m;
-  a.n = p.n;
-  a.d = p.d;
-  a.L = p.L;
-  a.ldr = p.ldr;
-  a.N = p.N;
-  a.xpad = L.xpad;
-  a.k = p.k;
-  a.J = p.J;
-  a.K = p.K;
-  a.S = p.S;
-  a.eps = eps;
-  a.inv_J = 1.0f / float(p.J);
-  a.sqrt_d = float(int64_t(1) << (p.k / 2));
-  a.seed = seed;
-  a.flags = flags;
-  a.a_vec4 =
-      (p.n % 4 == 0 && p.lda % 4 == 0 && (reinterpret_cast<uintptr_t>(p.A) & 15) == 0) ? 1 : 0;
-  a.nchunk = L.nchunk;
-  a.crows = L.crows;
-  a.pgroup = L.pgroup;
-  a.row_bytes = L.row_bytes;
-  a.off_coef = uint32_t(L.off_coef);
-  a.off_x = uint32_t(L.off_x);
-  a.off_means = uint32_t(L.off_means);
-  a.off_mu = uint32_t(L.off_mu);
-  a.off_sel = uint32_t(L.off_sel);
-  a.off_vals = uint32_t(L.off_vals);
-  a.means_gmem = static_cast<float*>(scratch);
-  a.out_idx = out_idx;
-  a.out_val = out_val;
-  a.out_count = out_count;
-  a.status = p.status();
-  const int64_t granule = 16 / int64_t(p.elem_bytes());
-  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
-  const bool xreg = p.n <= 1024;
-  if (p.dtype == KERDOCK_BF16) {
-    if (gpt <= 1) return xreg ? launch_noalloc_typed<__nv_bfloat16, 1, true>(L, a, grid, p.stream)
-                              : launch_noalloc_typed<__nv_bfloat16, 1, false>(L, a, grid, p.stream);
-    if (gpt <= 2) return xreg ? launch_noalloc_typed<__nv_bfloat16, 2, true>(L, a, grid, p.stream)
-                              : launch_noalloc_typed<__nv_bfloat16, 2, false>(L, a, grid, p.stream);
-    return launch_noalloc_typed<__nv_bfloat16, 4, false>(L, a, grid, p.stream);
-  }
-  if (gpt <= 1) return xreg ? launch_noalloc_typed<float, 1, true>(L, a, grid, p.stream)
-                            : launch_noalloc_typed<float, 1, false>(L, a, grid, p.stream);
-  if (gpt <= 2) return xreg ? launch_noalloc_typed<float, 2, true>(L, a, grid, p.stream)
-                            : launch_noalloc_typed<float, 2, false>(L, a, grid, p.stream);
-  return launch_noalloc_typed<float, 4, false>(L, a, grid, p.stream);
+  a.ldx = ldx;
+  return dispatch_single(p, a, grid);
+}
+
+// ---------------------------------------------------------------------------
+// Batches of queries over any mix of plans (one persistent launch).
+// ---------------------------------------------------------------------------
+int prepare_batch_kernel(const LaunchCfg& cfg) {
+  KD_CUDA_TRY(cudaFuncSetAttribute(query_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(cfg.total)));
+  return KERDOCK_OK;
+}
+
+int launch_batch(const LaunchCfg& cfg, const QueryDesc* descs, const int32_t* order,
+                 const int64_t* cta_start, int grid, cudaStream_t stream) {
+  BatchArgs a{};
+  a.cfg = cfg;
+  a.descs = descs;
+  a.order = order;
+  a.cta_start = cta_start;
+  query_batch_kernel<<<unsigned(grid), kThreads, cfg.total, stream>>>(a);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
 }
 
 }  // namespace kd

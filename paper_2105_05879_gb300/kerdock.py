@@ -32,7 +32,12 @@ EXPORTED = [
     "kerdock_preprocess", "kerdock_apply_workspace_bytes", "kerdock_apply",
     "kerdock_apply_debug", "kerdock_sync", "kerdock_debug_signs", "kerdock_plan_destroy",
     "kerdock_strerror", "kerdock_version", "kerdock_apply_noalloc",
+    "kerdock_batch_workspace_bytes", "kerdock_batch_create", "kerdock_batch_launch",
+    "kerdock_batch_set_tuning", "kerdock_batch_tune", "kerdock_batch_sync",
+    "kerdock_batch_destroy", "kerdock_plan_set_tuning", "kerdock_plan_tune",
 ]
+
+KERDOCK_BATCH_GRAPH = 1
 
 
 class KerdockError(RuntimeError):
@@ -52,6 +57,17 @@ class PlanInfo(ctypes.Structure):
         ("L", ctypes.c_int64), ("ldr", ctypes.c_int64), ("J", ctypes.c_int32),
         ("K", ctypes.c_int32), ("S", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("repr_bytes", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t),
+    ]
+
+
+class Query(ctypes.Structure):
+    """Mirror of kerdock_query_t."""
+    _fields_ = [
+        ("plan", ctypes.c_void_p), ("x", ctypes.c_void_p), ("J", ctypes.c_int32),
+        ("K", ctypes.c_int32), ("S", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("eps", ctypes.c_float), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64),
+        ("index", ctypes.c_int64), ("out_idx", ctypes.c_void_p), ("out_val", ctypes.c_void_p),
+        ("out_count", ctypes.c_void_p),
     ]
 
 
@@ -83,6 +99,22 @@ def load_library(path=None):
                                                c_sz, c_vp, c_vp, c_vp]),
         "kerdock_apply_noalloc": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float,
                                                  ctypes.c_uint64, c_i32, c_vp, c_vp, c_vp]),
+        "kerdock_batch_workspace_bytes": (c_sz, [ctypes.POINTER(Query), c_i64]),
+        "kerdock_batch_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(Query), c_i64,
+                                                c_vp, c_sz, c_vp, c_i32]),
+        "kerdock_batch_launch": (ctypes.c_int, [P]),
+        "kerdock_batch_set_tuning": (ctypes.c_int, [P, c_i32, c_i32]),
+        "kerdock_batch_tune": (ctypes.c_int, [P, c_i32, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_float)]),
+        "kerdock_batch_sync": (ctypes.c_int, [P]),
+        "kerdock_batch_destroy": (ctypes.c_int, [P]),
+        "kerdock_plan_set_tuning": (ctypes.c_int, [P, c_i32, c_i32]),
+        "kerdock_plan_tune": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float,
+                                             ctypes.c_uint64, c_vp, c_vp, c_vp, c_vp, c_sz, c_i32,
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_float)]),
         "kerdock_sync": (ctypes.c_int, [P]),
         "kerdock_debug_signs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32), c_sz]),
         "kerdock_plan_destroy": (ctypes.c_int, [P]),
@@ -151,6 +183,58 @@ def kerdock_apply_noalloc(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_pt
     memory; the scratch is a fixed array inside the library (see kerdock.h)."""
     _check(load_library().kerdock_apply_noalloc(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
                                                 val_ptr, cnt_ptr), "kerdock_apply_noalloc")
+
+
+def kerdock_batch_workspace_bytes(queries):
+    arr = (Query * len(queries))(*queries)
+    return load_library().kerdock_batch_workspace_bytes(arr, len(queries))
+
+
+def kerdock_batch_create(queries, ws_ptr, ws_bytes, stream, options):
+    arr = (Query * len(queries))(*queries)
+    h = ctypes.c_void_p()
+    _check(load_library().kerdock_batch_create(ctypes.byref(h), arr, len(queries), ws_ptr,
+                                               ws_bytes, stream, options), "kerdock_batch_create")
+    return h
+
+
+def kerdock_batch_launch(batch):
+    _check(load_library().kerdock_batch_launch(batch), "kerdock_batch_launch")
+
+
+def kerdock_batch_set_tuning(batch, ring_kb, crows):
+    _check(load_library().kerdock_batch_set_tuning(batch, ring_kb, crows),
+           "kerdock_batch_set_tuning")
+
+
+def kerdock_batch_tune(batch, reps):
+    rk, cr, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load_library().kerdock_batch_tune(batch, reps, ctypes.byref(rk), ctypes.byref(cr),
+                                             ctypes.byref(ms)), "kerdock_batch_tune")
+    return rk.value, cr.value, ms.value
+
+
+def kerdock_batch_sync(batch):
+    _check(load_library().kerdock_batch_sync(batch), "kerdock_batch_sync")
+
+
+def kerdock_batch_destroy(batch):
+    if batch is not None:
+        load_library().kerdock_batch_destroy(batch)
+
+
+def kerdock_plan_set_tuning(plan, ring_kb, crows):
+    _check(load_library().kerdock_plan_set_tuning(plan, ring_kb, crows), "kerdock_plan_set_tuning")
+
+
+def kerdock_plan_tune(plan, X_ptr, q, ldx, eps, seed, idx_ptr, val_ptr, cnt_ptr, ws_ptr, ws_bytes,
+                      reps):
+    rk, cr, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load_library().kerdock_plan_tune(plan, X_ptr, q, ldx, eps, seed, idx_ptr, val_ptr,
+                                            cnt_ptr, ws_ptr, ws_bytes, reps, ctypes.byref(rk),
+                                            ctypes.byref(cr), ctypes.byref(ms)),
+           "kerdock_plan_tune")
+    return rk.value, cr.value, ms.value
 
 
 def kerdock_sync(plan):
@@ -278,6 +362,72 @@ class KerdockPlan:
     def close(self):
         if self.handle is not None:
             kerdock_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KerdockBatch:
+    """Queries over several KerdockPlans answered by one persistent launch
+    (optionally a replayed CUDA graph).  ``specs`` is a list of dicts with
+    keys plan, x (1-D CUDA float32 tensor, n floats), J, K, S, eps, seed,
+    index and optionally flags.  Outputs are allocated here."""
+
+    def __init__(self, specs, graph=True, stream=None):
+        import torch
+        self.torch = torch
+        self.specs = specs
+        dev = specs[0]["plan"].device
+        self.outputs = []
+        queries = []
+        for sp in specs:
+            S = int(sp["S"])
+            idx = torch.empty(S, dtype=torch.int32, device=dev)
+            val = torch.empty(S, dtype=torch.float32, device=dev)
+            cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+            self.outputs.append((idx, val, cnt))
+            x = sp["x"]
+            assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+            queries.append(Query(plan=sp["plan"].handle.value, x=x.data_ptr(), J=int(sp["J"]),
+                                 K=int(sp["K"]), S=S, flags=int(sp.get("flags", 0)),
+                                 eps=float(sp["eps"]), reserved=0, seed=int(sp["seed"]),
+                                 index=int(sp["index"]), out_idx=idx.data_ptr(),
+                                 out_val=val.data_ptr(), out_count=cnt.data_ptr()))
+        self.queries = queries
+        nb = kerdock_batch_workspace_bytes(queries)
+        if nb == 0:
+            raise KerdockError(-1, "kerdock_batch_workspace_bytes")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.handle = kerdock_batch_create(queries, self.ws.data_ptr(), nb, self.stream.cuda_stream,
+                                           KERDOCK_BATCH_GRAPH if graph else 0)
+
+    def launch(self):
+        kerdock_batch_launch(self.handle)
+
+    def tune(self, reps=3):
+        return kerdock_batch_tune(self.handle, reps)
+
+    def set_tuning(self, ring_kb, crows):
+        kerdock_batch_set_tuning(self.handle, ring_kb, crows)
+
+    def sync(self):
+        kerdock_batch_sync(self.handle)
+
+    def results(self):
+        out = []
+        for idx, val, cnt in self.outputs:
+            c = int(cnt.item())
+            out.append((idx[:c].cpu().numpy().astype(np.int64), val[:c].cpu().numpy().astype(np.float64)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            kerdock_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

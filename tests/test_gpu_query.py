@@ -228,3 +228,27 @@ def test_query_d4096(K, dtype):
     check_query(A64, None, X64, plan, res, 0.15, 9, J, Kb, S, 12, dtype=dtype, lazy=True,
                 full=True)
     plan.close()
+
+
+def test_plan_autotune_keeps_results(K, tmp_path, monkeypatch):
+    # the ring geometry chosen by the autotuner changes timing, not results
+    from paper_2105_05879_gb300 import tuning
+    monkeypatch.setenv("KERDOCK_TUNING_CACHE", str(tmp_path / "tune.json"))
+    torch = torch_cuda()
+    wl = workloads.WORKLOADS["n64"]
+    A = wl.make_A().astype(np.float32)
+    X = workloads.queries_from_codes(f32(A), wl.make_codes()).astype(np.float32)
+    plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S)
+    plan.preprocess(torch.from_numpy(A).cuda())
+    Xt = torch.from_numpy(X).cuda()
+    ref = [t.cpu().numpy() for t in plan.apply(Xt, wl.eps, 3)]
+    rk, cr, ms = tuning.autotune_plan(plan, Xt, wl.eps, 3, reps=2)
+    assert (tmp_path / "tune.json").exists()
+    rk2, cr2, _ = tuning.autotune_plan(plan, Xt, wl.eps, 3, reps=2)  # from the cache
+    assert (rk2, cr2) == (rk, cr)
+    got = [t.cpu().numpy() for t in plan.apply(Xt, wl.eps, 3)]
+    np.testing.assert_array_equal(got[2], ref[2])
+    for q in range(X.shape[0]):
+        np.testing.assert_array_equal(got[0][q, :got[2][q]], ref[0][q, :ref[2][q]])
+        np.testing.assert_array_equal(got[1][q, :got[2][q]], ref[1][q, :ref[2][q]])
+    plan.close()
