@@ -97,24 +97,22 @@ __global__ void signs_kernel(uint32_t* __restrict__ signs, uint32_t* __restrict_
     s_upper[a] = U;
   }
   __syncthreads();
-  for (int64_t w = threadIdx.x; w < words_per_row; w += blockDim.x) {
-    uint32_t bits = 0;
-    for (int j = 0; j < 32; ++j) {
-      const int64_t p = w * 32 + j;
-      if (p >= d) break;
-      bits |= quad_form(s_upper, k, uint32_t(p)) << j;
-    }
-    signs[int64_t(b) * words_per_row + w] = bits;
+  // p-order table: each thread evaluates Q at one p, a warp ballot packs 32 bits.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t words = d >= 32 ? d / 32 : 1;
+  for (int64_t w = warp; w < words; w += nwarps) {
+    const int64_t p = w * 32 + lane;
+    const uint32_t bits = __ballot_sync(0xffffffffu, p < d ? quad_form(s_upper, k, uint32_t(p)) : 0u);
+    if (lane == 0) signs[int64_t(b) * words_per_row + w] = bits;
   }
+  for (int64_t w = words + threadIdx.x; w < words_per_row; w += blockDim.x)
+    signs[int64_t(b) * words_per_row + w] = 0u;  // row padding
   // Lane-transposed layout: word [g][L], bit t <-> p = 32 (32 g + t) + L.
-  for (int64_t i = threadIdx.x; i < twords_per_row; i += blockDim.x) {
+  for (int64_t i = warp; i < twords_per_row; i += nwarps) {
     const int64_t g = i >> 5, L = i & 31;
-    uint32_t bits = 0;
-    for (int t = 0; t < 32; ++t) {
-      const int64_t p = 32 * (32 * g + t) + L;
-      if (p < d) bits |= quad_form(s_upper, k, uint32_t(p)) << t;
-    }
-    tsigns[int64_t(b) * twords_per_row + i] = bits;
+    const int64_t p = 32 * (32 * g + lane) + L;
+    const uint32_t bits = __ballot_sync(0xffffffffu, p < d ? quad_form(s_upper, k, uint32_t(p)) : 0u);
+    if (lane == 0) tsigns[int64_t(b) * twords_per_row + i] = bits;
   }
 }
 
@@ -122,7 +120,7 @@ __global__ void signs_kernel(uint32_t* __restrict__ signs, uint32_t* __restrict_
 
 int launch_signs(const Plan& p) {
   KD_CUDA_TRY(cudaMemsetAsync(p.table, 0, kStatusBytes, p.stream));
-  signs_kernel<<<unsigned(p.d / 2), 128, 0, p.stream>>>(p.signs(), p.tsigns(), p.k,
+  signs_kernel<<<unsigned(p.d / 2), 256, 0, p.stream>>>(p.signs(), p.tsigns(), p.k,
                                                          p.sign_words, p.tsign_words);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
