@@ -243,6 +243,59 @@ int kerdock_plan_tune(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_
                       void* ws_dev, size_t ws_bytes, int32_t reps, int32_t* ring_kb,
                       int32_t* crows, float* best_ms);
 
+/* ------------------------------------------------------------------------
+ * Learned proposal (a project form, not in the paper): a three-layer
+ * perceptron in bfloat16 (FP32 accumulation on tensor cores) maps a cheap
+ * sketch mu (a plan with small J, K) to one score per output index; the top
+ * scores replace the top-|mu| candidates of Algorithm 1's refinement step.
+ *   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3,
+ * trained with binary cross-entropy on logits (positive weight w+) and AdamW.
+ * ------------------------------------------------------------------------ */
+typedef struct kerdock_mlp_s* kerdock_mlp_t;
+
+/* in_dim, hidden, out_dim even; max_batch rows per forward/backward call. */
+int kerdock_mlp_create(kerdock_mlp_t* mlp, int32_t in_dim, int32_t hidden, int32_t out_dim,
+                       int32_t max_batch);
+/* Device bytes for the state (FP32 master weights, gradients, AdamW moments,
+ * bfloat16 weight copies) and for the activations of max_batch rows. */
+int kerdock_mlp_sizes(kerdock_mlp_t mlp, size_t* state_bytes, size_t* work_bytes,
+                      int64_t* param_count);
+int kerdock_mlp_bind(kerdock_mlp_t mlp, void* state_dev, size_t state_bytes, void* work_dev,
+                     size_t work_bytes, void* stream);
+/* Device pointers of the FP32 parameters and gradients (layout W1, b1, W2,
+ * b2, W3, b3, row-major; offsets[7] receives the 6 start offsets and the end).
+ * After writing parameters directly call kerdock_mlp_sync_weights. */
+int kerdock_mlp_pointers(kerdock_mlp_t mlp, float** params, float** grads, int64_t* offsets);
+int kerdock_mlp_sync_weights(kerdock_mlp_t mlp);
+/* Weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from the SplitMix64 counter hash,
+ * zero biases and moments. */
+int kerdock_mlp_init(kerdock_mlp_t mlp, uint64_t seed);
+/* logits (B x out_dim FP32) for features feat_scale * feats (B x in_dim FP32). */
+int kerdock_mlp_forward(kerdock_mlp_t mlp, const float* feats, int32_t B, float feat_scale,
+                        float* logits);
+/* Forward + backward for labels (B x out_dim, 0/1): fills the gradients and
+ * the loss (read with kerdock_mlp_loss). */
+int kerdock_mlp_backward(kerdock_mlp_t mlp, const float* feats, const float* labels, int32_t B,
+                         float feat_scale, float pos_weight);
+int kerdock_mlp_loss(kerdock_mlp_t mlp, float* loss_host);
+/* One AdamW step (decoupled weight decay) on all parameters. */
+int kerdock_mlp_adamw(kerdock_mlp_t mlp, float lr, float beta1, float beta2, float eps,
+                      float weight_decay);
+int kerdock_mlp_destroy(kerdock_mlp_t mlp);
+
+/* Refinement from scores: for each of q queries take the S indices with the
+ * largest scores (q x m FP32, ties to the smaller index), compute a_i^T x
+ * exactly (Algorithm 1's last step) and keep |value| >= eps (all S with
+ * KERDOCK_FLAG_FULL_OUTPUT).  Outputs as kerdock_apply with capacity S. */
+int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                          const float* scores, int32_t S, float eps, int32_t flags,
+                          int32_t* out_idx, float* out_val, int32_t* out_count);
+
+/* A second plan over the same bound and preprocessed representation with
+ * other J, K, S (e.g. a cheap sketch setting).  The clone shares the source's
+ * device memory and stream; the source must outlive it. */
+int kerdock_plan_clone(kerdock_plan_t* out, kerdock_plan_t src, int32_t J, int32_t K, int32_t S);
+
 /* Synchronise the plan's stream and report the first error any kernel of
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);

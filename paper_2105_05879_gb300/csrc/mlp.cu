@@ -1,0 +1,527 @@
+// mlp.cu -- the learned-proposal network and the score-ranked refinement.
+//
+// Not in the paper: a project form that replaces the |mu| ranking of
+// Algorithm 1's top-S step by the scores of a small network fed with a cheap
+// sketch mu (reduced N), so that fewer samples and fewer refined rows reach the
+// same support.  The network is a three-layer perceptron in bfloat16 with FP32
+// accumulation on tensor cores (mma.sync m16n8k16), trained on the GPU with
+// binary cross-entropy on logits and AdamW:
+//   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3.
+// Every product of the forward and backward passes is one strided GEMM kernel
+// C = op(A) op(B)^T with a fused epilogue (bias, ReLU, ReLU mask, FP32/BF16).
+#include <cstring>
+#include <new>
+
+#include "kerdock_internal.cuh"
+
+namespace kd {
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 32, GTHREADS = 128;
+
+struct GemmArgs {
+  int M, N, K;
+  const __nv_bfloat16* A;  // element (m, k) at A[m * sAm + k * sAk]
+  int64_t sAm, sAk;
+  const __nv_bfloat16* B;  // element (n, k) at B[n * sBn + k * sBk]
+  int64_t sBn, sBk;
+};
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// C[m, n] = sum_k A(m, k) B(n, k), 64 x 64 tiles, 4 warps of 32 x 32, epilogue
+// functor per element.
+template <class Epi>
+__global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g, const Epi epi) {
+  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + 8];
+  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + 8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int group = lane >> 2, tig = lane & 3;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+    for (int i = tid; i < GBM * GBK; i += GTHREADS) {
+      int mm, kk;
+      if (g.sAk == 1) { mm = i / GBK; kk = i % GBK; } else { mm = i % GBM; kk = i / GBM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[mm][kk] = (gm < g.M && gk < g.K) ? g.A[int64_t(gm) * g.sAm + int64_t(gk) * g.sAk] : zero;
+    }
+    for (int i = tid; i < GBN * GBK; i += GTHREADS) {
+      int nn, kk;
+      if (g.sBk == 1) { nn = i / GBK; kk = i % GBK; } else { nn = i % GBN; kk = i / GBN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      Bs[nn][kk] = (gn < g.N && gk < g.K) ? g.B[int64_t(gn) * g.sBn + int64_t(gk) * g.sBk] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < GBK; ks += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int r = wm + mt * 16 + group, c = ks + tig * 2;
+        a[mt][0] = ld_pair(&As[r][c]);
+        a[mt][1] = ld_pair(&As[r + 8][c]);
+        a[mt][2] = ld_pair(&As[r][c + 8]);
+        a[mt][3] = ld_pair(&As[r + 8][c + 8]);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int r = wn + nt * 8 + group, c = ks + tig * 2;
+        b[nt][0] = ld_pair(&Bs[r][c]);
+        b[nt][1] = ld_pair(&Bs[r][c + 8]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = m0 + wm + mt * 16 + group + (e >= 2 ? 8 : 0);
+        const int c = n0 + wn + nt * 8 + tig * 2 + (e & 1);
+        if (r < g.M && c < g.N) epi(r, c, acc[mt][nt][e]);
+      }
+}
+
+struct EpiBiasReluBf16 {  // C = bf16(relu(acc + bias[c]))
+  const float* bias;
+  __nv_bfloat16* C;
+  int ldc;
+  __device__ void operator()(int r, int c, float v) const {
+    v += bias[c];
+    C[int64_t(r) * ldc + c] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+  }
+};
+struct EpiBiasF32 {  // C = acc + bias[c]
+  const float* bias;
+  float* C;
+  int ldc;
+  __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v + bias[c]; }
+};
+struct EpiMaskBf16 {  // C = bf16(acc) where H > 0, else 0 (ReLU derivative, relu'(0) = 0)
+  const __nv_bfloat16* H;
+  __nv_bfloat16* C;
+  int ld;
+  __device__ void operator()(int r, int c, float v) const {
+    const int64_t i = int64_t(r) * ld + c;
+    C[i] = __bfloat162float(H[i]) > 0.f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(0.f);
+  }
+};
+struct EpiF32 {  // C = acc
+  float* C;
+  int ldc;
+  __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v; }
+};
+
+template <class Epi>
+int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
+  const dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM));
+  gemm_bf16_kernel<Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+// features = bf16(scale * mu)
+__global__ void to_bf16_kernel(const float* __restrict__ x, int64_t count, float scale,
+                               __nv_bfloat16* __restrict__ y) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = __float2bfloat16_rn(scale * x[i]);
+}
+
+// BCE with logits: dZ = (w+ y (sigmoid(z) - 1) + (1 - y) sigmoid(z)) / B, and the
+// summed loss (w+ y softplus(-z) + (1 - y) softplus(z)) / B into *loss.
+__global__ void bce_kernel(const float* __restrict__ Z, const float* __restrict__ Y,
+                           int64_t count, float inv_B, float pos_weight,
+                           __nv_bfloat16* __restrict__ dZ, float* __restrict__ loss) {
+  float part = 0.f;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float z = Z[i], y = Y[i];
+    const float sig = 1.f / (1.f + expf(-z));
+    dZ[i] = __float2bfloat16_rn((pos_weight * y * (sig - 1.f) + (1.f - y) * sig) * inv_B);
+    const float sp_pos = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));  // softplus(z)
+    const float sp_neg = sp_pos - z;                                // softplus(-z)
+    part += (pos_weight * y * sp_neg + (1.f - y) * sp_pos) * inv_B;
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
+}
+
+// db[n] = sum_b dY[b, n]
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dY, int B, int N,
+                                 float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += __bfloat162float(dY[int64_t(b) * N + n]);
+  db[n] = s;
+}
+
+// AdamW over all parameters (decoupled weight decay); refreshes the bf16 copy
+// of the weight matrices.
+struct AdamArgs {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t count;
+  float lr, beta1, beta2, eps, wd, c1, c2;  // c1 = 1/(1-beta1^t), c2 = 1/(1-beta2^t)
+  int64_t w_begin[3], w_end[3];             // weight-matrix ranges in p
+  __nv_bfloat16* wbf[3];                    // their bf16 copies
+};
+
+__global__ void adamw_kernel(const AdamArgs a) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < a.count;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float g = a.g[i];
+    const float m = a.beta1 * a.m[i] + (1.f - a.beta1) * g;
+    const float v = a.beta2 * a.v[i] + (1.f - a.beta2) * g * g;
+    a.m[i] = m;
+    a.v[i] = v;
+    const float p = a.p[i] - a.lr * ((m * a.c1) / (sqrtf(v * a.c2) + a.eps) + a.wd * a.p[i]);
+    a.p[i] = p;
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+      if (i >= a.w_begin[w] && i < a.w_end[w]) a.wbf[w][i - a.w_begin[w]] = __float2bfloat16_rn(p);
+  }
+}
+
+// Uniform(-bound, bound) initial weights from the SplitMix64 counter hash, zero
+// biases and optimiser moments.
+__global__ void init_kernel(float* __restrict__ p, int64_t count, uint64_t seed,
+                            const int64_t* __restrict__ seg_end, const float* __restrict__ bound,
+                            int nseg) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    int s = 0;
+    while (s < nseg - 1 && i >= seg_end[s]) ++s;
+    const uint64_t z = splitmix64_mix(seed + 0x9E3779B97F4A7C15ull * uint64_t(i + 1));
+    const float u = float(z >> 40) * (1.0f / 16777216.0f);  // [0, 1)
+    p[i] = bound[s] * (2.f * u - 1.f);
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* __restrict__ x, int64_t count,
+                                   __nv_bfloat16* __restrict__ y) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+unsigned grid_for(int64_t count, int threads) {
+  int64_t g = (count + threads - 1) / threads;
+  if (g > 4096) g = 4096;
+  return unsigned(g < 1 ? 1 : g);
+}
+
+}  // namespace
+}  // namespace kd
+
+struct kerdock_mlp_s {
+  int in = 0, hid = 0, out = 0, max_batch = 0;
+  int64_t off[7] = {};  // parameter offsets: W1, b1, W2, b2, W3, b3, end
+  int64_t count = 0;    // parameters
+  size_t state_bytes = 0, work_bytes = 0;
+  // state
+  float* master = nullptr;
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  __nv_bfloat16* wbf[3] = {};
+  float* loss = nullptr;
+  // work
+  __nv_bfloat16* X0 = nullptr;
+  __nv_bfloat16* H1 = nullptr;
+  __nv_bfloat16* H2 = nullptr;
+  float* Z = nullptr;
+  __nv_bfloat16* dZ = nullptr;
+  __nv_bfloat16* dH2 = nullptr;
+  __nv_bfloat16* dH1 = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  int64_t step = 0;
+};
+
+namespace {
+
+size_t a256(size_t v) { return (v + 255) / 256 * 256; }
+
+int mlp_forward_impl(kerdock_mlp_s* n, const float* feats, int B, float scale, float* logits) {
+  using namespace kd;
+  to_bf16_kernel<<<grid_for(int64_t(B) * n->in, 256), 256, 0, n->stream>>>(
+      feats, int64_t(B) * n->in, scale, n->X0);
+  KD_CUDA_TRY(cudaGetLastError());
+  GemmArgs g{};
+  // H1 = relu(X0 W1^T + b1)
+  g = GemmArgs{B, n->hid, n->in, n->X0, n->in, 1, n->wbf[0], n->in, 1};
+  int rc = gemm(g, EpiBiasReluBf16{n->master + n->off[1], n->H1, n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  // H2 = relu(H1 W2^T + b2)
+  g = GemmArgs{B, n->hid, n->hid, n->H1, n->hid, 1, n->wbf[1], n->hid, 1};
+  rc = gemm(g, EpiBiasReluBf16{n->master + n->off[3], n->H2, n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  // Z = H2 W3^T + b3
+  g = GemmArgs{B, n->out, n->hid, n->H2, n->hid, 1, n->wbf[2], n->hid, 1};
+  return gemm(g, EpiBiasF32{n->master + n->off[5], logits, n->out}, n->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int kerdock_mlp_create(kerdock_mlp_t* mlp, int32_t in_dim, int32_t hidden, int32_t out_dim,
+                       int32_t max_batch) {
+  if (mlp == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  *mlp = nullptr;
+  if (in_dim < 1 || hidden < 1 || out_dim < 1 || max_batch < 1) return KERDOCK_ERR_INVALID_ARG;
+  if (in_dim % 2 || hidden % 2 || out_dim % 2 || in_dim > 65536 || hidden > 65536 ||
+      out_dim > 65536 || max_batch > 1 << 20)
+    return KERDOCK_ERR_UNSUPPORTED;
+  auto* n = new (std::nothrow) kerdock_mlp_s();
+  if (n == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  n->in = in_dim;
+  n->hid = hidden;
+  n->out = out_dim;
+  n->max_batch = max_batch;
+  const int64_t sizes[6] = {int64_t(hidden) * in_dim, hidden, int64_t(hidden) * hidden,
+                            hidden, int64_t(out_dim) * hidden, out_dim};
+  n->off[0] = 0;
+  for (int i = 0; i < 6; ++i) n->off[i + 1] = n->off[i] + sizes[i];
+  n->count = n->off[6];
+  const size_t P = size_t(n->count);
+  n->state_bytes = 4 * a256(P * 4) + a256(size_t(sizes[0]) * 2) + a256(size_t(sizes[2]) * 2) +
+                   a256(size_t(sizes[4]) * 2) + 256;
+  const size_t B = size_t(max_batch);
+  n->work_bytes = a256(B * in_dim * 2) + 2 * a256(B * hidden * 2) + a256(B * out_dim * 4) +
+                  a256(B * out_dim * 2) + 2 * a256(B * hidden * 2);
+  *mlp = n;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_sizes(kerdock_mlp_t mlp, size_t* state_bytes, size_t* work_bytes,
+                      int64_t* param_count) {
+  if (mlp == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  if (state_bytes) *state_bytes = mlp->state_bytes;
+  if (work_bytes) *work_bytes = mlp->work_bytes;
+  if (param_count) *param_count = mlp->count;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_bind(kerdock_mlp_t mlp, void* state_dev, size_t state_bytes, void* work_dev,
+                     size_t work_bytes, void* stream) {
+  if (mlp == nullptr || state_dev == nullptr || work_dev == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  kerdock_mlp_s* n = mlp;
+  if (state_bytes < n->state_bytes || work_bytes < n->work_bytes) return KERDOCK_ERR_CAPACITY;
+  if ((reinterpret_cast<uintptr_t>(state_dev) & 255) || (reinterpret_cast<uintptr_t>(work_dev) & 255))
+    return KERDOCK_ERR_ALIGNMENT;
+  const size_t P = size_t(n->count);
+  char* s = static_cast<char*>(state_dev);
+  n->master = reinterpret_cast<float*>(s);
+  s += a256(P * 4);
+  n->grads = reinterpret_cast<float*>(s);
+  s += a256(P * 4);
+  n->m = reinterpret_cast<float*>(s);
+  s += a256(P * 4);
+  n->v = reinterpret_cast<float*>(s);
+  s += a256(P * 4);
+  for (int w = 0; w < 3; ++w) {
+    n->wbf[w] = reinterpret_cast<__nv_bfloat16*>(s);
+    s += a256(size_t(n->off[2 * w + 1] - n->off[2 * w]) * 2);
+  }
+  n->loss = reinterpret_cast<float*>(s);
+  const size_t B = size_t(n->max_batch);
+  char* w = static_cast<char*>(work_dev);
+  n->X0 = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256(B * n->in * 2);
+  n->H1 = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256(B * n->hid * 2);
+  n->H2 = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256(B * n->hid * 2);
+  n->Z = reinterpret_cast<float*>(w);
+  w += a256(B * n->out * 4);
+  n->dZ = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256(B * n->out * 2);
+  n->dH2 = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256(B * n->hid * 2);
+  n->dH1 = reinterpret_cast<__nv_bfloat16*>(w);
+  n->stream = static_cast<cudaStream_t>(stream);
+  n->bound = true;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_pointers(kerdock_mlp_t mlp, float** params, float** grads, int64_t* offsets) {
+  if (mlp == nullptr || !mlp->bound) return KERDOCK_ERR_NOT_BOUND;
+  if (params) *params = mlp->master;
+  if (grads) *grads = mlp->grads;
+  if (offsets)
+    for (int i = 0; i < 7; ++i) offsets[i] = mlp->off[i];
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_init(kerdock_mlp_t mlp, uint64_t seed) {
+  if (mlp == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  kerdock_mlp_s* n = mlp;
+  if (!n->bound) return KERDOCK_ERR_NOT_BOUND;
+  // U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases
+  int64_t seg_end[6];
+  float bound[6];
+  const int fan[3] = {n->in, n->hid, n->hid};
+  for (int i = 0; i < 6; ++i) {
+    seg_end[i] = n->off[i + 1];
+    bound[i] = (i % 2 == 0) ? 1.f / sqrtf(float(fan[i / 2])) : 0.f;
+  }
+  // the two small tables travel in the loss slot's neighbourhood: use the grads
+  // buffer (overwritten by every backward) as a staging area
+  int64_t* d_seg = reinterpret_cast<int64_t*>(n->grads);
+  float* d_bound = reinterpret_cast<float*>(d_seg + 8);
+  KD_CUDA_TRY(cudaMemcpyAsync(d_seg, seg_end, sizeof(seg_end), cudaMemcpyHostToDevice, n->stream));
+  KD_CUDA_TRY(cudaMemcpyAsync(d_bound, bound, sizeof(bound), cudaMemcpyHostToDevice, n->stream));
+  kd::init_kernel<<<kd::grid_for(n->count, 256), 256, 0, n->stream>>>(n->master, n->count, seed,
+                                                                       d_seg, d_bound, 6);
+  KD_CUDA_TRY(cudaGetLastError());
+  KD_CUDA_TRY(cudaMemsetAsync(n->m, 0, size_t(n->count) * 4, n->stream));
+  KD_CUDA_TRY(cudaMemsetAsync(n->v, 0, size_t(n->count) * 4, n->stream));
+  KD_CUDA_TRY(cudaStreamSynchronize(n->stream));  // the staging tables are host locals
+  for (int w = 0; w < 3; ++w) {
+    const int64_t cnt = n->off[2 * w + 1] - n->off[2 * w];
+    kd::f32_to_bf16_kernel<<<kd::grid_for(cnt, 256), 256, 0, n->stream>>>(
+        n->master + n->off[2 * w], cnt, n->wbf[w]);
+    KD_CUDA_TRY(cudaGetLastError());
+  }
+  n->step = 0;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_sync_weights(kerdock_mlp_t mlp) {
+  if (mlp == nullptr || !mlp->bound) return KERDOCK_ERR_NOT_BOUND;
+  for (int w = 0; w < 3; ++w) {
+    const int64_t cnt = mlp->off[2 * w + 1] - mlp->off[2 * w];
+    kd::f32_to_bf16_kernel<<<kd::grid_for(cnt, 256), 256, 0, mlp->stream>>>(
+        mlp->master + mlp->off[2 * w], cnt, mlp->wbf[w]);
+    KD_CUDA_TRY(cudaGetLastError());
+  }
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_forward(kerdock_mlp_t mlp, const float* feats, int32_t B, float feat_scale,
+                        float* logits) {
+  if (mlp == nullptr || feats == nullptr || logits == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  if (!mlp->bound) return KERDOCK_ERR_NOT_BOUND;
+  if (B < 1 || B > mlp->max_batch) return KERDOCK_ERR_CAPACITY;
+  return mlp_forward_impl(mlp, feats, B, feat_scale, logits);
+}
+
+int kerdock_mlp_backward(kerdock_mlp_t mlp, const float* feats, const float* labels, int32_t B,
+                         float feat_scale, float pos_weight) {
+  using namespace kd;
+  if (mlp == nullptr || feats == nullptr || labels == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  kerdock_mlp_s* n = mlp;
+  if (!n->bound) return KERDOCK_ERR_NOT_BOUND;
+  if (B < 1 || B > n->max_batch) return KERDOCK_ERR_CAPACITY;
+  int rc = mlp_forward_impl(n, feats, B, feat_scale, n->Z);
+  if (rc != KERDOCK_OK) return rc;
+  KD_CUDA_TRY(cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream));
+  const int64_t zc = int64_t(B) * n->out;
+  bce_kernel<<<grid_for(zc, 256), 256, 0, n->stream>>>(n->Z, labels, zc, 1.f / float(B),
+                                                        pos_weight, n->dZ, n->loss);
+  KD_CUDA_TRY(cudaGetLastError());
+  float* G = n->grads;
+  GemmArgs g{};
+  // dW3 = dZ^T H2, db3 = sum_b dZ
+  g = GemmArgs{n->out, n->hid, B, n->dZ, 1, n->out, n->H2, 1, n->hid};
+  rc = gemm(g, EpiF32{G + n->off[4], n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  bias_grad_kernel<<<(n->out + 255) / 256, 256, 0, n->stream>>>(n->dZ, B, n->out, G + n->off[5]);
+  // dH2 = (dZ W3) * [H2 > 0]
+  g = GemmArgs{B, n->hid, n->out, n->dZ, n->out, 1, n->wbf[2], 1, n->hid};
+  rc = gemm(g, EpiMaskBf16{n->H2, n->dH2, n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  // dW2 = dH2^T H1, db2
+  g = GemmArgs{n->hid, n->hid, B, n->dH2, 1, n->hid, n->H1, 1, n->hid};
+  rc = gemm(g, EpiF32{G + n->off[2], n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  bias_grad_kernel<<<(n->hid + 255) / 256, 256, 0, n->stream>>>(n->dH2, B, n->hid, G + n->off[3]);
+  // dH1 = (dH2 W2) * [H1 > 0]
+  g = GemmArgs{B, n->hid, n->hid, n->dH2, n->hid, 1, n->wbf[1], 1, n->hid};
+  rc = gemm(g, EpiMaskBf16{n->H1, n->dH1, n->hid}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  // dW1 = dH1^T X0, db1
+  g = GemmArgs{n->hid, n->in, B, n->dH1, 1, n->hid, n->X0, 1, n->in};
+  rc = gemm(g, EpiF32{G + n->off[0], n->in}, n->stream);
+  if (rc != KERDOCK_OK) return rc;
+  bias_grad_kernel<<<(n->hid + 255) / 256, 256, 0, n->stream>>>(n->dH1, B, n->hid, G + n->off[1]);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_loss(kerdock_mlp_t mlp, float* loss_host) {
+  if (mlp == nullptr || loss_host == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  if (!mlp->bound) return KERDOCK_ERR_NOT_BOUND;
+  KD_CUDA_TRY(cudaMemcpyAsync(loss_host, mlp->loss, sizeof(float), cudaMemcpyDeviceToHost,
+                              mlp->stream));
+  KD_CUDA_TRY(cudaStreamSynchronize(mlp->stream));
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_adamw(kerdock_mlp_t mlp, float lr, float beta1, float beta2, float eps,
+                      float weight_decay) {
+  if (mlp == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  kerdock_mlp_s* n = mlp;
+  if (!n->bound) return KERDOCK_ERR_NOT_BOUND;
+  n->step += 1;
+  kd::AdamArgs a{};
+  a.p = n->master;
+  a.g = n->grads;
+  a.m = n->m;
+  a.v = n->v;
+  a.count = n->count;
+  a.lr = lr;
+  a.beta1 = beta1;
+  a.beta2 = beta2;
+  a.eps = eps;
+  a.wd = weight_decay;
+  a.c1 = float(1.0 / (1.0 - std::pow(double(beta1), double(n->step))));
+  a.c2 = float(1.0 / (1.0 - std::pow(double(beta2), double(n->step))));
+  for (int w = 0; w < 3; ++w) {
+    a.w_begin[w] = n->off[2 * w];
+    a.w_end[w] = n->off[2 * w + 1];
+    a.wbf[w] = n->wbf[w];
+  }
+  kd::adamw_kernel<<<kd::grid_for(n->count, 256), 256, 0, n->stream>>>(a);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_destroy(kerdock_mlp_t mlp) {
+  delete mlp;
+  return KERDOCK_OK;
+}
+
+}  // extern "C"

@@ -329,6 +329,23 @@ int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_wor
   return KERDOCK_OK;
 }
 
+int kerdock_plan_clone(kerdock_plan_t* out, kerdock_plan_t src, int32_t J, int32_t K, int32_t S) {
+  if (out == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (src == nullptr || J < 1 || K < 1 || S < 1) return KERDOCK_ERR_INVALID_ARG;
+  if (K > kd::kMaxK || int64_t(J) * K > kd::kMaxN) return KERDOCK_ERR_UNSUPPORTED;
+  auto* h = new (std::nothrow) kerdock_plan_s();
+  if (h == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  h->p = src->p;  // shares the bound memory, stream, A and preprocessed state
+  h->p.J = J;
+  h->p.K = K;
+  h->p.S = int(S < h->p.m ? S : h->p.m);
+  h->p.N = int64_t(J) * K;
+  h->p.tuning = kd::Tuning{};
+  *out = h;
+  return KERDOCK_OK;
+}
+
 int kerdock_plan_destroy(kerdock_plan_t plan) {
   delete plan;
   return KERDOCK_OK;

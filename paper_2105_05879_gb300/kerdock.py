@@ -35,6 +35,10 @@ EXPORTED = [
     "kerdock_batch_workspace_bytes", "kerdock_batch_create", "kerdock_batch_launch",
     "kerdock_batch_set_tuning", "kerdock_batch_tune", "kerdock_batch_sync",
     "kerdock_batch_destroy", "kerdock_plan_set_tuning", "kerdock_plan_tune",
+    "kerdock_mlp_create", "kerdock_mlp_sizes", "kerdock_mlp_bind", "kerdock_mlp_pointers",
+    "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
+    "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
+    "kerdock_plan_clone",
 ]
 
 KERDOCK_BATCH_GRAPH = 1
@@ -115,6 +119,24 @@ def load_library(path=None):
                                              ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_float)]),
+        "kerdock_mlp_create": (ctypes.c_int, [ctypes.POINTER(P), c_i32, c_i32, c_i32, c_i32]),
+        "kerdock_mlp_sizes": (ctypes.c_int, [P, ctypes.POINTER(c_sz), ctypes.POINTER(c_sz),
+                                             ctypes.POINTER(c_i64)]),
+        "kerdock_mlp_bind": (ctypes.c_int, [P, c_vp, c_sz, c_vp, c_sz, c_vp]),
+        "kerdock_mlp_pointers": (ctypes.c_int, [P, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp),
+                                                ctypes.POINTER(c_i64)]),
+        "kerdock_mlp_sync_weights": (ctypes.c_int, [P]),
+        "kerdock_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "kerdock_mlp_forward": (ctypes.c_int, [P, c_vp, c_i32, ctypes.c_float, c_vp]),
+        "kerdock_mlp_backward": (ctypes.c_int, [P, c_vp, c_vp, c_i32, ctypes.c_float,
+                                                ctypes.c_float]),
+        "kerdock_mlp_loss": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float)]),
+        "kerdock_mlp_adamw": (ctypes.c_int, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float]),
+        "kerdock_mlp_destroy": (ctypes.c_int, [P]),
+        "kerdock_refine_scores": (ctypes.c_int, [P, c_vp, c_i64, c_i64, c_vp, c_i32,
+                                                 ctypes.c_float, c_i32, c_vp, c_vp, c_vp]),
+        "kerdock_plan_clone": (ctypes.c_int, [ctypes.POINTER(P), P, c_i32, c_i32, c_i32]),
         "kerdock_sync": (ctypes.c_int, [P]),
         "kerdock_debug_signs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32), c_sz]),
         "kerdock_plan_destroy": (ctypes.c_int, [P]),
@@ -237,6 +259,77 @@ def kerdock_plan_tune(plan, X_ptr, q, ldx, eps, seed, idx_ptr, val_ptr, cnt_ptr,
     return rk.value, cr.value, ms.value
 
 
+def kerdock_plan_clone(plan, J, K, S):
+    h = ctypes.c_void_p()
+    _check(load_library().kerdock_plan_clone(ctypes.byref(h), plan, J, K, S), "kerdock_plan_clone")
+    return h
+
+
+def kerdock_refine_scores(plan, X_ptr, q, ldx, scores_ptr, S, eps, flags, idx_ptr, val_ptr, cnt_ptr):
+    _check(load_library().kerdock_refine_scores(plan, X_ptr, q, ldx, scores_ptr, S, eps, flags,
+                                                idx_ptr, val_ptr, cnt_ptr), "kerdock_refine_scores")
+
+
+def kerdock_mlp_create(in_dim, hidden, out_dim, max_batch):
+    h = ctypes.c_void_p()
+    _check(load_library().kerdock_mlp_create(ctypes.byref(h), in_dim, hidden, out_dim, max_batch),
+           "kerdock_mlp_create")
+    return h
+
+
+def kerdock_mlp_sizes(mlp):
+    a, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+    _check(load_library().kerdock_mlp_sizes(mlp, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "kerdock_mlp_sizes")
+    return a.value, b.value, c.value
+
+
+def kerdock_mlp_bind(mlp, state_ptr, state_bytes, work_ptr, work_bytes, stream):
+    _check(load_library().kerdock_mlp_bind(mlp, state_ptr, state_bytes, work_ptr, work_bytes, stream),
+           "kerdock_mlp_bind")
+
+
+def kerdock_mlp_pointers(mlp):
+    p, g = ctypes.c_void_p(), ctypes.c_void_p()
+    off = (ctypes.c_int64 * 7)()
+    _check(load_library().kerdock_mlp_pointers(mlp, ctypes.byref(p), ctypes.byref(g), off),
+           "kerdock_mlp_pointers")
+    return p.value, g.value, list(off)
+
+
+def kerdock_mlp_sync_weights(mlp):
+    _check(load_library().kerdock_mlp_sync_weights(mlp), "kerdock_mlp_sync_weights")
+
+
+def kerdock_mlp_init(mlp, seed):
+    _check(load_library().kerdock_mlp_init(mlp, seed), "kerdock_mlp_init")
+
+
+def kerdock_mlp_forward(mlp, feats_ptr, B, scale, logits_ptr):
+    _check(load_library().kerdock_mlp_forward(mlp, feats_ptr, B, scale, logits_ptr),
+           "kerdock_mlp_forward")
+
+
+def kerdock_mlp_backward(mlp, feats_ptr, labels_ptr, B, scale, pos_weight):
+    _check(load_library().kerdock_mlp_backward(mlp, feats_ptr, labels_ptr, B, scale, pos_weight),
+           "kerdock_mlp_backward")
+
+
+def kerdock_mlp_loss(mlp):
+    v = ctypes.c_float()
+    _check(load_library().kerdock_mlp_loss(mlp, ctypes.byref(v)), "kerdock_mlp_loss")
+    return v.value
+
+
+def kerdock_mlp_adamw(mlp, lr, beta1, beta2, eps, wd):
+    _check(load_library().kerdock_mlp_adamw(mlp, lr, beta1, beta2, eps, wd), "kerdock_mlp_adamw")
+
+
+def kerdock_mlp_destroy(mlp):
+    if mlp is not None:
+        load_library().kerdock_mlp_destroy(mlp)
+
+
 def kerdock_sync(plan):
     _check(load_library().kerdock_sync(plan), "kerdock_sync")
 
@@ -356,6 +449,30 @@ class KerdockPlan:
     def sync(self):
         kerdock_sync(self.handle)
 
+    def clone(self, J, K, S):
+        """A plan over the same representation with other (J, K, S)."""
+        c = KerdockPlan.__new__(KerdockPlan)
+        c.torch, c.dtype, c.device = self.torch, self.dtype, self.device
+        c.handle = kerdock_plan_clone(self.handle, J, K, S)
+        c.info = kerdock_plan_info(c.handle)
+        c.repr, c.table, c._stream, c.A, c._ws = self.repr, self.table, self._stream, self.A, None
+        c._parent = self
+        return c
+
+    def refine_scores(self, X, scores, S, eps, flags=0, out=None):
+        """Top-S of scores (q x m), exact A_S x, threshold (Algorithm 1's last step)."""
+        t = self.torch
+        q = X.shape[0]
+        if out is None:
+            out = (t.empty((q, S), dtype=t.int32, device=self.device),
+                   t.empty((q, S), dtype=t.float32, device=self.device),
+                   t.empty((q,), dtype=t.int32, device=self.device))
+        idx, val, cnt = out
+        self._sync_stream()
+        kerdock_refine_scores(self.handle, X.data_ptr(), q, X.stride(0), scores.data_ptr(), S,
+                              float(eps), flags, idx.data_ptr(), val.data_ptr(), cnt.data_ptr())
+        return idx, val, cnt
+
     def signs(self):
         return kerdock_debug_signs(self.handle)
 
@@ -428,6 +545,73 @@ class KerdockBatch:
     def close(self):
         if getattr(self, "handle", None) is not None:
             kerdock_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class KerdockMLP:
+    """The learned-proposal network with PyTorch-allocated device buffers."""
+
+    def __init__(self, in_dim, hidden, out_dim, max_batch, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.handle = kerdock_mlp_create(in_dim, hidden, out_dim, max_batch)
+        sb, wb, self.count = kerdock_mlp_sizes(self.handle)
+        self.state = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        self.work = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        kerdock_mlp_bind(self.handle, self.state.data_ptr(), sb, self.work.data_ptr(), wb,
+                         s.cuda_stream)
+        self.dims = (in_dim, hidden, out_dim)
+        self.max_batch = max_batch
+        p, g, self.offsets = kerdock_mlp_pointers(self.handle)
+        self.params = self._view(p)
+        self.grads = self._view(g)
+
+    def _view(self, ptr):
+        # a float32 tensor over the library's parameter/gradient block
+        t = self.torch
+        base = self.state.data_ptr()
+        off = (ptr - base) // 4
+        return self.state.view(t.float32)[off:off + self.count]
+
+    def tensors(self, flat):
+        i, h, o = self.dims
+        shapes = [(h, i), (h,), (h, h), (h,), (o, h), (o,)]
+        return [flat[self.offsets[k]:self.offsets[k + 1]].view(*shapes[k]) for k in range(6)]
+
+    def init(self, seed):
+        kerdock_mlp_init(self.handle, seed)
+
+    def forward(self, feats, scale, out=None):
+        t = self.torch
+        B = feats.shape[0]
+        out = out if out is not None else t.empty((B, self.dims[2]), dtype=t.float32, device=self.device)
+        kerdock_mlp_forward(self.handle, feats.data_ptr(), B, float(scale), out.data_ptr())
+        return out
+
+    def backward(self, feats, labels, scale, pos_weight):
+        kerdock_mlp_backward(self.handle, feats.data_ptr(), labels.data_ptr(), feats.shape[0],
+                             float(scale), float(pos_weight))
+
+    def loss(self):
+        return kerdock_mlp_loss(self.handle)
+
+    def adamw(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+        kerdock_mlp_adamw(self.handle, lr, beta1, beta2, eps, wd)
+
+    def sync_weights(self):
+        kerdock_mlp_sync_weights(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            kerdock_mlp_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
