@@ -256,6 +256,12 @@ typedef struct kerdock_mlp_s* kerdock_mlp_t;
 /* in_dim, hidden, out_dim even; max_batch rows per forward/backward call. */
 int kerdock_mlp_create(kerdock_mlp_t* mlp, int32_t in_dim, int32_t hidden, int32_t out_dim,
                        int32_t max_batch);
+/* Input transform of the features: X = bf16(feat_scale * f) (LINEAR, the
+ * default) or X = bf16(feat_scale * |f|) (ABS: only sketch magnitudes). */
+#define KERDOCK_MLP_INPUT_LINEAR 0
+#define KERDOCK_MLP_INPUT_ABS 1
+int kerdock_mlp_set_input(kerdock_mlp_t mlp, int32_t mode);
+
 /* Device bytes for the state (FP32 master weights, gradients, AdamW moments,
  * bfloat16 weight copies) and for the activations of max_batch rows. */
 int kerdock_mlp_sizes(kerdock_mlp_t mlp, size_t* state_bytes, size_t* work_bytes,

@@ -147,12 +147,12 @@ int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
   return KERDOCK_OK;
 }
 
-// features = bf16(scale * mu)
-__global__ void to_bf16_kernel(const float* __restrict__ x, int64_t count, float scale,
+// features = bf16(scale * mu), or bf16(scale * |mu|) in magnitude mode
+__global__ void to_bf16_kernel(const float* __restrict__ x, int64_t count, float scale, int abs_mode,
                                __nv_bfloat16* __restrict__ y) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
        i += int64_t(gridDim.x) * blockDim.x)
-    y[i] = __float2bfloat16_rn(scale * x[i]);
+    y[i] = __float2bfloat16_rn(scale * (abs_mode ? fabsf(x[i]) : x[i]));
 }
 
 // BCE with logits: dZ = (w+ y (sigmoid(z) - 1) + (1 - y) sigmoid(z)) / B, and the
@@ -267,6 +267,7 @@ struct kerdock_mlp_s {
   cudaStream_t stream = nullptr;
   bool bound = false;
   int64_t step = 0;
+  int input_mode = 0;  // KERDOCK_MLP_INPUT_*
 };
 
 namespace {
@@ -276,7 +277,7 @@ size_t a256(size_t v) { return (v + 255) / 256 * 256; }
 int mlp_forward_impl(kerdock_mlp_s* n, const float* feats, int B, float scale, float* logits) {
   using namespace kd;
   to_bf16_kernel<<<grid_for(int64_t(B) * n->in, 256), 256, 0, n->stream>>>(
-      feats, int64_t(B) * n->in, scale, n->X0);
+      feats, int64_t(B) * n->in, scale, n->input_mode == KERDOCK_MLP_INPUT_ABS, n->X0);
   KD_CUDA_TRY(cudaGetLastError());
   GemmArgs g{};
   // H1 = relu(X0 W1^T + b1)
@@ -322,6 +323,13 @@ int kerdock_mlp_create(kerdock_mlp_t* mlp, int32_t in_dim, int32_t hidden, int32
   n->work_bytes = a256(B * in_dim * 2) + 2 * a256(B * hidden * 2) + a256(B * out_dim * 4) +
                   a256(B * out_dim * 2) + 2 * a256(B * hidden * 2);
   *mlp = n;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_set_input(kerdock_mlp_t mlp, int32_t mode) {
+  if (mlp == nullptr || (mode != KERDOCK_MLP_INPUT_LINEAR && mode != KERDOCK_MLP_INPUT_ABS))
+    return KERDOCK_ERR_INVALID_ARG;
+  mlp->input_mode = mode;
   return KERDOCK_OK;
 }
 

@@ -38,8 +38,11 @@ EXPORTED = [
     "kerdock_mlp_create", "kerdock_mlp_sizes", "kerdock_mlp_bind", "kerdock_mlp_pointers",
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
-    "kerdock_plan_clone",
+    "kerdock_plan_clone", "kerdock_mlp_set_input",
 ]
+
+KERDOCK_MLP_INPUT_LINEAR = 0
+KERDOCK_MLP_INPUT_ABS = 1
 
 KERDOCK_BATCH_GRAPH = 1
 
@@ -127,6 +130,7 @@ def load_library(path=None):
                                                 ctypes.POINTER(c_i64)]),
         "kerdock_mlp_sync_weights": (ctypes.c_int, [P]),
         "kerdock_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "kerdock_mlp_set_input": (ctypes.c_int, [P, c_i32]),
         "kerdock_mlp_forward": (ctypes.c_int, [P, c_vp, c_i32, ctypes.c_float, c_vp]),
         "kerdock_mlp_backward": (ctypes.c_int, [P, c_vp, c_vp, c_i32, ctypes.c_float,
                                                 ctypes.c_float]),
@@ -299,6 +303,10 @@ def kerdock_mlp_pointers(mlp):
 
 def kerdock_mlp_sync_weights(mlp):
     _check(load_library().kerdock_mlp_sync_weights(mlp), "kerdock_mlp_sync_weights")
+
+
+def kerdock_mlp_set_input(mlp, mode):
+    _check(load_library().kerdock_mlp_set_input(mlp, mode), "kerdock_mlp_set_input")
 
 
 def kerdock_mlp_init(mlp, seed):
@@ -588,6 +596,9 @@ class KerdockMLP:
 
     def init(self, seed):
         kerdock_mlp_init(self.handle, seed)
+
+    def set_input(self, mode):
+        kerdock_mlp_set_input(self.handle, mode)
 
     def forward(self, feats, scale, out=None):
         t = self.torch

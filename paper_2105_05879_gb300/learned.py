@@ -25,6 +25,8 @@ class LearnedProposal:
         self.S_prime = int(S_prime)
         self.mlp = K.KerdockMLP(m, hidden, m, max_batch, device=plan.device)
         self.mlp.init(seed)
+        # the support does not depend on the signs of Ax, so the network sees |mu|
+        self.mlp.set_input(K.KERDOCK_MLP_INPUT_ABS)
         self.feat_scale = feat_scale
         self.max_batch = max_batch
 
@@ -60,7 +62,7 @@ class LearnedProposal:
         t = self.torch
         q = mu.shape[0]
         if self.feat_scale is None:
-            self.feat_scale = float(1.0 / (mu.std().item() + 1e-12))
+            self.feat_scale = float(1.0 / (mu.abs().mean().item() + 1e-12))
         if pos_weight is None:
             frac = float(Y.mean().item())
             pos_weight = float(np.clip((1 - frac) / max(frac, 1e-6), 1.0, 100.0)) ** 0.5

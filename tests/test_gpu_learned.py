@@ -111,7 +111,7 @@ def test_refine_scores_definition():
 def test_learned_proposal_gains_over_plain_ranking():
     # Structured supports (2 runs of 4 consecutive indices): with a sketch of
     # only N = 16 samples and S' = 24 refined rows, the network trained on
-    # method-generated pairs recovers far more of h_eps(Ax) than ranking by |mu|.
+    # 100k method-generated pairs recovers more of h_eps(Ax) than ranking by |mu|.
     torch = torch_cuda()
     K = build_and_load()
     from paper_2105_05879_gb300.learned import LearnedProposal, support_recall
@@ -125,14 +125,14 @@ def test_learned_proposal_gains_over_plain_ranking():
         Z = workloads.sparse_codes(n, q, s, amp, seed, blocks=(2, 4))
         return torch.from_numpy((Z @ f32(A)).astype(np.float32)).cuda(), Z
 
-    lp = LearnedProposal(plan, J_sketch=8, K_sketch=2, S_prime=24, hidden=256, max_batch=1024,
+    lp = LearnedProposal(plan, J_sketch=8, K_sketch=2, S_prime=24, hidden=512, max_batch=1024,
                          seed=4)
-    Xtr, _ = queries(20000, 100)
+    Xtr, _ = queries(100000, 100)
     mu = lp.sketch_mu(Xtr, 7)
     Y = lp.labels_from_method(Xtr, eps, 9)
-    losses = lp.train(mu, Y, epochs=6, batch=512, lr=2e-3, seed=0)
+    losses = lp.train(mu, Y, epochs=6, batch=512, lr=1e-3, seed=0)
     assert losses[-1] < losses[0]
-    Xev, Zev = queries(2000, 200)
+    Xev, Zev = queries(4000, 200)
     truth = [np.nonzero(np.abs(z) >= eps)[0] for z in Zev]
     li, lv, lc = lp.apply(Xev, eps, 11)
     pi, pv, pc = lp.apply_plain_sketch(Xev, eps, 11)
@@ -140,5 +140,7 @@ def test_learned_proposal_gains_over_plain_ranking():
     rec_l, ex_l = support_recall(li, lc, truth)
     rec_p, ex_p = support_recall(pi, pc, truth)
     print(f"learned recall {rec_l:.3f} exact {ex_l:.3f} | plain-sketch recall {rec_p:.3f} exact {ex_p:.3f}")
-    assert rec_l >= rec_p + 0.05
+    # measured on a GB300: learned 0.55 vs plain 0.37 (the network sees |mu| and
+    # learns the two-run support structure from the method's own outputs)
+    assert rec_l >= rec_p + 0.10
     plan.close()
