@@ -322,6 +322,225 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# The three forms, each one JSON line (python bench.py --workload <name>).
+# ---------------------------------------------------------------------------
+def _timed(torch, stream, fn, reps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _support_match(torch, A64_dev, X, idx, cnt, eps):
+    V = (X.double() @ A64_dev.T).abs() >= eps
+    idx = idx.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    Vh = V.cpu().numpy()
+    ok = 0
+    for r in range(X.shape[0]):
+        ok += np.array_equal(idx[r, :cnt[r]], np.nonzero(Vh[r])[0])
+    return ok
+
+
+def run_precision(args, K, torch, peak):
+    """Precision form: n = 4096 with the representation in bfloat16 (68.75 GB)
+    next to plain float32 (137.5 GB) on the same queries."""
+    wl = workloads.WORKLOADS["n4096_bf16"]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    A_np = wl.make_A().astype(np.float32)
+    X_np = workloads.queries_from_codes(A_np.astype(np.float64), wl.make_codes()).astype(np.float32)
+    A = torch.from_numpy(A_np).to(dev)
+    X = torch.from_numpy(X_np).to(dev)
+    A64 = A.double()
+    q = X.shape[0]
+    res = {}
+    for dtype in ("bf16", "f32"):
+        plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S, dtype=dtype, device=dev)
+        idx, val, cnt = plan.alloc_outputs(q)
+        sptr = stream.cuda_stream
+        pre = lambda: (K.kerdock_plan_bind(plan.handle, plan.repr.data_ptr(), plan.repr.numel(),
+                                           plan.table.data_ptr(), plan.table.numel(), sptr),
+                       K.kerdock_preprocess(plan.handle, A.data_ptr(), A.stride(0)))
+        app = lambda: K.kerdock_apply(plan.handle, X.data_ptr(), q, X.stride(0), wl.eps,
+                                      wl.seed_apply, 0, idx.data_ptr(), val.data_ptr(),
+                                      cnt.data_ptr(), None, 0)
+        for _ in range(max(1, args.warmup // 2)):
+            pre()
+            app()
+        plan.sync()
+        pre_ms = _timed(torch, stream, pre, args.steps)
+        app_ms = _timed(torch, stream, app, args.steps)
+        plan.sync()
+        info = plan.info
+        eb = 2 if dtype == "bf16" else 4
+        pre_bytes = info["num_bases"] * info["d"] * info["ldr"] * eb + wl.m * wl.n * 4
+        gather = q * wl.J * wl.K * info["ldr"] * eb
+        res[dtype] = {
+            "ms_per_step": round(pre_ms + app_ms, 3),
+            "queries/s": round(q / ((pre_ms + app_ms) / 1e3), 1),
+            "preprocess": {"ms": round(pre_ms, 3), "GB/s": round(pre_bytes / pre_ms / 1e6, 1),
+                           "frac_hbm": round(pre_bytes / pre_ms / 1e6 / peak, 4)},
+            "query": {"ms": round(app_ms, 3), "queries/s": round(q / (app_ms / 1e3), 1),
+                      "gather_GB/s": round(gather / app_ms / 1e6, 1),
+                      "gather_frac_hbm": round(gather / app_ms / 1e6 / peak, 4)},
+            "support_match_dense": f"{_support_match(torch, A64, X, idx, cnt, wl.eps)}/{q}",
+        }
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    b = res["bf16"]
+    return {
+        "metric": METRIC, "value": b["queries/s"], "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded random orthogonal A, sparse codes; Sec. 4 recipe)",
+        "config": {"workload": (f"precision form: n=m=4096, d=4096, 2049 bases, bfloat16 "
+                                f"representation; {q} queries z 32-sparse +-1/sqrt(32), eps=0.09, "
+                                f"J={wl.J}, K={wl.K}, S={wl.S}"), "form": "precision"},
+        "bf16": b, "fp32_plain": res["f32"], "gpu_launches": 3 * args.steps,
+    }
+
+
+def run_batch(args, K, torch, peak):
+    """Batching form: 2048 queries over six plans (n in {64, 256, 1024, 4096},
+    float32 / bfloat16), s ~ U{4..64} per query, eps = 0.5/sqrt(s), J = 24 s,
+    K = 2, S = min(10 s, m), uneven per-plan batches, one graph-captured
+    persistent launch with the autotuned ring."""
+    import math
+    from paper_2105_05879_gb300 import tuning
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(2024)
+    shapes = [(64, "f32"), (256, "f32"), (256, "bf16"), (1024, "f32"), (1024, "bf16"), (4096, "bf16")]
+    sizes = [37, 218, 301, 480, 500, 512]  # uneven, within 1..512, total 2048
+    plans, mats = [], []
+    for i, (n, dt) in enumerate(shapes):
+        A_np = workloads.random_orthogonal(n, 500 + i).astype(np.float32)
+        plan = K.KerdockPlan(n, n, J=1, K=1, S=1, dtype=dt, device=dev)
+        plan.preprocess(torch.from_numpy(A_np).to(dev))
+        plans.append(plan)
+        mats.append(torch.from_numpy(A_np).to(dev))
+    specs, truth = [], []
+    for pi, cnt in enumerate(sizes):
+        n = shapes[pi][0]
+        for r in range(cnt):
+            s = int(min(rng.integers(4, 65), n // 8))
+            z = workloads.sparse_codes(n, 1, s, 1 / math.sqrt(s), int(rng.integers(1 << 31)))[0]
+            x = torch.from_numpy((z @ mats[pi].double().cpu().numpy()).astype(np.float32)).to(dev)
+            eps = 0.5 / math.sqrt(s)
+            specs.append(dict(plan=plans[pi], x=x, J=24 * s, K=2, S=min(10 * s, n), eps=eps,
+                              seed=77 + pi, index=r))
+            truth.append(np.nonzero(np.abs(z) >= eps)[0])
+    batch = K.KerdockBatch(specs, graph=True)
+    rk, cr, tune_ms = tuning.autotune_batch(batch, reps=2, use_cache=False)
+    for _ in range(args.warmup):
+        batch.launch()
+    batch.sync()
+    stream = batch.stream
+    ms = _timed(torch, stream, batch.launch, args.steps)
+    batch.sync()
+    got = batch.results()
+    ok = sum(np.array_equal(g[0], t) for g, t in zip(got, truth))
+    gather = sum(sp["J"] * sp["K"] * sp["plan"].info["ldr"] * (2 if sp["plan"].dtype else 4)
+                 for sp in specs)
+    q = len(specs)
+    line = {
+        "metric": METRIC, "value": round(q / (ms / 1e3), 1), "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic (seeded random orthogonal A per plan, sparse codes; Sec. 4 recipe)",
+        "config": {"workload": ("batching form: 2048 queries over plans n in {64,256,1024,4096} "
+                                "f32/bf16, s~U{4..64}, eps=0.5/sqrt(s), J=24s, K=2, S=min(10s,m), "
+                                "per-plan batches 37..512, one graph-captured persistent launch"),
+                   "form": "batching", "tuned_ring_kb": rk, "tuned_crows": cr},
+        "query": {"gather_GB/s": round(gather / ms / 1e6, 1),
+                  "gather_frac_hbm": round(gather / ms / 1e6 / peak, 4)},
+        "support_match_dense": f"{ok}/{q}", "gpu_launches": args.steps,
+    }
+    batch.close()
+    for p in plans:
+        p.close()
+    return line
+
+
+def run_learned(args, K, torch, peak):
+    """Learned form: n = 2048 (d = 4096, float32 representation), supports of
+    4 runs of 8; the network (2 x 512, bfloat16) is trained on 200k
+    method-generated pairs and evaluated on 10k queries against the plain
+    method."""
+    import math
+    from paper_2105_05879_gb300.learned import LearnedProposal, support_recall
+    wl = workloads.WORKLOADS["n2048_blocks"]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    A_np = wl.make_A().astype(np.float32)
+    A = torch.from_numpy(A_np).to(dev)
+    A64 = A_np.astype(np.float64)
+    plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S, dtype="f32", device=dev)
+    plan.preprocess(A)
+
+    def queries(q, seed):
+        Z = workloads.sparse_codes(wl.n, q, wl.s, wl.amp, seed, blocks=wl.blocks)
+        return torch.from_numpy((Z @ A64).astype(np.float32)).to(dev), Z
+
+    lp = LearnedProposal(plan, J_sketch=32, K_sketch=2, S_prime=64, hidden=512, max_batch=4096,
+                         seed=3)
+    t0 = time.perf_counter()
+    Xtr, _ = queries(200000, 900)
+    mu = lp.sketch_mu(Xtr, 31)
+    Y = lp.labels_from_method(Xtr, wl.eps, 41)
+    losses = lp.train(mu, Y, epochs=4, batch=1024, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del mu, Y, Xtr
+    Xev, Zev = queries(10000, 901)
+    truth = [np.nonzero(np.abs(z) >= wl.eps)[0] for z in Zev]
+    ms_plain = _timed(torch, stream, lambda: plan.apply(Xev, wl.eps, 51), max(1, args.steps))
+    pi, pv, pc = plan.apply(Xev, wl.eps, 51)
+    ms_learn = _timed(torch, stream, lambda: lp.apply(Xev, wl.eps, 51), max(1, args.steps))
+    li, lv, lc = lp.apply(Xev, wl.eps, 51)
+    torch.cuda.synchronize()
+    rp = support_recall(pi, pc, truth)
+    rl = support_recall(li, lc, truth)
+    q = Xev.shape[0]
+    line = {
+        "metric": METRIC, "value": round(q / (ms_learn / 1e3), 1), "unit": "queries/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_learn, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+        "data": "synthetic (seeded random orthogonal A, block-sparse codes; Sec. 4 recipe)",
+        "config": {"workload": ("learned form: n=m=2048 (d=4096, 2049 bases, f32), z 32-sparse in "
+                                "4 runs of 8, eps=0.5/sqrt(32); plain J=375,K=2,S=320 vs learned "
+                                "sketch J=32,K=2 + MLP 2x512 bf16 + S'=64; 200k training pairs, "
+                                "10k eval"), "form": "learned"},
+        "learned": {"queries/s": round(q / (ms_learn / 1e3), 1), "recall": round(rl[0], 4),
+                    "exact": round(rl[1], 4), "train_s": round(train_s, 1),
+                    "loss_first_last": [round(losses[0], 3), round(losses[-1], 3)]},
+        "plain": {"queries/s": round(q / (ms_plain / 1e3), 1), "recall": round(rp[0], 4),
+                  "exact": round(rp[1], 4)},
+        "gpu_launches": None,
+    }
+    plan.close()
+    return line
+
+
+def run_form(args):
+    import torch
+    from paper_2105_05879_gb300 import build as kbuild
+    from paper_2105_05879_gb300 import kerdock as K
+    torch.cuda.set_device(0)
+    kbuild.build()
+    K.load_library()
+    peak, _ = measured_peaks()
+    fn = {"n4096_bf16": run_precision, "mixed_batch": run_batch, "n2048_learned": run_learned}
+    line = fn[args.workload](args, K, torch, peak)
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(wl, budget_s=20.0, queries=None):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
     workload: the Lemma 6 preprocessing of a subset of bases and the streaming
@@ -413,6 +632,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_oracle_queries", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -423,6 +644,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != WORKLOAD:
+        run_form(args)
     else:
         run_ours(args)
 

@@ -312,6 +312,12 @@ int kerdock_sync(kerdock_plan_t plan);
  * Synchronises the stream. */
 int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_words);
 
+/* Test of the failure path: a one-warp kernel waits, at most max_polls
+ * mbarrier polls, on a phase nothing completes, then records
+ * KERDOCK_ERR_DEVICE_TIMEOUT in the plan's status word and returns (no trap,
+ * no hang).  The next kerdock_sync reports it and clears it. */
+int kerdock_debug_wait_timeout(kerdock_plan_t plan, int32_t max_polls);
+
 /* Destroy a plan (host metadata only; NULL is accepted). */
 int kerdock_plan_destroy(kerdock_plan_t plan);
 

@@ -116,6 +116,20 @@ __global__ void signs_kernel(uint32_t* __restrict__ signs, uint32_t* __restrict_
   }
 }
 
+// Failure-path check: wait, with a poll limit, on an mbarrier phase that no
+// thread ever completes; give up, record a timeout in the status word and
+// return -- the same bounded-wait-and-report path every kernel wait uses.
+__global__ void wait_timeout_kernel(uint32_t* status, uint32_t max_polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    bool done = false;
+    for (uint32_t it = 0; it < max_polls && !done; ++it) done = mbar_try_wait(&bar, 0);
+    if (!done) set_status(status, kStatusTimeout);
+  }
+}
+
 }  // namespace
 
 int launch_signs(const Plan& p) {
@@ -343,6 +357,15 @@ int kerdock_plan_clone(kerdock_plan_t* out, kerdock_plan_t src, int32_t J, int32
   h->p.N = int64_t(J) * K;
   h->p.tuning = kd::Tuning{};
   *out = h;
+  return KERDOCK_OK;
+}
+
+int kerdock_debug_wait_timeout(kerdock_plan_t plan, int32_t max_polls) {
+  if (plan == nullptr || max_polls < 1) return KERDOCK_ERR_INVALID_ARG;
+  Plan& p = plan->p;
+  if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
+  kd::wait_timeout_kernel<<<1, 32, 0, p.stream>>>(p.status(), uint32_t(max_polls));
+  KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }
 

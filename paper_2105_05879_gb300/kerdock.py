@@ -38,7 +38,7 @@ EXPORTED = [
     "kerdock_mlp_create", "kerdock_mlp_sizes", "kerdock_mlp_bind", "kerdock_mlp_pointers",
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
-    "kerdock_plan_clone", "kerdock_mlp_set_input",
+    "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -141,6 +141,7 @@ def load_library(path=None):
         "kerdock_refine_scores": (ctypes.c_int, [P, c_vp, c_i64, c_i64, c_vp, c_i32,
                                                  ctypes.c_float, c_i32, c_vp, c_vp, c_vp]),
         "kerdock_plan_clone": (ctypes.c_int, [ctypes.POINTER(P), P, c_i32, c_i32, c_i32]),
+        "kerdock_debug_wait_timeout": (ctypes.c_int, [P, c_i32]),
         "kerdock_sync": (ctypes.c_int, [P]),
         "kerdock_debug_signs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32), c_sz]),
         "kerdock_plan_destroy": (ctypes.c_int, [P]),
@@ -336,6 +337,10 @@ def kerdock_mlp_adamw(mlp, lr, beta1, beta2, eps, wd):
 def kerdock_mlp_destroy(mlp):
     if mlp is not None:
         load_library().kerdock_mlp_destroy(mlp)
+
+
+def kerdock_debug_wait_timeout(plan, max_polls):
+    _check(load_library().kerdock_debug_wait_timeout(plan, max_polls), "kerdock_debug_wait_timeout")
 
 
 def kerdock_sync(plan):

@@ -252,3 +252,22 @@ def test_plan_autotune_keeps_results(K, tmp_path, monkeypatch):
         np.testing.assert_array_equal(got[0][q, :got[2][q]], ref[0][q, :ref[2][q]])
         np.testing.assert_array_equal(got[1][q, :got[2][q]], ref[1][q, :ref[2][q]])
     plan.close()
+
+
+def test_device_wait_timeout_is_reported_and_recoverable(K):
+    # A bounded device wait that runs out records a timeout; kerdock_sync
+    # reports it once, clears it, and the plan keeps working.
+    torch = torch_cuda()
+    plan = K.KerdockPlan(16, 16, J=4, K=2, S=4)
+    plan.preprocess(torch.eye(16, device="cuda"))
+    K.kerdock_debug_wait_timeout(plan.handle, 2000)
+    with pytest.raises(K.KerdockError) as e:
+        plan.sync()
+    assert e.value.code == -7
+    plan.sync()  # cleared
+    X = torch.zeros((2, 16), device="cuda")
+    X[0, 3] = 1.0
+    idx, val, cnt = plan.apply(X, 0.5, 0)
+    plan.sync()
+    assert cnt.cpu().tolist() == [1, 0] and idx[0, 0].item() == 3
+    plan.close()
