@@ -256,9 +256,10 @@ def test_plan_autotune_keeps_results(K, tmp_path, monkeypatch):
 
 def test_device_wait_timeout_is_reported_and_recoverable(K):
     # A bounded device wait that runs out records a timeout; kerdock_sync
-    # reports it once, clears it, and the plan keeps working.
+    # reports it once, clears it, and the plan keeps working (S = m: every row
+    # is refined, so the output is exact whatever the sketch).
     torch = torch_cuda()
-    plan = K.KerdockPlan(16, 16, J=4, K=2, S=4)
+    plan = K.KerdockPlan(16, 16, J=4, K=2, S=16)
     plan.preprocess(torch.eye(16, device="cuda"))
     K.kerdock_debug_wait_timeout(plan.handle, 2000)
     with pytest.raises(K.KerdockError) as e:
