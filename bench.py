@@ -488,13 +488,13 @@ def run_learned(args, K, torch, peak):
         Z = workloads.sparse_codes(wl.n, q, wl.s, wl.amp, seed, blocks=wl.blocks)
         return torch.from_numpy((Z @ A64).astype(np.float32)).to(dev), Z
 
-    lp = LearnedProposal(plan, J_sketch=32, K_sketch=2, S_prime=64, hidden=512, max_batch=4096,
-                         seed=3)
+    lp = LearnedProposal(plan, J_sketch=128, K_sketch=2, S_prime=96, hidden=512, max_batch=4096,
+                         seed=3, residual=True)
     t0 = time.perf_counter()
     Xtr, _ = queries(200000, 900)
     mu = lp.sketch_mu(Xtr, 31)
     Y = lp.labels_from_method(Xtr, wl.eps, 41)
-    losses = lp.train(mu, Y, epochs=4, batch=1024, lr=1e-3, seed=0)
+    losses = lp.train(mu, Y, epochs=10, batch=1024, lr=1e-3, seed=0)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del mu, Y, Xtr
@@ -504,9 +504,12 @@ def run_learned(args, K, torch, peak):
     pi, pv, pc = plan.apply(Xev, wl.eps, 51)
     ms_learn = _timed(torch, stream, lambda: lp.apply(Xev, wl.eps, 51), max(1, args.steps))
     li, lv, lc = lp.apply(Xev, wl.eps, 51)
+    ms_sk = _timed(torch, stream, lambda: lp.apply_plain_sketch(Xev, wl.eps, 51), max(1, args.steps))
+    si, sv, sc = lp.apply_plain_sketch(Xev, wl.eps, 51)
     torch.cuda.synchronize()
     rp = support_recall(pi, pc, truth)
     rl = support_recall(li, lc, truth)
+    rs = support_recall(si, sc, truth)
     q = Xev.shape[0]
     line = {
         "metric": METRIC, "value": round(q / (ms_learn / 1e3), 1), "unit": "queries/s",
@@ -515,13 +518,16 @@ def run_learned(args, K, torch, peak):
         "data": "synthetic (seeded random orthogonal A, block-sparse codes; Sec. 4 recipe)",
         "config": {"workload": ("learned form: n=m=2048 (d=4096, 2049 bases, f32), z 32-sparse in "
                                 "4 runs of 8, eps=0.5/sqrt(32); plain J=375,K=2,S=320 vs learned "
-                                "sketch J=32,K=2 + MLP 2x512 bf16 + S'=64; 200k training pairs, "
-                                "10k eval"), "form": "learned"},
+                                "sketch J=128,K=2 + residual MLP 2x512 bf16 (input |mu|) + S'=96; "
+                                "200k training pairs, 10 epochs, 10k eval"), "form": "learned"},
         "learned": {"queries/s": round(q / (ms_learn / 1e3), 1), "recall": round(rl[0], 4),
                     "exact": round(rl[1], 4), "train_s": round(train_s, 1),
                     "loss_first_last": [round(losses[0], 3), round(losses[-1], 3)]},
         "plain": {"queries/s": round(q / (ms_plain / 1e3), 1), "recall": round(rp[0], 4),
                   "exact": round(rp[1], 4)},
+        "plain_same_budget": {"queries/s": round(q / (ms_sk / 1e3), 1), "recall": round(rs[0], 4),
+                              "exact": round(rs[1], 4),
+                              "note": "top-S' of |mu| from the same sketch, no network"},
         "gpu_launches": None,
     }
     plan.close()

@@ -248,7 +248,7 @@ int kerdock_plan_tune(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_
  * perceptron in bfloat16 (FP32 accumulation on tensor cores) maps a cheap
  * sketch mu (a plan with small J, K) to one score per output index; the top
  * scores replace the top-|mu| candidates of Algorithm 1's refinement step.
- *   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3,
+ *   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3 (+ skip X),
  * trained with binary cross-entropy on logits (positive weight w+) and AdamW.
  * ------------------------------------------------------------------------ */
 typedef struct kerdock_mlp_s* kerdock_mlp_t;
@@ -261,6 +261,9 @@ int kerdock_mlp_create(kerdock_mlp_t* mlp, int32_t in_dim, int32_t hidden, int32
 #define KERDOCK_MLP_INPUT_LINEAR 0
 #define KERDOCK_MLP_INPUT_ABS 1
 int kerdock_mlp_set_input(kerdock_mlp_t mlp, int32_t mode);
+/* Residual logits Z = H2 W3^T + b3 + skip * X (in_dim == out_dim): with W3,
+ * b3 zero the network starts from the plain ranking by the features. */
+int kerdock_mlp_set_skip(kerdock_mlp_t mlp, float skip);
 
 /* Device bytes for the state (FP32 master weights, gradients, AdamW moments,
  * bfloat16 weight copies) and for the activations of max_batch rows. */

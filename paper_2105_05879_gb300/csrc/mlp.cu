@@ -118,11 +118,16 @@ struct EpiBiasReluBf16 {  // C = bf16(relu(acc + bias[c]))
     C[int64_t(r) * ldc + c] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
   }
 };
-struct EpiBiasF32 {  // C = acc + bias[c]
+struct EpiBiasF32 {  // C = acc + bias[c] (+ skip * X[r, c] when skip != 0: residual logits)
   const float* bias;
   float* C;
   int ldc;
-  __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v + bias[c]; }
+  const __nv_bfloat16* X;
+  float skip;
+  __device__ void operator()(int r, int c, float v) const {
+    const int64_t i = int64_t(r) * ldc + c;
+    C[i] = v + bias[c] + (skip != 0.f ? skip * __bfloat162float(X[i]) : 0.f);
+  }
 };
 struct EpiMaskBf16 {  // C = bf16(acc) where H > 0, else 0 (ReLU derivative, relu'(0) = 0)
   const __nv_bfloat16* H;
@@ -268,6 +273,7 @@ struct kerdock_mlp_s {
   bool bound = false;
   int64_t step = 0;
   int input_mode = 0;  // KERDOCK_MLP_INPUT_*
+  float skip = 0.f;    // residual logits Z += skip * X (needs in_dim == out_dim)
 };
 
 namespace {
@@ -290,7 +296,7 @@ int mlp_forward_impl(kerdock_mlp_s* n, const float* feats, int B, float scale, f
   if (rc != KERDOCK_OK) return rc;
   // Z = H2 W3^T + b3
   g = GemmArgs{B, n->out, n->hid, n->H2, n->hid, 1, n->wbf[2], n->hid, 1};
-  return gemm(g, EpiBiasF32{n->master + n->off[5], logits, n->out}, n->stream);
+  return gemm(g, EpiBiasF32{n->master + n->off[5], logits, n->out, n->X0, n->skip}, n->stream);
 }
 
 }  // namespace
@@ -330,6 +336,13 @@ int kerdock_mlp_set_input(kerdock_mlp_t mlp, int32_t mode) {
   if (mlp == nullptr || (mode != KERDOCK_MLP_INPUT_LINEAR && mode != KERDOCK_MLP_INPUT_ABS))
     return KERDOCK_ERR_INVALID_ARG;
   mlp->input_mode = mode;
+  return KERDOCK_OK;
+}
+
+int kerdock_mlp_set_skip(kerdock_mlp_t mlp, float skip) {
+  if (mlp == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  if (skip != 0.f && mlp->in != mlp->out) return KERDOCK_ERR_INVALID_ARG;
+  mlp->skip = skip;
   return KERDOCK_OK;
 }
 

@@ -39,6 +39,7 @@ EXPORTED = [
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
+    "kerdock_mlp_set_skip",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -131,6 +132,7 @@ def load_library(path=None):
         "kerdock_mlp_sync_weights": (ctypes.c_int, [P]),
         "kerdock_mlp_init": (ctypes.c_int, [P, ctypes.c_uint64]),
         "kerdock_mlp_set_input": (ctypes.c_int, [P, c_i32]),
+        "kerdock_mlp_set_skip": (ctypes.c_int, [P, ctypes.c_float]),
         "kerdock_mlp_forward": (ctypes.c_int, [P, c_vp, c_i32, ctypes.c_float, c_vp]),
         "kerdock_mlp_backward": (ctypes.c_int, [P, c_vp, c_vp, c_i32, ctypes.c_float,
                                                 ctypes.c_float]),
@@ -308,6 +310,10 @@ def kerdock_mlp_sync_weights(mlp):
 
 def kerdock_mlp_set_input(mlp, mode):
     _check(load_library().kerdock_mlp_set_input(mlp, mode), "kerdock_mlp_set_input")
+
+
+def kerdock_mlp_set_skip(mlp, skip):
+    _check(load_library().kerdock_mlp_set_skip(mlp, skip), "kerdock_mlp_set_skip")
 
 
 def kerdock_mlp_init(mlp, seed):
@@ -604,6 +610,9 @@ class KerdockMLP:
 
     def set_input(self, mode):
         kerdock_mlp_set_input(self.handle, mode)
+
+    def set_skip(self, skip):
+        kerdock_mlp_set_skip(self.handle, float(skip))
 
     def forward(self, feats, scale, out=None):
         t = self.torch

@@ -17,7 +17,7 @@ from . import kerdock as K
 
 class LearnedProposal:
     def __init__(self, plan, J_sketch, K_sketch, S_prime, hidden=512, max_batch=1024, seed=1,
-                 feat_scale=None):
+                 feat_scale=None, residual=False):
         self.plan = plan
         self.torch = plan.torch
         m = plan.info["m"]
@@ -27,6 +27,14 @@ class LearnedProposal:
         self.mlp.init(seed)
         # the support does not depend on the signs of Ax, so the network sees |mu|
         self.mlp.set_input(K.KERDOCK_MLP_INPUT_ABS)
+        if residual:
+            # logits = MLP(|mu|) + |mu| with the last layer zeroed: training starts
+            # from the plain top-|mu| ranking and learns corrections to it
+            self.mlp.set_skip(1.0)
+            W3, b3 = self.mlp.tensors(self.mlp.params)[4:6]
+            W3.zero_()
+            b3.zero_()
+            self.mlp.sync_weights()
         self.feat_scale = feat_scale
         self.max_batch = max_batch
 
