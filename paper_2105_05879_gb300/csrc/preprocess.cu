@@ -82,13 +82,18 @@ __device__ __forceinline__ void fwht_across(float2 (&v)[NH]) {
 
 template <typename T>
 __device__ __forceinline__ void store_pair(T* dst, float2 v);
+// Streaming (evict-first) stores: the representation is written once here and
+// read back only by later queries, long after it has left L2.
 template <>
 __device__ __forceinline__ void store_pair<float>(float* dst, float2 v) {
-  *reinterpret_cast<float2*>(dst) = v;
+  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(v.x), "f"(v.y) : "memory");
 }
 template <>
 __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* dst, float2 v) {
-  *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(v.x, v.y);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  asm volatile("st.global.cs.b32 [%0], %1;" ::"l"(dst),
+               "r"(*reinterpret_cast<const uint32_t*>(&h))
+               : "memory");
 }
 
 // Per-size configuration.  A CTA owns TI = 16 rows; D = NW * 2^LH * RG with
@@ -121,8 +126,38 @@ struct PreArgs {
   void* R;
   int64_t ldr;
   int64_t num_tiles;
-  int64_t items;  // num_tiles * (d/2 + 1)
+  int64_t group;  // G: consecutive CTAs (or clusters) that sweep the bases in step
 };
+
+// Work split.  Tiles are taken in groups of G adjacent tiles; the G CTAs (or
+// clusters) of a group own one tile each and walk the same range of (tile
+// group, basis) items, so that at any time the group writes G adjacent row
+// segments of every output row R[b][w][.] and L2 receives whole 128-byte
+// lines instead of isolated 32- or 64-byte pieces.  Within a CTA the items are
+// tile-major, so the A tile in shared memory is reloaded only when the tile
+// changes.
+struct ItemRange {
+  int64_t beg, end, slot;
+};
+__device__ __forceinline__ ItemRange item_range(int64_t unit, int64_t units, int64_t group,
+                                                int64_t num_tiles, int64_t B) {
+  const int64_t ngrp = units / group, grp = unit / group;
+  const int64_t ntg = (num_tiles + group - 1) / group;
+  const int64_t items = ntg * B;
+  const int64_t per = items / ngrp, rem = items % ngrp;
+  ItemRange r;
+  r.beg = grp * per + (grp < rem ? grp : rem);
+  r.end = r.beg + per + (grp < rem ? 1 : 0);
+  r.slot = unit % group;
+  // a slot past the last tile has nothing to do in the last tile group, which
+  // is the tail of the item space
+  if ((ntg - 1) * group + r.slot >= num_tiles) {
+    const int64_t lim = (ntg - 1) * B;
+    if (r.end > lim) r.end = lim;
+    if (r.beg > r.end) r.beg = r.end;
+  }
+  return r;
+}
 
 template <int LOG_D, typename OutT>
 __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
@@ -146,9 +181,8 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   const int rp = lane & 7, wsel = lane >> 3;             // phase 2: row pair, w selector
   const float sqrt_d = float(1 << (LOG_D / 2));
 
-  const int64_t per = a.items / gridDim.x, rem = a.items % gridDim.x;
-  const int64_t beg = blockIdx.x * per + (blockIdx.x < rem ? blockIdx.x : rem);
-  const int64_t end = beg + per + (blockIdx.x < rem ? 1 : 0);
+  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  const int64_t beg = ir.beg, end = ir.end;
   int64_t cur_tile = -1;
 
   // Sign words of the first item's basis; later ones are prefetched one item ahead.
@@ -164,8 +198,9 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   }
 
   for (int64_t item = beg; item < end; ++item) {
-    const int64_t t = item / B;
-    const int b = int(item - t * B);
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
     const int64_t i0 = t * kTileRows;
     const bool ident = b == D / 2;
     uint32_t* mk = Msk + (item & 1) * MSTRIDE;
@@ -294,15 +329,14 @@ __global__ void __launch_bounds__(Big::THREADS, 1)
   const int rp = lane & 15, wsel = lane >> 4;
   const float sqrt_d = 64.f;
 
-  const int64_t ncl = gridDim.x / C::CL, cid = blockIdx.x / C::CL;
-  const int64_t per = a.items / ncl, rem = a.items % ncl;
-  const int64_t beg = cid * per + (cid < rem ? cid : rem);
-  const int64_t end = beg + per + (cid < rem ? 1 : 0);
+  const ItemRange ir =
+      item_range(blockIdx.x / C::CL, gridDim.x / C::CL, a.group, a.num_tiles, B);
   int64_t cur_tile = -1;
 
-  for (int64_t item = beg; item < end; ++item) {
-    const int64_t t = item / B;
-    const int b = int(item - t * B);
+  for (int64_t item = ir.beg; item < ir.end; ++item) {
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
     const int64_t i0 = t * C::TI;
     const bool ident = b == C::D / 2;
     cluster.sync();  // every CTA of the cluster is done reading the exchange buffers
@@ -378,6 +412,13 @@ __global__ void __launch_bounds__(Big::THREADS, 1)
   cluster.sync();  // keep this CTA's shared memory alive until the others are done
 }
 
+// Largest power of two <= limit and <= num_tiles (the tile group size G).
+int64_t pick_group(int64_t num_tiles, int64_t limit) {
+  int64_t g = 1;
+  while (g * 2 <= limit && g * 2 <= num_tiles) g *= 2;
+  return g;
+}
+
 template <typename OutT>
 int launch_d4096(const Plan& p) {
   using C = Big;
@@ -394,7 +435,6 @@ int launch_d4096(const Plan& p) {
   a.R = p.repr;
   a.ldr = p.ldr;
   a.num_tiles = (p.ldr + C::TI - 1) / C::TI;
-  a.items = a.num_tiles * p.B;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -410,9 +450,13 @@ int launch_d4096(const Plan& p) {
   int clusters = 0;
   KD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
   if (clusters < 1) return KERDOCK_ERR_UNSUPPORTED;
-  int64_t ncl = clusters;
-  if (ncl > a.items) ncl = a.items;
-  cfg.gridDim = dim3(unsigned(ncl * C::CL));
+  // groups of up to 4 clusters on adjacent 32-row tiles: 4 x 64 B = two whole
+  // 128-byte lines per output row for bfloat16
+  a.group = pick_group(a.num_tiles, clusters < 4 ? clusters : 4);
+  int64_t ngrp = clusters / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  cfg.gridDim = dim3(unsigned(ngrp * a.group * C::CL));
   KD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
   return KERDOCK_OK;
 }
@@ -436,10 +480,13 @@ int launch_small(const Plan& p) {
   a.R = p.repr;
   a.ldr = p.ldr;
   a.num_tiles = (p.ldr + kTileRows - 1) / kTileRows;
-  a.items = a.num_tiles * p.B;
-  int64_t grid = int64_t(p.num_sms) * occ;
-  if (grid > a.items) grid = a.items;
-  kern<<<unsigned(grid), C::THREADS, C::SMEM, p.stream>>>(a);
+  // groups of up to 16 CTAs on adjacent 16-row tiles (256 consecutive rows)
+  a.group = pick_group(a.num_tiles, 16);
+  int64_t ngrp = int64_t(p.num_sms) * occ / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  if (ngrp < 1) ngrp = 1;
+  kern<<<unsigned(ngrp * a.group), C::THREADS, C::SMEM, p.stream>>>(a);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }
