@@ -112,8 +112,7 @@ struct PreCfg {
   static constexpr int AST = D + 4;            // A-tile row stride (floats): conflict-free LDS.128
   static constexpr int XST = RGP * kTileRows + 16;  // floats per source in X (bank shift 16)
   static constexpr int THREADS = NW * 32;
-  static constexpr size_t SMEM = size_t(kTileRows) * AST * 4 + size_t(SRC) * XST * 4 +
-                                 2 * size_t(D > 32 ? D : 32) * 4;
+  static constexpr size_t SMEM = size_t(kTileRows) * AST * 4 + size_t(SRC) * XST * 4;
   static_assert(WPS >= 1, "phase 2 needs at least one w per thread");
   static_assert(RG >= 4, "vector loads need 4 registers");
 };
@@ -165,13 +164,11 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   using C = PreCfg<LOG_D>;
   constexpr int D = C::D, RG = C::RG, RGP = C::RGP, AST = C::AST, SRC = C::SRC;
   constexpr int XST = C::XST;
-  constexpr int MPT = (D + C::THREADS - 1) / C::THREADS;  // sign masks per thread
+  constexpr int NWD = RG >= 32 ? RG / 32 : 1;  // sign words per phase-1 thread
   constexpr int64_t B = D / 2 + 1;
   extern __shared__ __align__(16) float smem[];
   float* At = smem;                                 // [16][AST]
   float* X = smem + size_t(kTileRows) * AST;        // [SRC][XST]: [w][row] per source
-  uint32_t* Msk = reinterpret_cast<uint32_t*>(X + size_t(SRC) * XST);  // [2][max(D,32)]
-  constexpr int MSTRIDE = D > 32 ? D : 32;
   OutT* R = static_cast<OutT*>(a.R);
   const int lane = threadIdx.x & 31;
   const int g = threadIdx.x >> 5;
@@ -185,26 +182,13 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   const int64_t beg = ir.beg, end = ir.end;
   int64_t cur_tile = -1;
 
-  // Sign words of the first item's basis; later ones are prefetched one item ahead.
-  uint32_t words[MPT];
-  {
-    const int b0 = int(beg % B);
-    const uint32_t* srow = a.signs + int64_t(b0 < D / 2 ? b0 : 0) * a.sign_words;
-#pragma unroll
-    for (int c = 0; c < MPT; ++c) {
-      const int p = threadIdx.x + c * C::THREADS;
-      words[c] = p < D ? __ldg(srow + (p >> 5)) : 0u;
-    }
-  }
-
   for (int64_t item = beg; item < end; ++item) {
     const int64_t tg = item / B;
     const int b = int(item - tg * B);
     const int64_t t = tg * a.group + ir.slot;
     const int64_t i0 = t * kTileRows;
     const bool ident = b == D / 2;
-    uint32_t* mk = Msk + (item & 1) * MSTRIDE;
-    __syncthreads();  // everyone is done with the previous item's tile, exchange and masks
+    __syncthreads();  // everyone is done with the previous item's tile and exchange
     if (t != cur_tile) {
       for (int idx = threadIdx.x; idx < kTileRows * D; idx += C::THREADS) {
         const int i = idx / D, p = idx % D;
@@ -214,34 +198,38 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
       }
       cur_tile = t;
     }
+    // Sign bits of this thread's p range [src*RG, (src+1)*RG) (step (i) of
+    // Lemma 6), shifted down to bit 0 when RG < 32.
+    uint32_t wcur[NWD];
+    {
+      const uint32_t* srow = a.signs + int64_t(b < D / 2 ? b : 0) * a.sign_words;
+      if (RG >= 32) {
 #pragma unroll
-    for (int c = 0; c < MPT; ++c) {  // step (i) of Lemma 6 as float sign masks
-      const int p = threadIdx.x + c * C::THREADS;
-      if (p < D) mk[p] = ((words[c] >> (p & 31)) & 1u) << 31;
-    }
-    if (item + 1 < end) {  // prefetch the next item's sign words
-      const int bn = int((item + 1) % B);
-      const uint32_t* srow = a.signs + int64_t(bn < D / 2 ? bn : 0) * a.sign_words;
-#pragma unroll
-      for (int c = 0; c < MPT; ++c) {
-        const int p = threadIdx.x + c * C::THREADS;
-        words[c] = p < D ? __ldg(srow + (p >> 5)) : 0u;
+        for (int c = 0; c < NWD; ++c) wcur[c] = p1 ? __ldg(srow + src * NWD + c) : 0u;
+      } else {
+        const int p0 = src * RG;
+        wcur[0] = p1 ? __ldg(srow + (p0 >> 5)) >> (p0 & 31) : 0u;
       }
     }
     __syncthreads();
 
-    // Phase 1: lane = (row, half), registers = p in [src*RG, (src+1)*RG) as pairs.
+    // Phase 1: lane = (row, half), registers = p in [src*RG, (src+1)*RG) as
+    // pairs; the sign flip XORs bit r of the thread's sign words into the
+    // float sign bit.
     float2 v[RG / 2];
     if (p1) {
 #pragma unroll
       for (int r = 0; r < RG; r += 4) {
         float4 q = *reinterpret_cast<const float4*>(&At[row * AST + src * RG + r]);
         if (!ident) {
-          const uint4 m4 = *reinterpret_cast<const uint4*>(&mk[src * RG + r]);
-          q.x = __uint_as_float(__float_as_uint(q.x) ^ m4.x);
-          q.y = __uint_as_float(__float_as_uint(q.y) ^ m4.y);
-          q.z = __uint_as_float(__float_as_uint(q.z) ^ m4.z);
-          q.w = __uint_as_float(__float_as_uint(q.w) ^ m4.w);
+          uint32_t f[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            f[e] = (wcur[(r + e) >> 5] << (31 - ((r + e) & 31))) & 0x80000000u;
+          q.x = __uint_as_float(__float_as_uint(q.x) ^ f[0]);
+          q.y = __uint_as_float(__float_as_uint(q.y) ^ f[1]);
+          q.z = __uint_as_float(__float_as_uint(q.z) ^ f[2]);
+          q.w = __uint_as_float(__float_as_uint(q.w) ^ f[3]);
         }
         v[r / 2] = make_float2(q.x, q.y);
         v[r / 2 + 1] = make_float2(q.z, q.w);
@@ -277,11 +265,10 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
         }
         const int64_t orow = i0 + 2 * rp;
         if (orow < a.ldr) {
+          // output w = h * RG + part * RGP + wl for source h
+          OutT* rb = R + (int64_t(b) * D + part * RGP + wl) * a.ldr + orow;
 #pragma unroll
-          for (int h = 0; h < SRC; ++h) {
-            const int64_t w = int64_t(h) * RG + part * RGP + wl;
-            store_pair<OutT>(R + (int64_t(b) * D + w) * a.ldr + orow, y[h]);
-          }
+          for (int h = 0; h < SRC; ++h) store_pair<OutT>(rb + int64_t(h) * RG * a.ldr, y[h]);
         }
       }
     }
