@@ -1,0 +1,82 @@
+"""The multi-rank host logic of bench.py on CPU: two gloo ranks.
+
+The GPU job shards independent query batches over ranks (weak scaling, no
+data-path collective); the only cross-rank steps are the timing barrier and
+the max over ranks of the step time.  These tests run that logic as two CPU
+processes on the gloo backend.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w, r, local = bench.dist_setup()
+    assert (w, r, local) == (world, rank, rank)
+    # each rank's step time differs; every rank must see the slowest one
+    step_ms = 1.0 + 0.5 * rank
+    got = bench.max_over_ranks(step_ms, world)
+    # shard of the n = 64 workload: its own queries and sample stream
+    wl = workloads.WORKLOADS["n64"]
+    shard = bench.rank_shard(wl, rank)
+    codes = wl.make_codes(offset_seed=shard["codes_offset"])
+    dist.barrier()
+    np.savez(os.path.join(out_dir, f"rank{rank}.npz"), got=got, codes=codes,
+             seed_apply=shard["seed_apply"])
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_and_disjoint_shards(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    r0 = np.load(tmp_path / "rank0.npz")
+    r1 = np.load(tmp_path / "rank1.npz")
+    # max over ranks: both ranks report the slower rank's time
+    assert float(r0["got"]) == pytest.approx(1.5)
+    assert float(r1["got"]) == pytest.approx(1.5)
+    # the two ranks answer different queries with different sample streams
+    assert int(r0["seed_apply"]) != int(r1["seed_apply"])
+    assert r0["codes"].shape == r1["codes"].shape
+    assert not np.array_equal(r0["codes"], r1["codes"])
+    s0 = [tuple(np.nonzero(c)[0]) for c in r0["codes"]]
+    s1 = [tuple(np.nonzero(c)[0]) for c in r1["codes"]]
+    assert s0 != s1
+
+
+def test_job_rate_counts_all_ranks():
+    import bench
+    # 1000 queries per rank in 2 ms on the slowest of 4 ranks
+    assert bench.job_rate(4, 1000, 2.0) == pytest.approx(2.0e6)
+    assert bench.job_rate(1, 1000, 2.0) == pytest.approx(5.0e5)
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(3.25, 1) == 3.25
+    wl = __import__("workloads").WORKLOADS["n1024"]
+    # rank 0 keeps the workload's own seeds (the single-GPU bench line)
+    sh = bench.rank_shard(wl, 0)
+    assert sh["codes_offset"] == 0 and sh["seed_apply"] == wl.seed_apply
