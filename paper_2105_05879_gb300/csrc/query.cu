@@ -121,17 +121,20 @@ __device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v)
 // (-1)^{(w >> 5).t}, both folded into that word.  Four samples are processed
 // together so that their loads, sums and warp reductions overlap.  x comes
 // from registers (XREG, n <= 1024: xr[t] = x_{32t+L}) or from shared memory.
-template <bool XREG>
-__device__ __forceinline__ void kerdock_coefficients4(const uint32_t* __restrict__ tsigns,
-                                                      int64_t tstride, const uint32_t (&ell)[4],
-                                                      int kbits, uint32_t dmask, int groups,
-                                                      int lane, const float (&xr)[32],
-                                                      const float* xs, float (&c)[4]) {
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  uint32_t whi[4], pl[4], wmask[4];
-  const uint32_t* rows[4];
+template <bool XREG, int NS>
+__device__ __forceinline__ void kerdock_coefficients(const uint32_t* __restrict__ tsigns,
+                                                     int64_t tstride, const uint32_t (&ell)[4],
+                                                     int kbits, uint32_t dmask, int groups,
+                                                     int lane, const float (&xr)[32],
+                                                     const float* xs, float (&c)[4]) {
+  // d <= 4096: at most four 1024-point groups; x in registers means n <= 1024
+  constexpr int kMaxGroups = XREG ? 1 : 4;
+  float part[NS];
+  uint32_t whi[NS], pl[NS], wmask[NS];
+  const uint32_t* rows[NS];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
+  for (int s = 0; s < NS; ++s) {
+    part[s] = 0.f;
     const uint32_t w = ell[s] & dmask;
     whi[s] = w >> 5;
     pl[s] = __popc(w & 31u & uint32_t(lane)) & 1u;
@@ -141,29 +144,34 @@ __device__ __forceinline__ void kerdock_coefficients4(const uint32_t* __restrict
     const uint32_t bmax = (dmask + 1u) / 2u - 1u;
     rows[s] = tsigns + int64_t(b < bmax ? b : bmax) * tstride;
   }
-  for (int g = 0; g < groups; ++g) {
-    uint32_t F[4];
+  // every group's sign words are requested before the first is used
+  uint32_t F[kMaxGroups][NS];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) F[s] = __ldg(rows[s] + (g << 5) + lane);
+  for (int g = 0; g < kMaxGroups; ++g)
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      F[s] ^= wmask[s];
-      if ((__popc(whi[s] & uint32_t(g << 5)) & 1u) ^ pl[s]) F[s] = ~F[s];
+    for (int s = 0; s < NS; ++s) F[g][s] = g < groups ? __ldg(rows[s] + (g << 5) + lane) : 0u;
+#pragma unroll
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (g >= groups) break;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      F[g][s] ^= wmask[s];
+      if ((__popc(whi[s] & uint32_t(g << 5)) & 1u) ^ pl[s]) F[g][s] = ~F[g][s];
     }
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
       const float xv = XREG ? xr[t] : xs[((g << 5) + t) * 32 + lane];
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-        part[s] += __uint_as_float(__float_as_uint(xv) ^ ((F[s] << (31 - t)) & 0x80000000u));
+      for (int s = 0; s < NS; ++s)
+        part[s] += __uint_as_float(__float_as_uint(xv) ^ ((F[g][s] << (31 - t)) & 0x80000000u));
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int s = 0; s < 4; ++s) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
+    for (int s = 0; s < NS; ++s) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) c[s] = part[s];
+  for (int s = 0; s < 4; ++s) c[s] = s < NS ? part[s] : 0.f;
 }
 
 struct Shared {
@@ -370,7 +378,13 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
 #pragma unroll
     for (int s2 = 0; s2 < 4; ++s2) ell[s2] = __shfl_sync(0xffffffffu, my_ell, s2 < cnt ? s2 : 0);
     float c[4];
-    kerdock_coefficients4<XREG>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
+    // a chunk holds CR samples: compute exactly those (CR is uniform per launch)
+    if (CR == 4)
+      kerdock_coefficients<XREG, 4>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
+    else if (CR == 2)
+      kerdock_coefficients<XREG, 2>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
+    else
+      kerdock_coefficients<XREG, 1>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
     // the gather warps must be done with this chunk's previous samples
     if (st.cc >= nchunk && !wait_phase(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg.status))
       return false;
@@ -641,7 +655,14 @@ __device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& 
     }
     named_barrier_sync(kFinalBarrier, kFinalThreads);
 
-    // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.
+    // a8: exact refinement v_i = a_i^T x, four rows per warp in flight.  All S
+    // rows are first requested into L2 by bulk prefetches (one instruction per
+    // row, no registers held), so the dot products below mostly hit L2.
+    if (qd.a_vec4) {
+      const uint32_t rbytes = uint32_t(qd.n) * 4u;
+      for (int r = ft; r < qd.S; r += kFinalThreads)
+        bulk_prefetch_l2(qd.A + int64_t(sel[r]) * qd.lda, rbytes);
+    }
     for (int r0 = fw * 4; r0 < qd.S; r0 += kFinalWarps * 4) {
       float racc[4] = {0.f, 0.f, 0.f, 0.f};
       const float* arow[4];

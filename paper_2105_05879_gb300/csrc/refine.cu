@@ -138,6 +138,10 @@ __global__ void __launch_bounds__(kRThreads) score_refine_kernel(const RefineArg
       }
     }
     __syncthreads();
+    if (a.a_vec4) {  // all S rows requested into L2 up front (no registers held)
+      const uint32_t rbytes = uint32_t(a.n) * 4u;
+      for (int r = tid; r < a.S; r += kRThreads) bulk_prefetch_l2(a.A + int64_t(sel[r]) * a.lda, rbytes);
+    }
     const float* x = a.X + q * a.ldx;
     const bool xv4 = a.a_vec4 && (a.ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
     for (int r0 = warp * 4; r0 < a.S; r0 += kRWarps * 4) {
