@@ -392,9 +392,11 @@ def run_precision(args, K, torch, peak):
         pre = lambda: (K.kerdock_plan_bind(plan.handle, plan.repr.data_ptr(), plan.repr.numel(),
                                            plan.table.data_ptr(), plan.table.numel(), sptr),
                        K.kerdock_preprocess(plan.handle, A.data_ptr(), A.stride(0)))
+        ws = plan.workspace(q)
+        wsp, wsb = (ws.data_ptr(), ws.numel()) if ws is not None else (None, 0)
         app = lambda: K.kerdock_apply(plan.handle, X.data_ptr(), q, X.stride(0), wl.eps,
                                       wl.seed_apply, 0, idx.data_ptr(), val.data_ptr(),
-                                      cnt.data_ptr(), None, 0)
+                                      cnt.data_ptr(), wsp, wsb)
         for _ in range(max(1, args.warmup // 2)):
             pre()
             app()

@@ -35,51 +35,75 @@
 namespace kd {
 namespace {
 
-constexpr int kCoefWarps = 3;
-constexpr int kGatherWarps = 8;
+// Warp roles: warp 0 produces, warps [1, 1 + CW) compute coefficients,
+// warps [1 + CW, 12) gather and warps [12, 16) finalize.  A coefficient costs n
+// sign-adds and a gathered row m multiply-adds, so the best split follows n/m:
+// measured on GB300 with m = n = 4096 (bfloat16), CW = 3 took 17.3 ms for 4096
+// queries against 19.3 ms (CW = 4) and 20.0 ms (CW = 5), while with m = 256,
+// n = 4096 CW = 5 was 1.7x faster than CW = 3.  The library's workloads have
+// m = n, so both constants are 3; the split stays a template parameter.
 constexpr int kFinalWarps = 4;
 constexpr int kFirstCoefWarp = 1;
-constexpr int kFirstGatherWarp = kFirstCoefWarp + kCoefWarps;
-constexpr int kFirstFinalWarp = kFirstGatherWarp + kGatherWarps;
+constexpr int kFirstFinalWarp = 12;
 constexpr int kWarps = kFirstFinalWarp + kFinalWarps;  // 16
 constexpr int kThreads = kWarps * 32;                   // 512
-constexpr int kGatherThreads = kGatherWarps * 32;
 constexpr int kFinalThreads = kFinalWarps * 32;
+constexpr int kCoefWarpsSmall = 3;  // n <= 1024
+constexpr int kCoefWarpsLarge = 3;  // n > 1024
+template <int CW>
+struct Roles {
+  static constexpr int kCoefWarps = CW;
+  static constexpr int kFirstGatherWarp = kFirstCoefWarp + CW;
+  static constexpr int kGatherWarps = kFirstFinalWarp - kFirstGatherWarp;
+  static constexpr int kGatherThreads = kGatherWarps * 32;
+};
 constexpr int kMaxSlots = 64;  // ring rows
 constexpr int kMaxChunks = 64;
-constexpr int kMinChunks = 4;  // > kCoefWarps: each coefficient warp steps kCoefWarps chunks
+// > every CW: each coefficient warp steps CW chunks and starts at chunk cw < CW
+constexpr int kMinChunks =
+    (kCoefWarpsSmall > kCoefWarpsLarge ? kCoefWarpsSmall : kCoefWarpsLarge) + 1;
 constexpr int kXBufs = 3;
 constexpr int kMBufs = 2;
 constexpr int kFinalBarrier = 1;  // named barrier id of the finalizer warps
 constexpr size_t kSmemBudget = 227 * 1024 - 4096;  // dynamic bytes (static ~3 KB)
 constexpr size_t kRingCap = 160 * 1024;
-constexpr size_t kMeansSmemMax = 64 * 1024;
+constexpr size_t kMeansSmemMax = 32 * 1024;  // larger batch means go to global memory, leaving the ring its space
 
+// acc = c * v + acc on two float lanes at once (fma.rn.f32x2: each lane is the
+// same single-rounding FMA as fmaf).
+__device__ __forceinline__ float2 fma2(float2 c, float2 v, float2 acc) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&c)),
+        "l"(*reinterpret_cast<unsigned long long*>(&v)),
+        "l"(*reinterpret_cast<unsigned long long*>(&acc)));
+  return *reinterpret_cast<float2*>(&r);
+}
+
+// One 16-byte granule of a representation row: acc[e] += c * (elements 2e, 2e+1).
 template <typename RT>
 struct Granule;
 template <>
 struct Granule<float> {
   static constexpr int kElems = 4;
-  __device__ static void load(const unsigned char* p, float (&o)[4]) {
+  __device__ static void fma(const unsigned char* p, float2 c2, float2 (&acc)[2]) {
     const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = v.x;
-    o[1] = v.y;
-    o[2] = v.z;
-    o[3] = v.w;
+    acc[0] = fma2(c2, make_float2(v.x, v.y), acc[0]);
+    acc[1] = fma2(c2, make_float2(v.z, v.w), acc[1]);
   }
 };
 template <>
 struct Granule<__nv_bfloat16> {
   static constexpr int kElems = 8;
-  __device__ static void load(const unsigned char* p, float (&o)[8]) {
+  // a bfloat16 is the top half of the float32 with the same value
+  __device__ static void fma(const unsigned char* p, float2 c2, float2 (&acc)[4]) {
     const uint4 v = *reinterpret_cast<const uint4*>(p);
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[e]));
-      o[2 * e] = f.x;
-      o[2 * e + 1] = f.y;
-    }
+    for (int e = 0; e < 4; ++e)
+      acc[e] = fma2(c2, make_float2(__uint_as_float(w[e] << 16), __uint_as_float(w[e] & 0xffff0000u)),
+                    acc[e]);
   }
 };
 
@@ -269,19 +293,21 @@ __device__ __forceinline__ Regions regions(unsigned char* smem, const LaunchCfg&
   return r;
 }
 
+template <int CW>
 __device__ __forceinline__ void init_barriers(Shared& sh, const LaunchCfg& c) {
+  using RL = Roles<CW>;
   if (threadIdx.x == 0) {
     for (int s = 0; s < c.nchunk; ++s) {
       mbar_init(&sh.row_full[s], uint32_t(c.crows));
       mbar_init(&sh.coef_full[s], 1);
-      mbar_init(&sh.slot_empty[s], kGatherWarps);
+      mbar_init(&sh.slot_empty[s], RL::kGatherWarps);
     }
     for (int b = 0; b < kXBufs; ++b) {
       mbar_init(&sh.x_full[b], 1);
-      mbar_init(&sh.x_empty[b], kCoefWarps + 1);
+      mbar_init(&sh.x_empty[b], RL::kCoefWarps + 1);
     }
     for (int b = 0; b < kMBufs; ++b) {
-      mbar_init(&sh.means_full[b], kGatherWarps);
+      mbar_init(&sh.means_full[b], RL::kGatherWarps);
       mbar_init(&sh.means_empty[b], 1);
     }
     sh.abort_flag = 0;
@@ -353,7 +379,7 @@ struct CoefState {
   uint64_t cbase;   // global chunk counter of the current query's first chunk
 };
 
-template <bool XREG>
+template <bool XREG, int CW>
 __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const LaunchCfg& cfg,
                            const Regions& rg, Shared& sh, const float* xq) {
   const int lane = threadIdx.x & 31;
@@ -366,7 +392,7 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
 #pragma unroll
   for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < cfg.xpad) ? xq[t * 32 + lane] : 0.f;
   const uint64_t cend = st.cbase + uint64_t((qd.N + CR - 1) / CR);
-  for (; st.cc < cend; st.cc += kCoefWarps) {
+  for (; st.cc < cend; st.cc += CW) {
     const int64_t j0 = int64_t(st.cc - st.cbase) * CR;
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
     // lanes 0..cnt-1 draw the chunk's indices; every lane gets all four
@@ -400,7 +426,7 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
       }
       mbar_arrive(&sh.coef_full[st.cs]);
     }
-    st.cs += kCoefWarps;
+    st.cs += CW;
     if (st.cs >= nchunk) {
       st.cs -= nchunk;
       st.ph ^= 1u;
@@ -411,11 +437,11 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
 }
 
 // XMODE: 0 = x in registers (n <= 1024), 1 = x in shared memory, 2 = per query.
-template <class Seq, int XMODE>
+template <class Seq, int XMODE, int CW>
 __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
   const int lane = threadIdx.x & 31;
   const int cw = (threadIdx.x >> 5) - kFirstCoefWarp;
-  CoefState st{uint32_t(cw), 0u, uint64_t(cw), 0};  // nchunk >= kMinChunks > kCoefWarps
+  CoefState st{uint32_t(cw), 0u, uint64_t(cw), 0};  // nchunk >= kMinChunks > CW
   const int64_t nq = seq.size();
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
@@ -424,12 +450,12 @@ __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& r
     const float* xq = rg.xbuf + xb * cfg.xpad;
     bool ok;
     if (XMODE == 0) {
-      ok = coef_query<true>(qd, qs, st, cfg, rg, sh, xq);
+      ok = coef_query<true, CW>(qd, qs, st, cfg, rg, sh, xq);
     } else if (XMODE == 1) {
-      ok = coef_query<false>(qd, qs, st, cfg, rg, sh, xq);
+      ok = coef_query<false, CW>(qd, qs, st, cfg, rg, sh, xq);
     } else {
-      ok = qd.n <= 1024 ? coef_query<true>(qd, qs, st, cfg, rg, sh, xq)
-                        : coef_query<false>(qd, qs, st, cfg, rg, sh, xq);
+      ok = qd.n <= 1024 ? coef_query<true, CW>(qd, qs, st, cfg, rg, sh, xq)
+                        : coef_query<false, CW>(qd, qs, st, cfg, rg, sh, xq);
     }
     if (!ok) return;
     __syncwarp();
@@ -438,21 +464,22 @@ __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& r
 }
 
 // ---------------------------------------------------------------- gather
-template <typename RT, int GPT>
+template <typename RT, int GPT, int CW>
 __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint32_t& ph,
                              const LaunchCfg& cfg, const Regions& rg, Shared& sh, float* means) {
   using G = Granule<RT>;
   constexpr int GR = G::kElems;
   const int lane = threadIdx.x & 31;
-  const int gt = threadIdx.x - kFirstGatherWarp * 32;
+  using RL = Roles<CW>;
+  const int gt = threadIdx.x - RL::kFirstGatherWarp * 32;
   const int CR = cfg.crows;
   const uint32_t nchunk = uint32_t(cfg.nchunk);
   const int mb = int(qs % kMBufs);
-  float acc[GPT][GR];
+  float2 acc[GPT][GR / 2];
 #pragma unroll
   for (int u = 0; u < GPT; ++u)
 #pragma unroll
-    for (int e = 0; e < GR; ++e) acc[u][e] = 0.f;
+    for (int e = 0; e < GR / 2; ++e) acc[u][e] = make_float2(0.f, 0.f);
   int batch_left = qd.J, batch = 0;
   for (int64_t j0 = 0; j0 < qd.N; j0 += CR) {
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
@@ -465,12 +492,9 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
       const unsigned char* row = rg.ring + (size_t(cs) * CR + s2) * cfg.slot_bytes;
 #pragma unroll
       for (int u = 0; u < GPT; ++u) {
-        const int gi = gt + u * kGatherThreads;
+        const int gi = gt + u * RL::kGatherThreads;
         if (gi * GR < qd.ldr) {
-          float v[GR];
-          G::load(row + size_t(gi) * 16, v);
-#pragma unroll
-          for (int e = 0; e < GR; ++e) acc[u][e] = fmaf(c, v[e], acc[u][e]);
+          G::fma(row + size_t(gi) * 16, make_float2(c, c), acc[u]);
         }
       }
       if (--batch_left == 0) {
@@ -480,12 +504,13 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
         float* mrow = means + int64_t(batch) * qd.ldr;
 #pragma unroll
         for (int u = 0; u < GPT; ++u) {
-          const int gi = gt + u * kGatherThreads;
+          const int gi = gt + u * RL::kGatherThreads;
           if (gi * GR < qd.ldr) {
 #pragma unroll
-            for (int e = 0; e < GR; ++e) {
-              mrow[gi * GR + e] = acc[u][e] * qd.inv_J;
-              acc[u][e] = 0.f;
+            for (int e = 0; e < GR / 2; ++e) {
+              mrow[gi * GR + 2 * e] = acc[u][e].x * qd.inv_J;
+              mrow[gi * GR + 2 * e + 1] = acc[u][e].y * qd.inv_J;
+              acc[u][e] = make_float2(0.f, 0.f);
             }
           }
         }
@@ -504,7 +529,7 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
 }
 
 // DYN: the representation type is chosen per query (batches of mixed plans).
-template <class Seq, typename RT, int GPT, bool DYN>
+template <class Seq, typename RT, int GPT, bool DYN, int CW>
 __device__ void gather_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
   const int lane = threadIdx.x & 31;
   uint32_t cs = 0, ph = 0;
@@ -515,10 +540,10 @@ __device__ void gather_role(const Seq& seq, const LaunchCfg& cfg, const Regions&
     bool ok;
     if (DYN) {
       ok = qd.dtype == KERDOCK_BF16
-               ? gather_query<__nv_bfloat16, GPT>(qd, qs, cs, ph, cfg, rg, sh, means)
-               : gather_query<float, GPT>(qd, qs, cs, ph, cfg, rg, sh, means);
+               ? gather_query<__nv_bfloat16, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
+               : gather_query<float, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
     } else {
-      ok = gather_query<RT, GPT>(qd, qs, cs, ph, cfg, rg, sh, means);
+      ok = gather_query<RT, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
     }
     if (!ok) return;
     if (cfg.means_gmem != nullptr) __threadfence_block();
@@ -721,18 +746,18 @@ __device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& 
   }
 }
 
-template <class Seq, typename RT, int GPT, bool DYN, int XMODE>
+template <class Seq, typename RT, int GPT, bool DYN, int XMODE, int CW>
 __device__ __forceinline__ void run_roles(const Seq& seq, const LaunchCfg& cfg, Shared& sh,
                                           unsigned char* smem) {
   const Regions rg = regions(smem, cfg);
-  init_barriers(sh, cfg);
+  init_barriers<CW>(sh, cfg);
   const int warp = threadIdx.x >> 5;
   if (warp == 0) {
     producer_role(seq, cfg, rg, sh);
-  } else if (warp < kFirstGatherWarp) {
-    coef_role<Seq, XMODE>(seq, cfg, rg, sh);
+  } else if (warp < Roles<CW>::kFirstGatherWarp) {
+    coef_role<Seq, XMODE, CW>(seq, cfg, rg, sh);
   } else if (warp < kFirstFinalWarp) {
-    gather_role<Seq, RT, GPT, DYN>(seq, cfg, rg, sh);
+    gather_role<Seq, RT, GPT, DYN, CW>(seq, cfg, rg, sh);
   } else {
     final_role(seq, cfg, rg, sh);
   }
@@ -745,7 +770,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Shared sh;
   SingleSeq seq{a};
-  run_roles<SingleSeq, RT, GPT, false, XREG ? 0 : 1>(seq, a.cfg, sh, smem);
+  run_roles<SingleSeq, RT, GPT, false, XREG ? 0 : 1, XREG ? kCoefWarpsSmall : kCoefWarpsLarge>(
+      seq, a.cfg, sh, smem);
 }
 
 // Batch kernel: any mix of plans (types and sizes), one descriptor per query.
@@ -753,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_batch_kernel(const BatchArg
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Shared sh;
   BatchSeq seq{a};
-  run_roles<BatchSeq, float, 4, true, 2>(seq, a.cfg, sh, smem);
+  run_roles<BatchSeq, float, 4, true, 2, kCoefWarpsSmall>(seq, a.cfg, sh, smem);
 }
 
 }  // namespace
@@ -794,7 +820,7 @@ bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c
   if (avail > cap) avail = cap;
   int ns = int(avail / per_slot);
   if (ns > kMaxSlots) ns = kMaxSlots;
-  int cr = tu.crows > 0 ? tu.crows : (ns >= 32 ? 4 : ns >= 8 ? 2 : 1);
+  int cr = tu.crows > 0 ? tu.crows : (ns >= 32 ? 4 : ns >= 2 * kMinChunks ? 2 : 1);
   if (cr != 1 && cr != 2 && cr != 4) return false;
   c.crows = cr;
   c.nchunk = ns / cr;
@@ -867,22 +893,30 @@ int launch_single(const QueryArgs& a, int64_t grid, cudaStream_t stream) {
   return KERDOCK_OK;
 }
 
+// Granules (16 bytes) per gather thread: the row's granules over the gather
+// threads of the role split used for this n (m <= 4096 and 256 gather threads
+// bound it by 4).
 int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
   const int64_t granule = 16 / int64_t(p.elem_bytes());
-  const int64_t gpt = (p.ldr / granule + kGatherThreads - 1) / kGatherThreads;
   const bool xreg = p.n <= 1024;
+  const int64_t gthreads = xreg ? Roles<kCoefWarpsSmall>::kGatherThreads
+                                : Roles<kCoefWarpsLarge>::kGatherThreads;
+  const int64_t gpt = (p.ldr / granule + gthreads - 1) / gthreads;
   if (p.dtype == KERDOCK_BF16) {
     if (gpt <= 1) return xreg ? launch_single<__nv_bfloat16, 1, true>(a, grid, p.stream)
                               : launch_single<__nv_bfloat16, 1, false>(a, grid, p.stream);
     if (gpt <= 2) return xreg ? launch_single<__nv_bfloat16, 2, true>(a, grid, p.stream)
                               : launch_single<__nv_bfloat16, 2, false>(a, grid, p.stream);
-    return launch_single<__nv_bfloat16, 4, false>(a, grid, p.stream);
+    if (gpt <= 4 && !xreg) return launch_single<__nv_bfloat16, 4, false>(a, grid, p.stream);
+    return KERDOCK_ERR_UNSUPPORTED;
   }
   if (gpt <= 1) return xreg ? launch_single<float, 1, true>(a, grid, p.stream)
                             : launch_single<float, 1, false>(a, grid, p.stream);
   if (gpt <= 2) return xreg ? launch_single<float, 2, true>(a, grid, p.stream)
                             : launch_single<float, 2, false>(a, grid, p.stream);
-  return launch_single<float, 4, false>(a, grid, p.stream);
+  if (gpt <= 4) return xreg ? launch_single<float, 4, true>(a, grid, p.stream)
+                            : launch_single<float, 4, false>(a, grid, p.stream);
+  return KERDOCK_ERR_UNSUPPORTED;
 }
 
 }  // namespace
