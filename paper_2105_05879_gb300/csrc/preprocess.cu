@@ -276,127 +276,181 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------
-// d = 4096: a cluster of four CTAs shares one tile of 32 rows.  CTA c holds the
-// quarter p in [1024 c, 1024 (c+1)) of those rows in shared memory and runs the
-// first ten butterfly stages there (7 in registers, 3 across its 8 warps via
-// its exchange buffer); the last five stages combine the 32 sources (8 warps x
-// 4 CTAs) per output, read from the four exchange buffers over distributed
-// shared memory.  Each CTA then stores a quarter of the w of the round.
+// d = 4096: a cluster of four CTAs shares one tile of TI rows (TI = 32: the
+// representation's rows then get 64-byte (bfloat16) or 128-byte (float32)
+// runs per output row).  Write p = 1024 q + 64 s + j: CTA q keeps the quarter
+// p in [1024 q, 1024 (q+1)) of the tile in shared memory; its thread (r, s)
+// holds row r's 64 values of source s in registers and runs the six butterfly
+// stages over j there (phase 1).  Output w = 64 w_hi + w_lo: the w_lo of the
+// phase-1 results are spread over the cluster, CTA c taking w_lo in
+// [16 c, 16 c + 16), and each CTA's thread (r, w_lo) combines the 64 sources
+// (q, s) of its column in two rounds of 32 (s < 8, s >= 8), five stages per
+// round plus one combining stage (phase 2).  Each round, every thread of the
+// sending half writes its values straight into the owners' exchange buffers
+// over distributed shared memory; split cluster barriers separate writing from
+// reading, and the "buffer free" half of each barrier pair overlaps with the
+// next round's arithmetic.
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
+template <int TI>
 struct Big {
-  static constexpr int D = 4096, Q = 1024, TI = 32, NW = 8, RG = 128, EXP = 2, RGP = RG / EXP;
-  static constexpr int CL = 4;                 // CTAs per cluster
-  static constexpr int SRC = NW * CL;          // 32 sources in phase 2
-  static constexpr int WPC = RGP / CL;         // w per CTA per round: 16
-  static constexpr int AST = Q + 4;            // A-tile row stride (floats)
-  static constexpr int XST = RGP * TI;         // floats per source: [w][row]
-  static constexpr int THREADS = NW * 32;
-  static constexpr size_t SMEM = size_t(TI) * AST * 4 + size_t(NW) * XST * 4 + size_t(Q) * 4;
+  static constexpr int D = 4096, Q = 1024, CL = 4;  // CTAs per cluster, p per CTA
+  static constexpr int NS = 16, RG = 64;             // sources per CTA, values per source
+  static constexpr int THREADS = TI * NS;            // thread (r, s) = (tid % TI, tid / TI)
+  static constexpr int WLC = RG / CL;                // w_lo per CTA: 16
+  static constexpr int HS = NS / 2;                  // sources per CTA per round: 8
+  static constexpr int RSRC = HS * CL;               // sources per round: 32
+  static constexpr int AST = Q + 4;                  // A-tile row stride (floats)
+  static constexpr int XSRC = WLC * TI + (TI == 32 ? 0 : 16);  // floats per source: [w_lo][row]
+  static constexpr size_t SMEM = size_t(TI) * AST * 4 + size_t(RSRC) * XSRC * 4;
+  static constexpr int MINB = THREADS >= 512 ? 1 : 2;
+  static_assert(THREADS <= 1024 && TI % 8 == 0, "tile");
 };
 
-template <typename OutT>
-__global__ void __launch_bounds__(Big::THREADS, 1)
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void store_one(T* dst, float v);
+template <>
+__device__ __forceinline__ void store_one<float>(float* dst, float v) {
+  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(dst), "f"(v) : "memory");
+}
+template <>
+__device__ __forceinline__ void store_one<__nv_bfloat16>(__nv_bfloat16* dst, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  asm volatile("st.global.cs.b16 [%0], %1;" ::"l"(dst),
+               "h"(*reinterpret_cast<const unsigned short*>(&h))
+               : "memory");
+}
+
+template <typename OutT, int TI>
+__global__ void __launch_bounds__(Big<TI>::THREADS, Big<TI>::MINB)
     preprocess_d4096_kernel(const PreArgs a) {
-  using C = Big;
+  using C = Big<TI>;
   constexpr int64_t B = C::D / 2 + 1;
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = int(cluster.block_rank());
+  const int q = int(cluster.block_rank());
   extern __shared__ __align__(16) float smem[];
-  float* At = smem;                                 // [32][AST]: this CTA's quarter
-  float* X = smem + size_t(C::TI) * C::AST;         // [8 sources][RGP w][32 rows]
-  uint32_t* Msk = reinterpret_cast<uint32_t*>(X + size_t(C::NW) * C::XST);  // [1024]
-  const float* Xc[C::CL];
+  float* At = smem;                            // [TI][AST]: this CTA's quarter of the tile
+  float* X = smem + size_t(TI) * C::AST;       // [32 sources][16 w_lo][TI rows]
+  float* Xc[C::CL];
 #pragma unroll
   for (int c = 0; c < C::CL; ++c) Xc[c] = cluster.map_shared_rank(X, c);
   OutT* R = static_cast<OutT*>(a.R);
-  const int lane = threadIdx.x & 31;
-  const int g = threadIdx.x >> 5;
-  const int rp = lane & 15, wsel = lane >> 4;
+  const int tid = threadIdx.x;
+  const int r = tid % TI, s = tid / TI;  // phase 1: (row, source); phase 2: (row, w_lo in CTA)
   const float sqrt_d = 64.f;
 
   const ItemRange ir =
       item_range(blockIdx.x / C::CL, gridDim.x / C::CL, a.group, a.num_tiles, B);
   int64_t cur_tile = -1;
+  cluster_arrive();  // pairs with the first "exchange buffers free" wait
 
   for (int64_t item = ir.beg; item < ir.end; ++item) {
     const int64_t tg = item / B;
     const int b = int(item - tg * B);
     const int64_t t = tg * a.group + ir.slot;
-    const int64_t i0 = t * C::TI;
+    const int64_t i0 = t * TI;
     const bool ident = b == C::D / 2;
-    cluster.sync();  // every CTA of the cluster is done reading the exchange buffers
     if (t != cur_tile) {
-      for (int idx = threadIdx.x; idx < C::TI * C::Q; idx += C::THREADS) {
-        const int i = idx / C::Q, p = idx % C::Q;
-        const int64_t gp = int64_t(crank) * C::Q + p;
+      __syncthreads();  // the previous tile's phase 1 is done everywhere in this CTA
+      for (int idx = tid; idx < TI * C::Q; idx += C::THREADS) {
+        const int i = idx / C::Q, pq = idx % C::Q;
+        const int64_t gp = int64_t(q) * C::Q + pq;
         float v = 0.f;
         if (i0 + i < a.m && gp < a.n) v = a.A[(i0 + i) * a.lda + gp];
-        At[i * C::AST + p] = v;
+        At[i * C::AST + pq] = v;
       }
       cur_tile = t;
+      __syncthreads();
     }
-    if (!ident) {  // step (i) of Lemma 6 for this quarter as float sign masks
-      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words + crank * (C::Q / 32);
-      for (int p = threadIdx.x; p < C::Q; p += C::THREADS)
-        Msk[p] = ((__ldg(srow + (p >> 5)) >> (p & 31)) & 1u) << 31;
-    }
-    __syncthreads();
 
-    // Phase 1: lane = row, registers = p in [g*RG, (g+1)*RG) of this quarter.
+    // Phase 1: step (i) of Lemma 6 from the source's two sign words, then the
+    // six stages over j in registers.
+    uint32_t wd[2] = {0u, 0u};
+    if (!ident) {
+      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words + q * (C::Q / 32) + s * 2;
+      wd[0] = __ldg(srow);
+      wd[1] = __ldg(srow + 1);
+    }
     float2 v[C::RG / 2];
 #pragma unroll
-    for (int r = 0; r < C::RG; r += 4) {
-      float4 q = *reinterpret_cast<const float4*>(&At[lane * C::AST + g * C::RG + r]);
+    for (int j = 0; j < C::RG; j += 4) {
+      float4 x4 = *reinterpret_cast<const float4*>(&At[r * C::AST + s * C::RG + j]);
       if (!ident) {
-        const uint4 m4 = *reinterpret_cast<const uint4*>(&Msk[g * C::RG + r]);
-        q.x = __uint_as_float(__float_as_uint(q.x) ^ m4.x);
-        q.y = __uint_as_float(__float_as_uint(q.y) ^ m4.y);
-        q.z = __uint_as_float(__float_as_uint(q.z) ^ m4.z);
-        q.w = __uint_as_float(__float_as_uint(q.w) ^ m4.w);
+        uint32_t f[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          f[e] = (wd[(j + e) >> 5] << (31 - ((j + e) & 31))) & 0x80000000u;
+        x4.x = __uint_as_float(__float_as_uint(x4.x) ^ f[0]);
+        x4.y = __uint_as_float(__float_as_uint(x4.y) ^ f[1]);
+        x4.z = __uint_as_float(__float_as_uint(x4.z) ^ f[2]);
+        x4.w = __uint_as_float(__float_as_uint(x4.w) ^ f[3]);
       }
-      v[r / 2] = make_float2(q.x, q.y);
-      v[r / 2 + 1] = make_float2(q.z, q.w);
+      v[j / 2] = make_float2(x4.x, x4.y);
+      v[j / 2 + 1] = make_float2(x4.z, x4.w);
     }
     if (!ident) fwht_pairs<C::RG / 2>(v);
 
+    // Phase 2 in two rounds of 32 sources (q', s') with s' / 8 == round.
+    float2 z[2][C::RSRC / 2];  // per round: pairs (source k, source k + 16)
 #pragma unroll
-    for (int part = 0; part < C::EXP; ++part) {
-      if (part > 0) cluster.sync();  // the previous round's remote reads are done
+    for (int e = 0; e < 2; ++e) {
+      cluster_wait();  // every CTA is done reading the exchange buffers
+      if ((s >> 3) == e) {
+        const int src = q * C::HS + (s & 7);
 #pragma unroll
-      for (int r2 = 0; r2 < C::RGP / 2; ++r2) {
-        const float2 val = v[part * (C::RGP / 2) + r2];
-        X[g * C::XST + (2 * r2) * C::TI + lane] = val.x;
-        X[g * C::XST + (2 * r2 + 1) * C::TI + lane] = val.y;
-      }
-      cluster.sync();  // all four exchange buffers hold this round
-      const int wl = crank * C::WPC + g * 2 + wsel;  // w within the round
-      float2 y[C::SRC];  // source s = 8 * cta + warp <-> p bits 7..11
-#pragma unroll
-      for (int c = 0; c < C::CL; ++c) {
-#pragma unroll
-        for (int h = 0; h < C::NW; ++h)
-          y[c * C::NW + h] =
-              *reinterpret_cast<const float2*>(&Xc[c][h * C::XST + wl * C::TI + 2 * rp]);
-      }
-      if (!ident) {
-        fwht_across<C::SRC>(y);
-      } else {
-#pragma unroll
-        for (int h = 0; h < C::SRC; ++h) y[h] = make_float2(y[h].x * sqrt_d, y[h].y * sqrt_d);
-      }
-      const int64_t orow = i0 + 2 * rp;
-      if (orow < a.ldr) {
-#pragma unroll
-        for (int h = 0; h < C::SRC; ++h) {
-          const int64_t w = int64_t(h) * C::RG + part * C::RGP + wl;
-          store_pair<OutT>(R + (int64_t(b) * C::D + w) * a.ldr + orow, y[h]);
+        for (int j = 0; j < C::RG; ++j) {
+          const float val = (j & 1) ? v[j / 2].y : v[j / 2].x;
+          Xc[j / C::WLC][src * C::XSRC + (j % C::WLC) * TI + r] = val;
         }
+      }
+      cluster_arrive();  // this round's values are written
+      cluster_wait();    // ... by every CTA of the cluster
+#pragma unroll
+      for (int k = 0; k < C::RSRC / 2; ++k)
+        z[e][k] = make_float2(X[k * C::XSRC + s * TI + r],
+                              X[(k + C::RSRC / 2) * C::XSRC + s * TI + r]);
+      cluster_arrive();  // done reading; the buffers may be refilled
+      if (!ident) {
+#pragma unroll
+        for (int k = 0; k < C::RSRC / 2; ++k)
+          z[e][k] = make_float2(z[e][k].x + z[e][k].y, z[e][k].x - z[e][k].y);
+        fwht_across<C::RSRC / 2>(z[e]);
+      }
+    }
+
+    // Combine the rounds (source bit s / 8) and store.  Round-local source
+    // k = 8 q' + (s' mod 8) and the round e give w_hi = 16 q' + 8 e + (s' mod 8).
+    const int64_t row = i0 + r;
+    if (row < a.ldr) {
+      OutT* rb = R + (int64_t(b) * C::D + q * C::WLC + s) * a.ldr + row;
+      const int64_t wstride = int64_t(C::RG) * a.ldr;  // one step of w_hi
+#pragma unroll
+      for (int k = 0; k < C::RSRC; ++k) {
+        const float z0 = (k < C::RSRC / 2) ? z[0][k].x : z[0][k - C::RSRC / 2].y;
+        const float z1 = (k < C::RSRC / 2) ? z[1][k].x : z[1][k - C::RSRC / 2].y;
+        float y0, y1;
+        if (ident) {
+          y0 = z0 * sqrt_d;
+          y1 = z1 * sqrt_d;
+        } else {
+          y0 = z0 + z1;
+          y1 = z0 - z1;
+        }
+        const int whi = (k >> 3) * 16 + (k & 7);
+        store_one<OutT>(rb + int64_t(whi) * wstride, y0);
+        store_one<OutT>(rb + int64_t(whi + 8) * wstride, y1);
       }
     }
   }
-  cluster.sync();  // keep this CTA's shared memory alive until the others are done
+  cluster_wait();  // pairs with the last arrive: no CTA leaves while others read its buffers
 }
 
 // Largest power of two <= limit and <= num_tiles (the tile group size G).
@@ -408,8 +462,9 @@ int64_t pick_group(int64_t num_tiles, int64_t limit) {
 
 template <typename OutT>
 int launch_d4096(const Plan& p) {
-  using C = Big;
-  auto kern = preprocess_d4096_kernel<OutT>;
+  constexpr int TI = 32;
+  using C = Big<TI>;
+  auto kern = preprocess_d4096_kernel<OutT, TI>;
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    int(C::SMEM)));
   PreArgs a;
@@ -421,7 +476,7 @@ int launch_d4096(const Plan& p) {
   a.sign_words = p.sign_words;
   a.R = p.repr;
   a.ldr = p.ldr;
-  a.num_tiles = (p.ldr + C::TI - 1) / C::TI;
+  a.num_tiles = (p.ldr + TI - 1) / TI;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
