@@ -555,7 +555,7 @@ def run_learned(args, K, torch, peak):
         "plain_same_budget": {"queries/s": round(q / (ms_sk / 1e3), 1), "recall": round(rs[0], 4),
                               "exact": round(rs[1], 4),
                               "note": "top-S' of |mu| from the same sketch, no network"},
-        "gpu_launches": None,
+        "gpu_launches": max(1, args.steps) * lp.launches_per_apply(q),
     }
     plan.close()
     return line

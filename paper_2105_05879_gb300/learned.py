@@ -105,6 +105,12 @@ class LearnedProposal:
         sc = self.scores(mu)
         return self.plan.refine_scores(X, sc, self.S_prime, eps, flags)
 
+    def launches_per_apply(self, q):
+        """Library kernels one apply(q) launches: one sketch query kernel per
+        65536 rows, four network kernels (input conversion, three layers) per
+        max_batch rows, one refinement kernel."""
+        return -(-q // 65536) + 4 * -(-q // self.max_batch) + 1
+
     def apply_plain_sketch(self, X, eps, seed, flags=0):
         """The fallback with the same budget: sketch -> top S' of |mu| -> refine."""
         mu = self.sketch_mu(X, seed)
