@@ -561,6 +561,101 @@ def run_learned(args, K, torch, peak):
     return line
 
 
+def fig1_errors(mu, idx, val, cnt, Z):
+    """Sec. 4's worst-case errors over the trials: max_t ||mu_t - Ax_t||_inf
+    for the median-of-means estimate and max_t ||h_t - Ax_t||_2 for h = x
+    multiplied by the rows of A at the S largest |mu| (all S refined values
+    kept), plus the fraction of trials with h = Ax (to 1e-5)."""
+    mu_err = np.abs(mu - Z).max(axis=1)
+    H = np.zeros_like(Z)
+    for t in range(Z.shape[0]):
+        c = int(cnt[t])
+        H[t, idx[t, :c]] = val[t, :c]
+    h_err = np.sqrt(((H - Z) ** 2).sum(axis=1))
+    return float(mu_err.max()), float(h_err.max()), float(np.mean(h_err < 1e-5))
+
+
+def run_fig1(args, K, torch, peak):
+    """Sec. 4's experiment on the GPU: A random orthogonal, n = 4096 (float32
+    representation, 137.5 GB), 1000 trials x with Ax exactly 20-sparse of equal
+    magnitudes at random positions, a (J, K) grid: worst-case errors of mu and
+    of h, and the query time against a naive dense matrix-vector product on the
+    same GPU (per query, A read from HBM each time, and batched over the 1000
+    trials as one matrix product)."""
+    n, s_, trials = 4096, 20, 1000
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    A_np = workloads.random_orthogonal(n, 11).astype(np.float32)
+    rng = np.random.default_rng(12)
+    Z = np.zeros((trials, n))
+    for t in range(trials):
+        sup = rng.choice(n, s_, replace=False)
+        Z[t, sup] = rng.choice([-1.0, 1.0], s_) / math.sqrt(s_)
+    A = torch.from_numpy(A_np).to(dev)
+    X = torch.from_numpy((Z @ A_np.astype(np.float64)).astype(np.float32)).to(dev)
+    Zf = X.cpu().double().numpy() @ A_np.astype(np.float64).T  # Ax of the float32 inputs (host)
+    Js = [25, 50, 100, 200, 375, 500, 750, 1000]
+    Ks = [1, 2, 3, 4, 6, 8, 12, 16]
+    plan = K.KerdockPlan(n, n, J=375, K=2, S=10 * s_, dtype="f32", device=dev)
+    plan.preprocess(A)
+    plan.sync()
+    # naive products on the same GPU (cuBLAS through torch, after warm-up): one
+    # matrix-vector product per query, 100 of them replayed from a CUDA graph
+    # (A, 64 MB, stays in the 129 MB L2 between them), and one product for all
+    # trials at once
+    xs = [X[t].clone() for t in range(100)]
+    ys = [torch.empty(n, device=dev) for _ in range(100)]
+    for _ in range(3):
+        torch.mv(A, xs[0], out=ys[0])
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for t in range(100):
+            torch.mv(A, xs[t], out=ys[t])
+    g.replay()
+    torch.cuda.synchronize()
+    gemv_ms = _timed(torch, stream, g.replay, 10) / 100
+    Y = torch.empty(n, trials, device=dev)
+    for _ in range(2):
+        torch.matmul(A, X.T, out=Y)
+    torch.cuda.synchronize()
+    gemm_ms = _timed(torch, stream, lambda: torch.matmul(A, X.T, out=Y), 5) / trials
+    del g, xs, ys, Y
+    grid = []
+    launches = 0
+    for Kk in Ks:
+        for J in Js:
+            c = plan.clone(J, Kk, 10 * s_)
+            out = c.alloc_outputs(trials)
+            idx, val, cnt, mu, _, _ = c.apply(X, 1.0, 77, flags=K.KERDOCK_FLAG_FULL_OUTPUT,
+                                              out=out, debug=True)
+            mu_err, h_err, exact = fig1_errors(mu.double().cpu().numpy(), idx.cpu().numpy(),
+                                               val.double().cpu().numpy(), cnt.cpu().numpy(), Zf)
+            ms = _timed(torch, stream, lambda: c.apply(X, 1.0, 77, flags=K.KERDOCK_FLAG_FULL_OUTPUT,
+                                                       out=out), 3) / trials
+            launches += 3
+            grid.append({"J": J, "K": Kk, "mu_err_inf_max": round(mu_err, 5),
+                         "h_err_2_max": round(h_err, 6), "exact_frac": round(exact, 4),
+                         "us_per_query": round(ms * 1e3, 3),
+                         "ratio_vs_gemv": round(ms / gemv_ms, 4),
+                         "ratio_vs_batched_gemm": round(ms / gemm_ms, 3)})
+            del c
+    ref = next(g for g in grid if g["J"] == 375 and g["K"] == 2)
+    return {
+        "metric": METRIC, "value": round(1e6 / ref["us_per_query"], 1), "unit": "queries/s",
+        "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": round(ref["us_per_query"] * trials / 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random orthogonal A; Ax 20-sparse, equal magnitudes; Sec. 4)",
+        "config": {"workload": ("Sec. 4 grid: n=m=4096 float32 representation, 1000 trials, "
+                                "s=20, delta=0, S=10s, (J,K) in {25..1000} x {1..16}; value at "
+                                "J=375, K=2"), "form": "fig1"},
+        "dense": {"gemv_us_per_query": round(gemv_ms * 1e3, 3),
+                  "batched_gemm_us_per_query": round(gemm_ms * 1e3, 3),
+                  "note": "cuBLAS float32 through torch; gemv with A resident in L2"},
+        "grid": grid, "gpu_launches": launches,
+    }
+
+
 def run_form(args):
     import torch
     from paper_2105_05879_gb300 import build as kbuild
@@ -569,7 +664,8 @@ def run_form(args):
     kbuild.build()
     K.load_library()
     peak, _ = measured_peaks()
-    fn = {"n4096_bf16": run_precision, "mixed_batch": run_batch, "n2048_learned": run_learned}
+    fn = {"n4096_bf16": run_precision, "mixed_batch": run_batch, "n2048_learned": run_learned,
+          "fig1": run_fig1}
     line = fn[args.workload](args, K, torch, peak)
     print(json.dumps(line), flush=True)
 
@@ -666,7 +762,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned"])
+                    choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_oracle_queries", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -80,3 +80,20 @@ def test_single_rank_needs_no_process_group():
     # rank 0 keeps the workload's own seeds (the single-GPU bench line)
     sh = bench.rank_shard(wl, 0)
     assert sh["codes_offset"] == 0 and sh["seed_apply"] == wl.seed_apply
+
+
+def test_fig1_errors_worst_case_over_trials():
+    import bench
+    Z = np.zeros((3, 8))
+    Z[0, [1, 5]] = [0.5, -0.5]
+    Z[1, [0, 2]] = [0.5, 0.5]
+    Z[2, [3, 4]] = [-0.5, 0.5]
+    mu = Z.copy()
+    mu[1, 7] = 0.25          # worst mu error 0.25 in trial 1
+    idx = np.array([[1, 5, 0], [0, 2, 7], [3, 6, 0]])
+    val = np.array([[0.5, -0.5, 0.0], [0.5, 0.5, 0.0], [-0.5, 0.1, 0.0]])
+    cnt = np.array([3, 3, 2])  # trial 2 misses index 4 and adds 0.1 at 6
+    mu_err, h_err, exact = bench.fig1_errors(mu, idx, val, cnt, Z)
+    assert mu_err == pytest.approx(0.25)
+    assert h_err == pytest.approx(np.sqrt(0.5 ** 2 + 0.1 ** 2))
+    assert exact == pytest.approx(2 / 3)
