@@ -17,6 +17,7 @@
 // 8-byte row pairs: a warp store writes two 128-byte runs of consecutive i of
 // output rows R[b][w][.] (float32).
 #include <cooperative_groups.h>
+#include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
 
 #include "kerdock_internal.cuh"
 
@@ -126,6 +127,7 @@ struct PreArgs {
   int64_t ldr;
   int64_t num_tiles;
   int64_t group;  // G: consecutive CTAs (or clusters) that sweep the bases in step
+  uint32_t* status;  // the plan's device status word
 };
 
 // Work split.  Tiles are taken in groups of G adjacent tiles; the G CTAs (or
@@ -476,6 +478,7 @@ int launch_d4096(const Plan& p) {
   a.sign_words = p.sign_words;
   a.R = p.repr;
   a.ldr = p.ldr;
+  a.status = p.status();
   a.num_tiles = (p.ldr + TI - 1) / TI;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -521,6 +524,7 @@ int launch_small(const Plan& p) {
   a.sign_words = p.sign_words;
   a.R = p.repr;
   a.ldr = p.ldr;
+  a.status = p.status();
   a.num_tiles = (p.ldr + kTileRows - 1) / kTileRows;
   // groups of up to 16 CTAs on adjacent 16-row tiles (256 consecutive rows)
   a.group = pick_group(a.num_tiles, 16);
@@ -533,6 +537,322 @@ int launch_small(const Plan& p) {
   return KERDOCK_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Precision form, d = 4096, bfloat16 representation: the three 16-point
+// stages of W_4096 = W_16 (x) W_16 (x) W_16 on the tensor cores
+// (mma.sync m16n8k16, bfloat16 operands, float32 accumulation).  Write
+// p = 256 p2 + 16 p1 + p0 and w = 256 w2 + 16 w1 + w0.  For one row and one
+// p2, stage 1 multiplies W_16 by the 16 x 16 block [p0][p1] (two n-tiles of
+// 8 p1) and gives [w0][p1]; its accumulator fragments are exactly the B
+// fragments of stage 2 over p1 (the C layout's columns are B's k), which gives
+// [w1][w0].  That block goes to shared memory (stmatrix) as E[row][w1][p2][w0];
+// stage 3 reads 16 p2 x 16 w0 per (row, w1) back with ldmatrix.trans, multiplies
+// by W_16 and gives [w2][w0]; eight rows of one w1 are packed as row pairs
+// into F[w2][w0][row] and written with one 4-D TMA store (16 rows x 16 w0 x
+// 16 w2).  The CTA's 16-row tile of A, rounded to bfloat16 once, sits in
+// tensor memory (128 KiB), laid out so that each thread's words for one
+// (row, p2) are four consecutive columns of its own lane.  Each stage's input
+// is rounded to bfloat16 (three roundings beside the final one); the identity
+// basis uses 4 I in all three stages (x 64 = sqrt(d)).
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int TI = 16, WARPS = 8, THREADS = WARPS * 32, D = 4096;
+constexpr int E_W1 = 16 * 32 + 16;           // bytes per (row, w1): 16 p2 x 32 B + pad
+constexpr int E_ROW = 16 * E_W1;             // bytes per row
+constexpr int E_BYTES = TI * E_ROW;          // 135168
+constexpr int F_WARP = 16 * 16 * TI * 2;     // [w2][w0][row] bfloat16 per warp: 8 KiB
+constexpr int MASK_WORDS = 16 * 32 * 4;      // [p2][lane][4]
+constexpr size_t SMEM = size_t(E_BYTES) + size_t(WARPS) * F_WARP + MASK_WORDS * 4 + 16;
+constexpr uint32_t TMEM_COLS = 256;          // 4 rows x 16 p2 x 4 words per lane
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+__device__ __forceinline__ void stmatrix_x4(uint32_t addr, uint32_t e0, uint32_t e1, uint32_t e2,
+                                            uint32_t e3) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+               "r"(e0), "r"(e1), "r"(e2), "r"(e3)
+               : "memory");
+}
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t (&m)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(m[0]), "=r"(m[1]), "=r"(m[2]), "=r"(m[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+      : "memory");
+}
+
+// Column of tensor memory holding a thread's four words for (row slot rl, p2).
+__device__ __forceinline__ uint32_t tcol(int rl, int p2) { return uint32_t((rl * 16 + p2) * 4); }
+
+__global__ void __launch_bounds__(THREADS, 1)
+    preprocess_d4096_tc_kernel(const PreArgs a, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int64_t B = D / 2 + 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* E = smem;
+  unsigned char* Fw = smem + E_BYTES + (threadIdx.x >> 5) * F_WARP;  // this warp's F
+  uint32_t* maskt = reinterpret_cast<uint32_t*>(smem + E_BYTES + WARPS * F_WARP);
+  uint32_t* tmem_slot = maskt + MASK_WORDS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int quarter = warp & 3, phalf = warp >> 2;  // lane quarter of tensor memory; p2 half
+  const bool aligned = (smem_addr(smem) & 1023u) == 0;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  const uint32_t tlane = tmem + (uint32_t(quarter * 32) << 16);
+  if (tid == 0 && !aligned) set_status(a.status, kStatusBadIndex);
+
+  // A fragments (rows g, g+8; columns 2q, 2q+1, 2q+8, 2q+9) of W_16 and of 4 I.
+  uint32_t aw[4], ai[4];
+  {
+    const int rr[4] = {g, g + 8, g, g + 8};
+    const int cc[4] = {2 * q, 2 * q, 2 * q + 8, 2 * q + 8};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float w0 = (__popc(rr[e] & cc[e]) & 1) ? -1.f : 1.f;
+      const float w1 = (__popc(rr[e] & (cc[e] + 1)) & 1) ? -1.f : 1.f;
+      aw[e] = pack_bf16x2(w0, w1);
+      ai[e] = pack_bf16x2(rr[e] == cc[e] ? 4.f : 0.f, rr[e] == cc[e] + 1 ? 4.f : 0.f);
+    }
+  }
+
+  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  int64_t cur_tile = -1;
+  for (int64_t item = ir.beg; item < ir.end; ++item) {
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
+    const int64_t i0 = t * TI;
+    const bool ident = b == D / 2;
+
+    if (t != cur_tile) {  // this warp's share of the tile into its lanes of tensor memory
+#pragma unroll 1
+      for (int rl = 0; rl < 4; ++rl) {
+        const int64_t row = i0 + quarter + 4 * rl;
+        const bool rv = row < a.m;
+        const float* arow = a.A + (rv ? row : 0) * a.lda;
+#pragma unroll 1
+        for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
+          uint32_t v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int p = p2 * 256 + (g + 8 * (j >> 1)) * 16 + 2 * q + 8 * (j & 1);
+            const float x0 = (rv && p < a.n) ? arow[p] : 0.f;
+            const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] : 0.f;
+            v[j] = pack_bf16x2(x0, x1);
+          }
+          tmem_st4(tlane + tcol(rl, p2), v);
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      cur_tile = t;
+    }
+
+    // Step (i) of Lemma 6 as bfloat16 sign masks in the threads' word order.
+    {
+      const uint32_t* srow = a.signs + int64_t(ident ? 0 : b) * a.sign_words;
+#pragma unroll
+      for (int u = 0; u < MASK_WORDS / THREADS; ++u) {
+        const int k = tid * (MASK_WORDS / THREADS) + u;
+        const int p2 = k >> 7, l = (k >> 2) & 31, j = k & 3;
+        const int p = p2 * 256 + ((l >> 2) + 8 * (j >> 1)) * 16 + 2 * (l & 3) + 8 * (j & 1);
+        uint32_t mk = 0u;
+        if (!ident) {
+          const uint32_t wd = __ldg(srow + (p >> 5)) >> (p & 31);
+          mk = ((wd & 1u) << 15) | ((wd & 2u) << 30);
+        }
+        maskt[k] = mk;
+      }
+    }
+    __syncthreads();  // masks ready; every warp is done reading E for the previous item
+
+    // Stages 1 and 2 for this warp's rows (quarter + 4 rl) and p2 half.
+    uint32_t A16[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) A16[e] = ident ? ai[e] : aw[e];
+#pragma unroll 1
+    for (int rl = 0; rl < 4; ++rl) {
+      const int r = quarter + 4 * rl;
+#pragma unroll 1
+      for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
+        uint32_t x[4];
+        tmem_ld4(tlane + tcol(rl, p2), x);
+        const uint4 mk = *reinterpret_cast<const uint4*>(&maskt[(p2 * 32 + lane) * 4]);
+        x[0] ^= mk.x;
+        x[1] ^= mk.y;
+        x[2] ^= mk.z;
+        x[3] ^= mk.w;
+        float d1a[4], d1b[4], d2a[4], d2b[4];
+        mma16816(d1a, A16, x[0], x[1]);  // [w0][p1 0..7]
+        mma16816(d1b, A16, x[2], x[3]);  // [w0][p1 8..15]
+        mma16816(d2a, A16, pack_bf16x2(d1a[0], d1a[1]), pack_bf16x2(d1b[0], d1b[1]));  // w0 0..7
+        mma16816(d2b, A16, pack_bf16x2(d1a[2], d1a[3]), pack_bf16x2(d1b[2], d1b[3]));  // w0 8..15
+        // [w1][w0] -> E[r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
+        const int mi = lane >> 3, mj = lane & 7;
+        const int w1 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
+        const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
+        stmatrix_x4(addr, pack_bf16x2(d2a[0], d2a[1]), pack_bf16x2(d2a[2], d2a[3]),
+                    pack_bf16x2(d2b[0], d2b[1]), pack_bf16x2(d2b[2], d2b[3]));
+      }
+    }
+    __syncthreads();  // E holds stages 1-2 of all 16 rows
+
+    // Stage 3: warp handles w1 = warp and warp + 8, 16 rows each.
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+      const int w1 = warp + 8 * s;
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncwarp();  // the previous TMA store has read this warp's F
+#pragma unroll 1
+      for (int g8 = 0; g8 < 2; ++g8) {
+        uint32_t packed[8][4];
+#pragma unroll
+        for (int rp = 0; rp < 4; ++rp) {
+          float v[2][8];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = 8 * g8 + 2 * rp + h;
+            const int mi = lane >> 3, mj = lane & 7;
+            const int p2 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
+            uint32_t m[4];
+            ldmatrix_x4_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
+            float d3a[4], d3b[4];
+            mma16816(d3a, A16, m[0], m[1]);  // [w2][w0 0..7]
+            mma16816(d3b, A16, m[2], m[3]);  // [w2][w0 8..15]
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              v[h][e] = d3a[e];
+              v[h][4 + e] = d3b[e];
+            }
+          }
+#pragma unroll
+          for (int pos = 0; pos < 8; ++pos) packed[pos][rp] = pack_bf16x2(v[0][pos], v[1][pos]);
+        }
+        // position pos: w2 = g + 8 ((pos >> 1) & 1), w0 = 2q + (pos & 1) + 8 (pos >> 2)
+#pragma unroll
+        for (int pos = 0; pos < 8; ++pos) {
+          const int w2 = g + 8 * ((pos >> 1) & 1), w0 = 2 * q + (pos & 1) + 8 * (pos >> 2);
+          *reinterpret_cast<uint4*>(Fw + ((w2 * 16 + w0) * TI + 8 * g8) * 2) =
+              make_uint4(packed[pos][0], packed[pos][1], packed[pos][2], packed[pos][3]);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && aligned) {
+        tma_store_4d(&tmap, smem_addr(Fw), int(i0), 0, w1, b * 16);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+}  // namespace tc
+
+int launch_d4096_tc(const Plan& p) {
+  tc::EncodeTiledFn enc = tc::encoder();
+  if (enc == nullptr) return KERDOCK_ERR_UNSUPPORTED;
+  // R[b][w][i] (bfloat16) as [(b, w2)][w1][w0][i]: box 16 rows x 16 w0 x 1 w1 x 16 w2
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {cuuint64_t(p.ldr), 16, 16, cuuint64_t(p.B) * 16};
+  const cuuint64_t strides[3] = {cuuint64_t(p.ldr) * 2, cuuint64_t(p.ldr) * 32,
+                                 cuuint64_t(p.ldr) * 512};
+  const cuuint32_t box[4] = {tc::TI, 16, 1, 16};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p.repr, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return KERDOCK_ERR_UNSUPPORTED;
+  auto kern = tc::preprocess_d4096_tc_kernel;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(tc::SMEM)));
+  PreArgs a;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.m = p.m;
+  a.n = p.n;
+  a.signs = p.signs();
+  a.sign_words = p.sign_words;
+  a.R = p.repr;
+  a.ldr = p.ldr;
+  a.status = p.status();
+  a.num_tiles = (p.ldr + tc::TI - 1) / tc::TI;
+  // groups of up to 16 CTAs (one per SM) on adjacent 16-row tiles
+  a.group = pick_group(a.num_tiles, 16);
+  int64_t ngrp = int64_t(p.num_sms) / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  if (ngrp < 1) ngrp = 1;
+  kern<<<unsigned(ngrp * a.group), tc::THREADS, tc::SMEM, p.stream>>>(a, map);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
 template <typename OutT>
 int launch_typed(const Plan& p) {
   switch (p.k) {
@@ -541,7 +861,9 @@ int launch_typed(const Plan& p) {
     case 6: return launch_small<6, OutT>(p);
     case 8: return launch_small<8, OutT>(p);
     case 10: return launch_small<10, OutT>(p);
-    case 12: return launch_d4096<OutT>(p);
+    case 12:
+      if (sizeof(OutT) == 2) return launch_d4096_tc(p);
+      return launch_d4096<OutT>(p);
     default: return KERDOCK_ERR_UNSUPPORTED;
   }
 }

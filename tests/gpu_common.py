@@ -40,14 +40,30 @@ def representation_slice(plan, b):
     return R[b, :, :m].float().cpu().numpy().astype(np.float64)
 
 
-def oracle_mu_bound_bf16(rows, c, J, K):
-    """Per-entry bound on |mu_bf16 - mu_exact| from rounding each stored entry
-    to bfloat16 (8 significant bits, relative error <= 2^-8):
-    |d ybar_k| <= 2^-8 (1/J) sum_j |c_j||R_j|,
-    and the median is 1-Lipschitz in the sup norm, so max_k bounds mu."""
-    contrib = np.abs(rows) * np.abs(c)[:, None]
+# Precision form at d = 4096: the three 16-point stages run on the tensor cores
+# with bfloat16 stage inputs, so besides the final rounding of each entry, the
+# rounding of A and of the two intermediate stages perturbs every entry of
+# R[b][:, i] by a few 2^-9 times its rms over w, which is ||a_i|| (W/sqrt(d) is
+# orthogonal).  Measured worst case over 8 bases x 4096 w x 256 rows: 0.016.
+TC_ABS = 2.0 ** -5
+
+
+def repr_bound_bf16(R_ref, row_norms=None):
+    """Per-entry bound on |R_bf16 - R_exact|: 2^-8 |R| (final rounding), plus
+    TC_ABS * ||a_i|| for the tensor-core stages (row_norms given)."""
+    bound = 2.0 ** -8 * np.abs(R_ref)
+    if row_norms is not None:
+        bound = bound + TC_ABS * np.asarray(row_norms)[None, :]
+    return bound
+
+
+def oracle_mu_bound_bf16(rows, c, J, K, row_norms=None):
+    """Per-entry bound on |mu_bf16 - mu_exact| from the representation bound
+    above: |d ybar_k| <= (1/J) sum_j |c_j| bound(R_j), and the median is
+    1-Lipschitz in the sup norm, so max_k bounds mu."""
+    contrib = np.abs(c)[:, None] * repr_bound_bf16(rows, row_norms)
     per_batch = contrib.reshape(K, J, -1).sum(axis=1) / J
-    return 2.0 ** -8 * per_batch.max(axis=0)
+    return per_batch.max(axis=0)
 
 
 def check_topS_valid(sel, mu_ref, S, tol):
