@@ -591,12 +591,20 @@ __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t (&m)[4
                : "r"(addr)
                : "memory");
 }
+// Loads are asynchronous: the registers are valid after tmem_wait_ld, which
+// names them so that the compiler does not read them earlier.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                : "r"(taddr)
                : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&u)[4], uint32_t (&v)[4]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(v[0]), "+r"(v[1]),
+                 "+r"(v[2]), "+r"(v[3])
+               :
+               : "memory");
 }
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
@@ -710,21 +718,37 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t A16[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) A16[e] = ident ? ai[e] : aw[e];
+    // 32 units (row slot rl, p2) per warp, two at a time; the next pair's words
+    // are loaded from tensor memory while this pair is multiplied.
+    auto unit_rl = [](int u) { return u >> 3; };
+    auto unit_p2 = [phalf](int u) { return 8 * phalf + (u & 7); };
+    uint32_t xa[4], xb[4];
+    tmem_ld4(tlane + tcol(unit_rl(0), unit_p2(0)), xa);
+    tmem_ld4(tlane + tcol(unit_rl(1), unit_p2(1)), xb);
+    tmem_wait_ld(xa, xb);
 #pragma unroll 1
-    for (int rl = 0; rl < 4; ++rl) {
-      const int r = quarter + 4 * rl;
-#pragma unroll 1
-      for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
-        uint32_t x[4];
-        tmem_ld4(tlane + tcol(rl, p2), x);
+    for (int u = 0; u < 32; u += 2) {
+      uint32_t x[2][4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        x[0][e] = xa[e];
+        x[1][e] = xb[e];
+      }
+      if (u + 2 < 32) {
+        tmem_ld4(tlane + tcol(unit_rl(u + 2), unit_p2(u + 2)), xa);
+        tmem_ld4(tlane + tcol(unit_rl(u + 3), unit_p2(u + 3)), xb);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = quarter + 4 * unit_rl(u + h), p2 = unit_p2(u + h);
         const uint4 mk = *reinterpret_cast<const uint4*>(&maskt[(p2 * 32 + lane) * 4]);
-        x[0] ^= mk.x;
-        x[1] ^= mk.y;
-        x[2] ^= mk.z;
-        x[3] ^= mk.w;
+        x[h][0] ^= mk.x;
+        x[h][1] ^= mk.y;
+        x[h][2] ^= mk.z;
+        x[h][3] ^= mk.w;
         float d1a[4], d1b[4], d2a[4], d2b[4];
-        mma16816(d1a, A16, x[0], x[1]);  // [w0][p1 0..7]
-        mma16816(d1b, A16, x[2], x[3]);  // [w0][p1 8..15]
+        mma16816(d1a, A16, x[h][0], x[h][1]);  // [w0][p1 0..7]
+        mma16816(d1b, A16, x[h][2], x[h][3]);  // [w0][p1 8..15]
         mma16816(d2a, A16, pack_bf16x2(d1a[0], d1a[1]), pack_bf16x2(d1b[0], d1b[1]));  // w0 0..7
         mma16816(d2b, A16, pack_bf16x2(d1a[2], d1a[3]), pack_bf16x2(d1b[2], d1b[3]));  // w0 8..15
         // [w1][w0] -> E[r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
@@ -734,6 +758,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         stmatrix_x4(addr, pack_bf16x2(d2a[0], d2a[1]), pack_bf16x2(d2a[2], d2a[3]),
                     pack_bf16x2(d2b[0], d2b[1]), pack_bf16x2(d2b[2], d2b[3]));
       }
+      tmem_wait_ld(xa, xb);
     }
     __syncthreads();  // E holds stages 1-2 of all 16 rows
 
@@ -768,12 +793,20 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int pos = 0; pos < 8; ++pos) packed[pos][rp] = pack_bf16x2(v[0][pos], v[1][pos]);
         }
-        // position pos: w2 = g + 8 ((pos >> 1) & 1), w0 = 2q + (pos & 1) + 8 (pos >> 2)
+        // position pos: w2 = g + 8 ((pos >> 1) & 1), w0 = 2q + (pos & 1) + 8 (pos >> 2).
+        // Lanes with q >= 2 take the odd/even partner first, so the eight lanes
+        // of a quarter-warp cover four 16-byte bank slots instead of two.
+        const int sw = (q >> 1) & 1;
 #pragma unroll
         for (int pos = 0; pos < 8; ++pos) {
-          const int w2 = g + 8 * ((pos >> 1) & 1), w0 = 2 * q + (pos & 1) + 8 * (pos >> 2);
-          *reinterpret_cast<uint4*>(Fw + ((w2 * 16 + w0) * TI + 8 * g8) * 2) =
-              make_uint4(packed[pos][0], packed[pos][1], packed[pos][2], packed[pos][3]);
+          const int ps = pos ^ sw;
+          const int w2 = g + 8 * ((ps >> 1) & 1), w0 = 2 * q + (ps & 1) + 8 * (ps >> 2);
+          uint4 val;
+          val.x = sw ? packed[pos ^ 1][0] : packed[pos][0];
+          val.y = sw ? packed[pos ^ 1][1] : packed[pos][1];
+          val.z = sw ? packed[pos ^ 1][2] : packed[pos][2];
+          val.w = sw ? packed[pos ^ 1][3] : packed[pos][3];
+          *reinterpret_cast<uint4*>(Fw + ((w2 * 16 + w0) * TI + 8 * g8) * 2) = val;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
