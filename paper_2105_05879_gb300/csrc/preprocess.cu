@@ -549,8 +549,8 @@ int launch_small(const Plan& p) {
 // [w1][w0].  That block goes to shared memory (stmatrix) as E[row][w1][p2][w0];
 // stage 3 reads 16 p2 x 16 w0 per (row, w1) back with ldmatrix.trans, multiplies
 // by W_16 and gives [w2][w0]; eight rows of one w1 are packed as row pairs
-// into F[w2][w0][row] and written with one 4-D TMA store (16 rows x 16 w0 x
-// 16 w2).  The CTA's 16-row tile of A, rounded to bfloat16 once, sits in
+// into F[w2][w0][row] (32-byte rows, 32-byte swizzle) and written with one
+// 4-D TMA store (16 rows x 16 w0 x 16 w2).  The CTA's 16-row tile of A, rounded to bfloat16 once, sits in
 // tensor memory (128 KiB), laid out so that each thread's words for one
 // (row, p2) are four consecutive columns of its own lane.  Each stage's input
 // is rounded to bfloat16 (three roundings beside the final one); the identity
@@ -794,19 +794,15 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int pos = 0; pos < 8; ++pos) packed[pos][rp] = pack_bf16x2(v[0][pos], v[1][pos]);
         }
         // position pos: w2 = g + 8 ((pos >> 1) & 1), w0 = 2q + (pos & 1) + 8 (pos >> 2).
-        // Lanes with q >= 2 take the odd/even partner first, so the eight lanes
-        // of a quarter-warp cover four 16-byte bank slots instead of two.
-        const int sw = (q >> 1) & 1;
+        // F uses the tensor map's 32-byte swizzle: the 16-byte half g8 of the
+        // 32-byte row (w2, w0) sits at g8 ^ (bit 2 of w0), so the eight lanes of
+        // a quarter-warp cover four bank slots instead of two.
 #pragma unroll
         for (int pos = 0; pos < 8; ++pos) {
-          const int ps = pos ^ sw;
-          const int w2 = g + 8 * ((ps >> 1) & 1), w0 = 2 * q + (ps & 1) + 8 * (ps >> 2);
-          uint4 val;
-          val.x = sw ? packed[pos ^ 1][0] : packed[pos][0];
-          val.y = sw ? packed[pos ^ 1][1] : packed[pos][1];
-          val.z = sw ? packed[pos ^ 1][2] : packed[pos][2];
-          val.w = sw ? packed[pos ^ 1][3] : packed[pos][3];
-          *reinterpret_cast<uint4*>(Fw + ((w2 * 16 + w0) * TI + 8 * g8) * 2) = val;
+          const int w2 = g + 8 * ((pos >> 1) & 1), w0 = 2 * q + (pos & 1) + 8 * (pos >> 2);
+          const int half = g8 ^ ((w0 >> 2) & 1);
+          *reinterpret_cast<uint4*>(Fw + (w2 * 16 + w0) * (TI * 2) + half * 16) =
+              make_uint4(packed[pos][0], packed[pos][1], packed[pos][2], packed[pos][3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -858,7 +854,7 @@ int launch_d4096_tc(const Plan& p) {
   const cuuint32_t box[4] = {tc::TI, 16, 1, 16};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p.repr, dims, strides, box, es,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return KERDOCK_ERR_UNSUPPORTED;
   auto kern = tc::preprocess_d4096_tc_kernel;
