@@ -305,6 +305,17 @@ int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, int64_t q, in
  * device memory and stream; the source must outlive it. */
 int kerdock_plan_clone(kerdock_plan_t* out, kerdock_plan_t src, int32_t J, int32_t K, int32_t S);
 
+/* Parameters with a guarantee (Theorem 3 with gamma = (eps - delta)/2, as
+ * the argument around Algorithm 1 asks of mu): J = ceil(4 e^2 a^2 / gamma^2)
+ * and K = ceil(2 ln(m / eta)), where a = max_i ||a_i|| (||A||_{2->inf}).
+ * Then for unit x with Ax in Sigma(A, s, delta), ||mu - Ax||_inf < gamma with
+ * probability >= 1 - eta.  Host only; no plan needed.
+ * Errors: INVALID_ARG unless a > 0, eps > delta >= 0, 0 < eta <= 1, m >= 1;
+ * UNSUPPORTED when K exceeds the library's 16 batches or J*K its sample
+ * limit (J and K are still written). */
+int kerdock_theory_parameters(double a_row_norm_max, double eps, double delta, double eta,
+                              int64_t m, int32_t* J, int32_t* K);
+
 /* Synchronise the plan's stream and report the first error any kernel of
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);

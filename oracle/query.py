@@ -10,6 +10,8 @@ with the CUDA library as an interface): sample j of query q is
 with SplitMix64 as published by Steele, Lea and Flood (OOPSLA 2014).
 Batch k of the median of means holds samples j in [kJ, (k+1)J).
 """
+import math
+
 import numpy as np
 
 from . import kerdock
@@ -118,6 +120,15 @@ def apply_one(A, R, x, eps, seed, q, J, K, S, k, lazy=False, return_mu=False):
     if return_mu:
         return idx, val, mu, ells, c
     return idx, val
+
+
+def theorem3_parameters(a_row_norm_max, eps, delta, eta, m):
+    """J and K of Theorem 3 for the accuracy gamma = (eps - delta)/2 that the
+    argument around Algorithm 1 asks of mu, failure probability eta."""
+    gamma = (eps - delta) / 2.0
+    J = math.ceil(4.0 * math.e ** 2 * a_row_norm_max ** 2 / gamma ** 2)
+    K = max(1, math.ceil(2.0 * math.log(m / eta)))
+    return J, K
 
 
 def dense_truth(A, x, eps):

@@ -5,6 +5,8 @@
 // Prop. 5 and every point p of F_2^k, the bit Q_{M_b}(p) that decides the
 // diagonal entry (-1)^{Q(p)} of D_{M_b}.  It is built on the device, one CTA
 // per field element b, straight from the finite-field construction.
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -375,3 +377,19 @@ int kerdock_plan_destroy(kerdock_plan_t plan) {
 }
 
 }  // extern "C"
+
+extern "C" int kerdock_theory_parameters(double a_row_norm_max, double eps, double delta,
+                                         double eta, int64_t m, int32_t* J, int32_t* K) {
+  if (J == nullptr || K == nullptr || !(a_row_norm_max > 0.0) || !(delta >= 0.0) ||
+      !(eps > delta) || !(eta > 0.0) || !(eta <= 1.0) || m < 1)
+    return KERDOCK_ERR_INVALID_ARG;
+  const double gamma = 0.5 * (eps - delta);
+  const double e = 2.718281828459045;  // Euler's number
+  const double j = std::ceil(4.0 * e * e * a_row_norm_max * a_row_norm_max / (gamma * gamma));
+  const double k = std::max(1.0, std::ceil(2.0 * std::log(double(m) / eta)));
+  if (!(j < 2147483647.0)) return KERDOCK_ERR_UNSUPPORTED;
+  *J = int32_t(j);
+  *K = int32_t(k);
+  if (k > double(kd::kMaxK) || j * k > double(kd::kMaxN)) return KERDOCK_ERR_UNSUPPORTED;
+  return KERDOCK_OK;
+}

@@ -39,7 +39,7 @@ EXPORTED = [
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
-    "kerdock_mlp_set_skip",
+    "kerdock_mlp_set_skip", "kerdock_theory_parameters",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -142,6 +142,9 @@ def load_library(path=None):
         "kerdock_mlp_destroy": (ctypes.c_int, [P]),
         "kerdock_refine_scores": (ctypes.c_int, [P, c_vp, c_i64, c_i64, c_vp, c_i32,
                                                  ctypes.c_float, c_i32, c_vp, c_vp, c_vp]),
+        "kerdock_theory_parameters": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, c_i64, ctypes.POINTER(c_i32),
+                                                     ctypes.POINTER(c_i32)]),
         "kerdock_plan_clone": (ctypes.c_int, [ctypes.POINTER(P), P, c_i32, c_i32, c_i32]),
         "kerdock_debug_wait_timeout": (ctypes.c_int, [P, c_i32]),
         "kerdock_sync": (ctypes.c_int, [P]),
@@ -181,6 +184,16 @@ def kerdock_plan_info(plan):
 def kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes, stream):
     _check(load_library().kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes,
                                             stream), "kerdock_plan_bind")
+
+
+def kerdock_theory_parameters(a_row_norm_max, eps, delta, eta, m):
+    """(J, K) of Theorem 3 for ||mu - Ax||_inf < (eps - delta)/2 w.p. >= 1 - eta.
+    Raises for invalid arguments and for (J, K) beyond the library's limits."""
+    J, K = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load_library().kerdock_theory_parameters(float(a_row_norm_max), float(eps), float(delta),
+                                                     float(eta), int(m), ctypes.byref(J),
+                                                     ctypes.byref(K)), "kerdock_theory_parameters")
+    return J.value, K.value
 
 
 def kerdock_set_stream(plan, stream):

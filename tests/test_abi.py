@@ -96,3 +96,25 @@ def test_strerror_and_version(lib):
     assert "timed out" in K.kerdock_strerror(-7)
     assert K.kerdock_strerror(-99) == "unknown error"
     assert K.kerdock_version() >= 100
+
+
+def test_theory_parameters_match_theorem3(lib):
+    # the library's host computation against the oracle's restatement of
+    # Theorem 3 (whose guarantee tests/test_oracle_query.py checks by Monte Carlo)
+    from oracle import query as oq
+    for a, eps, delta, eta, m in [(1.0, 0.5, 0.0, 0.2, 16), (1.0, 0.25, 0.0, 0.5, 64),
+                                  (0.7, 0.6, 0.1, 0.9, 1000), (1.0, 0.9, 0.2, 1.0, 2048)]:
+        J, Kb = K.kerdock_theory_parameters(a, eps, delta, eta, m)
+        assert (J, Kb) == oq.theorem3_parameters(a, eps, delta, eta, m)
+
+
+def test_theory_parameters_errors(lib):
+    for args in [(0.0, 0.5, 0.0, 0.1, 10), (1.0, 0.1, 0.2, 0.1, 10), (1.0, 0.5, -0.1, 0.1, 10),
+                 (1.0, 0.5, 0.0, 0.0, 10), (1.0, 0.5, 0.0, 1.5, 10), (1.0, 0.5, 0.0, 0.1, 0)]:
+        with pytest.raises(K.KerdockError) as ei:
+            K.kerdock_theory_parameters(*args)
+        assert ei.value.code == -1  # KERDOCK_ERR_INVALID_ARG
+    # the guarantee at n = 1024, eps = 0.125, eta = 0.01 needs K = 24 > 16 batches
+    with pytest.raises(K.KerdockError) as ei:
+        K.kerdock_theory_parameters(1.0, 0.125, 0.0, 0.01, 1024)
+    assert ei.value.code == -2  # KERDOCK_ERR_UNSUPPORTED

@@ -107,8 +107,7 @@ def test_theorem3_failure_rate():
     k, n = 4, 16
     A = workloads.random_orthogonal(n, 3)
     gamma, eta = 0.5, 0.2
-    J = math.ceil(4 * math.e ** 2 / gamma ** 2)
-    K = math.ceil(2 * math.log(n / eta))
+    J, K = query.theorem3_parameters(1.0, 2 * gamma, 0.0, eta, n)
     S = kerdock.sample_vectors(n, k)
     R = kerdock.representation_lemma6(A, k).reshape(-1, n)
     L = S.shape[0]
