@@ -6,16 +6,23 @@
 // sign-flipped, zero-padded row (Pi^* a_i)^T D_{M_b}.  The identity basis adds
 // R[d/2][w][i] = sqrt(d) A[i][w] (zero for w >= n).
 //
-// Kernel design (d <= 1024): a CTA owns a tile of 32 rows of A, kept in
-// shared memory across all the bases it processes, so A is read from HBM once.
-// Per basis the sign bits become float sign masks in shared memory (one XOR
-// per element).  Phase 1: a warp g holds, per lane (= row), RG = d/NW
-// consecutive p in registers as float pairs and runs log2(RG) butterfly
-// stages (packed add/sub.f32x2).  One shared-memory exchange then moves the
-// NW warp-owned chunks so that each thread holds two rows x two adjacent w
-// for the remaining log2(NW) stages (packed across the two rows), and stores
-// 8-byte row pairs: a warp store writes two 128-byte runs of consecutive i of
-// output rows R[b][w][.] (float32).
+// Kernels:
+//  * d <= 1024 (preprocess_small_kernel): a CTA owns a tile of 16 rows of A,
+//    kept in shared memory across all the bases it processes, so A is read
+//    from HBM once.  Per basis each thread flips the signs of its p range from
+//    its own sign words (one shift and one XOR per element).  Phase 1: a
+//    thread (row, source) holds RG consecutive p in registers as float pairs
+//    and runs log2(RG) butterfly stages (packed add/sub.f32x2).  One
+//    shared-memory exchange then moves the sources so that each thread holds
+//    two rows x one w for the remaining stages (packed across the two rows),
+//    and stores 8-byte row pairs (streaming stores).  Groups of 16 CTAs own
+//    adjacent tiles and walk the bases in step, so every 128-byte line of an
+//    output row R[b][w][.] is completed by two CTAs at about the same time.
+//  * d = 4096, float32 (preprocess_d4096_kernel): a 4-CTA cluster per 32-row
+//    tile, each CTA holding a quarter of p; the second half of the stages
+//    combines sources pushed over distributed shared memory.
+//  * d = 4096, bfloat16 (preprocess_d4096_tc_kernel, precision form): the
+//    three 16-point stages on the tensor cores.
 #include <cooperative_groups.h>
 #include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
 

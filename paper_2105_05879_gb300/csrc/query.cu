@@ -17,8 +17,8 @@
 //                 warp instruction puts up to 32 rows in flight; it also loads
 //                 x of upcoming queries.
 //   warps 1..3    coefficient warps: draw the same l_j themselves and compute
-//                 c_j for blocks of four samples at a time from the
-//                 lane-transposed sign table and x, ahead of the gather.
+//                 c_j for a ring chunk's samples (1, 2 or 4) at a time from
+//                 the lane-transposed sign table and x, ahead of the gather.
 //   warps 4..11   gather warps: each thread owns fixed 16-byte column granules
 //                 and accumulates c_j R[l_j] in registers in sample order (a
 //                 fixed, deterministic summation order); batch means go to a
