@@ -305,6 +305,21 @@ int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, int64_t q, in
  * device memory and stream; the source must outlive it. */
 int kerdock_plan_clone(kerdock_plan_t* out, kerdock_plan_t src, int32_t J, int32_t K, int32_t S);
 
+/* Algorithm 1's streaming step for q queries that share one sample set: the
+ * N = JK indices kerdock_apply draws for query 0 serve every query of the
+ * batch (each query is still Algorithm 1 with N uniform samples, so Theorem 3
+ * holds per query; failures of different queries become dependent).  The
+ * coefficients X S^T and the batch means C_k R_k / J run as tensor-core
+ * products (bfloat16 operands split hi + lo, float32 accumulation), then the
+ * median, top-S of |mu|, exact refinement and threshold as kerdock_apply.
+ * Outputs as kerdock_apply.  ws: device memory of
+ * kerdock_apply_shared_workspace_bytes(plan, q) bytes, 256-byte aligned.
+ * Errors as kerdock_apply; CAPACITY when ws is smaller than asked. */
+size_t kerdock_apply_shared_workspace_bytes(kerdock_plan_t plan, int64_t q);
+int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                         float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
+                         float* out_val, int32_t* out_count, void* ws, size_t ws_bytes);
+
 /* Parameters with a guarantee (Theorem 3 with gamma = (eps - delta)/2, as
  * the argument around Algorithm 1 asks of mu): J = ceil(4 e^2 a^2 / gamma^2)
  * and K = ceil(2 ln(m / eta)), where a = max_i ||a_i|| (||A||_{2->inf}).

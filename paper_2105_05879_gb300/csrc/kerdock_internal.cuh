@@ -110,6 +110,17 @@ int launch_batch(const LaunchCfg& cfg, const QueryDesc* descs, const int32_t* or
                  const int64_t* cta_start, int grid, cudaStream_t stream);
 constexpr int kQueryThreads = 512;
 
+// C[M x N] (float32, row stride ldc) = sum_k A(m, k) B(n, k) on the tensor
+// cores (bfloat16 operands, float32 accumulation; mlp.cu).
+struct GemmArgs {
+  int M, N, K;
+  const __nv_bfloat16* A;  // element (m, k) at A[m * sAm + k * sAk]
+  int64_t sAm, sAk;
+  const __nv_bfloat16* B;  // element (n, k) at B[n * sBn + k * sBk]
+  int64_t sBn, sBk;
+};
+int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream);
+
 // Launchers (return KERDOCK_OK or a negative error code).
 int launch_signs(const Plan& p);
 int launch_preprocess(const Plan& p);

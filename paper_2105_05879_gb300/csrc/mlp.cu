@@ -19,14 +19,6 @@ namespace {
 
 constexpr int GBM = 64, GBN = 64, GBK = 32, GTHREADS = 128;
 
-struct GemmArgs {
-  int M, N, K;
-  const __nv_bfloat16* A;  // element (m, k) at A[m * sAm + k * sAk]
-  int64_t sAm, sAk;
-  const __nv_bfloat16* B;  // element (n, k) at B[n * sBn + k * sBk]
-  int64_t sBn, sBk;
-};
-
 __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) {
   return *reinterpret_cast<const uint32_t*>(p);
 }
@@ -140,7 +132,7 @@ struct EpiMaskBf16 {  // C = bf16(acc) where H > 0, else 0 (ReLU derivative, rel
 };
 struct EpiF32 {  // C = acc
   float* C;
-  int ldc;
+  int64_t ldc;
   __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v; }
 };
 
@@ -247,6 +239,12 @@ unsigned grid_for(int64_t count, int threads) {
 }
 
 }  // namespace
+
+int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream) {
+  if (g.M < 1 || g.N < 1 || g.K < 1) return KERDOCK_OK;
+  return gemm(g, EpiF32{C, ldc}, stream);
+}
+
 }  // namespace kd
 
 struct kerdock_mlp_s {

@@ -1,0 +1,250 @@
+// shared.cu -- Algorithm 1's streaming step with one sample set shared by a
+// batch of queries.
+//
+// Every query of the batch uses the same N = JK indices l_j (those that
+// kerdock_apply draws for query 0).  Each query is still Algorithm 1 with N
+// independent uniform samples, so Theorem 3 holds per query; only the queries'
+// failure events become dependent.  Sharing turns the two sums of the
+// streaming step into dense products over the batch:
+//   C  = X S^T          (q x N: c_qj = s_{l_j}^T x_q, Algorithm 1)
+//   Y_k = C_k R_k / J   (q x m per batch k: the batch means of Theorem 3)
+// where S holds the N sample vectors (+-1, or sqrt(d) e_w for the identity
+// basis) and R_k the N/K gathered representation rows of batch k.  Both run on
+// the tensor cores with bfloat16 operands and float32 accumulation; float32
+// factors are split as hi + lo (hi = bf16(v), lo = bf16(v - hi)) so that the
+// products keep about 16 significant bits (C S^T: x_hi, x_lo against exact
+// +-1; C R: C_hi R_hi + C_lo R_hi + C_hi R_lo, or C_hi R + C_lo R for a
+// bfloat16 representation).  The entrywise median over the K batch means, the
+// top-S of |mu| and the exact refinement with the threshold (a6-a8) follow.
+#include "kerdock_internal.cuh"
+
+extern "C" int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, int64_t q,
+                                     int64_t ldx, const float* scores, int32_t S, float eps,
+                                     int32_t flags, int32_t* out_idx, float* out_val,
+                                     int32_t* out_count);
+
+namespace kd {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// l_j and the sample vector s_{l_j} (restricted to the first n coordinates,
+// Algorithm 1's Pi), twice per row: S2[j] = [s | s] against X2 = [x_hi | x_lo].
+__global__ void shared_samples_kernel(uint64_t seed, int64_t N, int64_t L, int kbits, int64_t n,
+                                      const uint32_t* __restrict__ signs, int64_t sign_words,
+                                      float sqrt_d, int64_t* ells, __nv_bfloat16* S2) {
+  const int64_t d = int64_t(1) << kbits;
+  for (int64_t j = blockIdx.x; j < N; j += gridDim.x) {
+    const uint64_t l = sample_index(seed, uint64_t(j), uint64_t(L));
+    if (threadIdx.x == 0) ells[j] = int64_t(l);
+    const int64_t b = int64_t(l >> kbits), w = int64_t(l & uint64_t(d - 1));
+    __nv_bfloat16* row = S2 + j * 2 * n;
+    for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+      float v;
+      if (b == d / 2) {
+        v = p == w ? sqrt_d : 0.f;
+      } else {
+        const uint32_t bit = (__ldg(signs + b * sign_words + (p >> 5)) >> (p & 31)) & 1u;
+        const uint32_t par = uint32_t(__popcll(uint64_t(w) & uint64_t(p))) & 1u;
+        v = (bit ^ par) ? -1.f : 1.f;
+      }
+      row[p] = __float2bfloat16_rn(v);
+      row[n + p] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// X2[r] = [x_hi | x_lo] for every query row.
+__global__ void split_queries_kernel(const float* __restrict__ X, int64_t q, int64_t ldx,
+                                     int64_t n, __nv_bfloat16* X2) {
+  for (int64_t r = blockIdx.x; r < q; r += gridDim.x)
+    for (int64_t p = threadIdx.x; p < n; p += blockDim.x) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(X[r * ldx + p], hi, lo);
+      X2[r * 2 * n + p] = hi;
+      X2[r * 2 * n + n + p] = lo;
+    }
+}
+
+// Per batch k the P copies of its J gathered rows stacked along the
+// contraction index: float32 [R_hi; R_hi; R_lo], bfloat16 [R; R].
+template <typename RT>
+__global__ void gather_rows_kernel(const RT* __restrict__ R, int64_t ldr, const int64_t* ells,
+                                   int64_t J, int64_t N, __nv_bfloat16* G3) {
+  constexpr int P = sizeof(RT) == 4 ? 3 : 2;
+  for (int64_t j = blockIdx.x; j < N; j += gridDim.x) {
+    const int64_t k = j / J, jj = j - k * J;
+    const RT* src = R + ells[j] * ldr;
+    __nv_bfloat16* dst = G3 + (k * P * J + jj) * ldr;
+    for (int64_t i = threadIdx.x; i < ldr; i += blockDim.x) {
+      if (P == 3) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(float(src[i]), hi, lo);
+        dst[i] = hi;
+        dst[J * ldr + i] = hi;
+        dst[2 * J * ldr + i] = lo;
+      } else {
+        const __nv_bfloat16 v = *reinterpret_cast<const __nv_bfloat16*>(&src[i]);
+        dst[i] = v;
+        dst[J * ldr + i] = v;
+      }
+    }
+  }
+}
+
+// A3[k][r] = P pieces of C[r][batch k] / J: float32 [c_hi | c_lo | c_hi],
+// bfloat16 [c_hi | c_lo].
+__global__ void split_coef_kernel(const float* __restrict__ C, int64_t q, int64_t N, int64_t J,
+                                  int64_t K, int P, float inv_J, __nv_bfloat16* A3) {
+  const int64_t PJ = P * J;
+  for (int64_t r = blockIdx.x; r < q; r += gridDim.x)
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      const int64_t k = j / J, jj = j - k * J;
+      __nv_bfloat16 hi, lo;
+      split_bf16(C[r * N + j] * inv_J, hi, lo);
+      __nv_bfloat16* a = A3 + (k * q + r) * PJ;
+      a[jj] = hi;
+      a[J + jj] = lo;
+      if (P == 3) a[2 * J + jj] = hi;
+    }
+}
+
+// scores = |median over the K batch means| (mean of the two middle values for
+// even K), q x m.
+__global__ void median_abs_kernel(const float* __restrict__ Y, int64_t q, int64_t m, int64_t ldr,
+                                  int K, float* scores) {
+  const int64_t total = q * m;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = t / m, i = t - r * m;
+    float v[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) v[k] = k < K ? Y[(int64_t(k) * q + r) * ldr + i] : 0.f;
+    float med;
+    if (K == 1) {
+      med = v[0];
+    } else if (K == 2) {
+      med = 0.5f * (v[0] + v[1]);
+    } else {
+      const int r_lo = (K - 1) / 2, r_hi = K / 2;
+      float lo = 0.f, hi = 0.f;
+#pragma unroll
+      for (int a = 0; a < kMaxK; ++a) {
+        if (a >= K) break;
+        int rank = 0;
+#pragma unroll
+        for (int c = 0; c < kMaxK; ++c)
+          if (c < K && (v[c] < v[a] || (v[c] == v[a] && c < a))) ++rank;
+        if (rank == r_lo) lo = v[a];
+        if (rank == r_hi) hi = v[a];
+      }
+      med = (K & 1) ? lo : 0.5f * (lo + hi);
+    }
+    scores[t] = fabsf(med);
+  }
+}
+
+struct SharedLayout {
+  size_t ells, S2, X2, C, A3, G3, Y, scores, total;
+};
+
+SharedLayout shared_layout(const Plan& p, int64_t q) {
+  const int64_t N = p.N, J = p.J, K = p.K, n = p.n, m = p.m, ldr = p.ldr;
+  const int64_t P = p.dtype == KERDOCK_BF16 ? 2 : 3;
+  SharedLayout s{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  s.ells = take(size_t(N) * 8);
+  s.S2 = take(size_t(N) * 2 * n * 2);
+  s.X2 = take(size_t(q) * 2 * n * 2);
+  s.C = take(size_t(q) * N * 4);
+  s.A3 = take(size_t(K) * q * P * J * 2);
+  s.G3 = take(size_t(K) * P * J * ldr * 2);
+  s.Y = take(size_t(K) * q * ldr * 4);
+  s.scores = take(size_t(q) * m * 4);
+  s.total = off;
+  return s;
+}
+
+unsigned grid_for(int64_t units) {
+  return unsigned(units < 1 ? 1 : (units > 65535 ? 65535 : units));
+}
+
+}  // namespace
+}  // namespace kd
+
+extern "C" size_t kerdock_apply_shared_workspace_bytes(kerdock_plan_t plan, int64_t q) {
+  if (plan == nullptr || q <= 0) return 0;
+  return kd::shared_layout(plan->p, q).total;
+}
+
+extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q,
+                                    int64_t ldx, float eps, uint64_t seed, int32_t flags,
+                                    int32_t* out_idx, float* out_val, int32_t* out_count,
+                                    void* ws, size_t ws_bytes) {
+  if (plan == nullptr || q < 0) return KERDOCK_ERR_INVALID_ARG;
+  kd::Plan& p = plan->p;
+  if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
+  if (!p.preprocessed) return KERDOCK_ERR_NOT_PREPROCESSED;
+  if (q == 0) return KERDOCK_OK;
+  if (X_dev == nullptr || out_idx == nullptr || out_val == nullptr || out_count == nullptr ||
+      ldx < p.n || flags < 0 || flags > KERDOCK_FLAG_FULL_OUTPUT)
+    return KERDOCK_ERR_INVALID_ARG;
+  if (!(flags & KERDOCK_FLAG_FULL_OUTPUT) && !(eps > 0.0f)) return KERDOCK_ERR_INVALID_ARG;
+  if (q > 65535 * int64_t(64)) return KERDOCK_ERR_UNSUPPORTED;  // GEMM grid rows
+  const kd::SharedLayout lay = kd::shared_layout(p, q);
+  if (ws == nullptr || ws_bytes < lay.total) return KERDOCK_ERR_CAPACITY;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return KERDOCK_ERR_ALIGNMENT;
+  char* base = static_cast<char*>(ws);
+  int64_t* ells = reinterpret_cast<int64_t*>(base + lay.ells);
+  __nv_bfloat16* S2 = reinterpret_cast<__nv_bfloat16*>(base + lay.S2);
+  __nv_bfloat16* X2 = reinterpret_cast<__nv_bfloat16*>(base + lay.X2);
+  float* C = reinterpret_cast<float*>(base + lay.C);
+  __nv_bfloat16* A3 = reinterpret_cast<__nv_bfloat16*>(base + lay.A3);
+  __nv_bfloat16* G3 = reinterpret_cast<__nv_bfloat16*>(base + lay.G3);
+  float* Y = reinterpret_cast<float*>(base + lay.Y);
+  float* scores = reinterpret_cast<float*>(base + lay.scores);
+  const int64_t N = p.N, J = p.J, K = p.K, n = p.n, m = p.m, ldr = p.ldr;
+  const int P = p.dtype == KERDOCK_BF16 ? 2 : 3;
+  cudaStream_t st = p.stream;
+
+  kd::shared_samples_kernel<<<kd::grid_for(N), kd::kThreads, 0, st>>>(
+      seed, N, p.L, p.k, n, p.signs(), p.sign_words, float(int64_t(1) << (p.k / 2)), ells, S2);
+  KD_CUDA_TRY(cudaGetLastError());
+  kd::split_queries_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(X_dev, q, ldx, n, X2);
+  KD_CUDA_TRY(cudaGetLastError());
+  if (P == 3)
+    kd::gather_rows_kernel<float><<<kd::grid_for(N), kd::kThreads, 0, st>>>(
+        static_cast<const float*>(p.repr), ldr, ells, J, N, G3);
+  else
+    kd::gather_rows_kernel<__nv_bfloat16><<<kd::grid_for(N), kd::kThreads, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(p.repr), ldr, ells, J, N, G3);
+  KD_CUDA_TRY(cudaGetLastError());
+  // C = X S^T over [x_hi | x_lo] and [s | s]
+  kd::GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
+  int rc = kd::gemm_bf16_f32(g1, C, N, st);
+  if (rc != KERDOCK_OK) return rc;
+  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(C, q, N, J, K, P,
+                                                                  1.0f / float(J), A3);
+  KD_CUDA_TRY(cudaGetLastError());
+  for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
+    kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * P * J, int64_t(P) * J, 1,
+                    G3 + k * P * J * ldr, 1, ldr};
+    rc = kd::gemm_bf16_f32(g2, Y + k * q * ldr, ldr, st);
+    if (rc != KERDOCK_OK) return rc;
+  }
+  kd::median_abs_kernel<<<kd::grid_for((q * m + kd::kThreads - 1) / kd::kThreads), kd::kThreads,
+                          0, st>>>(Y, q, m, ldr, int(K), scores);
+  KD_CUDA_TRY(cudaGetLastError());
+  return kerdock_refine_scores(plan, X_dev, q, ldx, scores, p.S, eps, flags, out_idx, out_val,
+                               out_count);
+}

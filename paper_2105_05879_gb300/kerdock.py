@@ -39,7 +39,8 @@ EXPORTED = [
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
-    "kerdock_mlp_set_skip", "kerdock_theory_parameters",
+    "kerdock_mlp_set_skip", "kerdock_theory_parameters", "kerdock_apply_shared_workspace_bytes",
+    "kerdock_apply_shared",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -142,6 +143,9 @@ def load_library(path=None):
         "kerdock_mlp_destroy": (ctypes.c_int, [P]),
         "kerdock_refine_scores": (ctypes.c_int, [P, c_vp, c_i64, c_i64, c_vp, c_i32,
                                                  ctypes.c_float, c_i32, c_vp, c_vp, c_vp]),
+        "kerdock_apply_shared_workspace_bytes": (c_sz, [P, c_i64]),
+        "kerdock_apply_shared": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float, ctypes.c_uint64,
+                                                c_i32, c_vp, c_vp, c_vp, c_vp, c_sz]),
         "kerdock_theory_parameters": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_double, c_i64, ctypes.POINTER(c_i32),
                                                      ctypes.POINTER(c_i32)]),
@@ -184,6 +188,13 @@ def kerdock_plan_info(plan):
 def kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes, stream):
     _check(load_library().kerdock_plan_bind(plan, repr_ptr, repr_bytes, table_ptr, table_bytes,
                                             stream), "kerdock_plan_bind")
+
+
+def kerdock_apply_shared(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr, cnt_ptr, ws_ptr,
+                         ws_bytes):
+    _check(load_library().kerdock_apply_shared(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
+                                               val_ptr, cnt_ptr, ws_ptr, ws_bytes),
+           "kerdock_apply_shared")
 
 
 def kerdock_theory_parameters(a_row_norm_max, eps, delta, eta, m):
@@ -480,6 +491,19 @@ class KerdockPlan:
 
     def sync(self):
         kerdock_sync(self.handle)
+
+    def apply_shared(self, X, eps, seed, flags=0, out=None):
+        """All rows of X share one sample set (kerdock_apply_shared)."""
+        t = self.torch
+        assert X.dtype == t.float32 and X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        q = X.shape[0]
+        idx, val, cnt = out if out is not None else self.alloc_outputs(q)
+        nb = load_library().kerdock_apply_shared_workspace_bytes(self.handle, q)
+        ws = t.empty(max(nb, 1), dtype=t.uint8, device=self.device)
+        self._sync_stream()
+        kerdock_apply_shared(self.handle, X.data_ptr(), q, X.stride(0), float(eps), int(seed), flags,
+                             idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), ws.data_ptr(), nb)
+        return idx, val, cnt
 
     def clone(self, J, K, S):
         """A plan over the same representation with other (J, K, S)."""
