@@ -101,6 +101,149 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g, c
       }
 }
 
+// The same product for 16-byte-aligned operands: each operand tile is moved by
+// cp.async in 16-byte pieces along its contiguous dimension (k for a
+// "k-major" operand, m or n otherwise) through a GSTAGES-deep shared-memory
+// ring, and the mma fragments are read with ldmatrix (.trans for the
+// m/n-major tiles).  Pieces past the matrix edge are zero-filled by the copy
+// itself (source size below 16 bytes), so ragged M, N and K need no branch in
+// the inner loop.
+constexpr int GSTAGES = 4;
+constexpr int KM_LD = GBK + 8;   // k-major tile [rows][GBK], padded: 80-byte rows
+constexpr int MM_LD = GBM + 8;   // m/n-major tile [GBK][rows], padded: 144-byte rows
+constexpr int TILE_ELEMS = GBM * KM_LD > GBK * MM_LD ? GBM * KM_LD : GBK * MM_LD;
+static_assert(GBM == GBN, "one tile shape serves both operands");
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+// Issue the copies of one GBK slice of a GBM-row operand tile: rows r0.., k0..
+// of a rows x K matrix with element (r, k) at P[r * s_r + k * s_k].
+template <bool KMAJOR>
+__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, const __nv_bfloat16* P, int64_t s_r,
+                                          int64_t s_k, int rows, int K, int r0, int k0, int tid) {
+  constexpr int PIECES = GBM * GBK / 8;
+#pragma unroll
+  for (int c = tid; c < PIECES; c += GTHREADS) {
+    int rr, kk, bytes;
+    const __nv_bfloat16* src = P;
+    uint32_t d;
+    if (KMAJOR) {  // piece = 8 consecutive k of one row
+      rr = c / (GBK / 8);
+      kk = (c % (GBK / 8)) * 8;
+      const int gr = r0 + rr, gk = k0 + kk;
+      bytes = (gr < rows && gk < K) ? 2 * min(8, K - gk) : 0;
+      if (bytes) src = P + int64_t(gr) * s_r + gk;
+      d = smem_addr(dst + rr * KM_LD + kk);
+    } else {  // piece = 8 consecutive rows of one k
+      kk = c / (GBM / 8);
+      rr = (c % (GBM / 8)) * 8;
+      const int gr = r0 + rr, gk = k0 + kk;
+      bytes = (gk < K && gr < rows) ? 2 * min(8, rows - gr) : 0;
+      if (bytes) src = P + int64_t(gk) * s_k + gr;
+      d = smem_addr(dst + kk * MM_LD + rr);
+    }
+    cp_async16(d, src, bytes);
+  }
+}
+
+template <bool AK, bool BK, class Epi>
+__global__ void __launch_bounds__(GTHREADS) gemm_bf16_async_kernel(const GemmArgs g,
+                                                                   const Epi epi) {
+  __shared__ __align__(128) __nv_bfloat16 As[GSTAGES][TILE_ELEMS];
+  __shared__ __align__(128) __nv_bfloat16 Bs[GSTAGES][TILE_ELEMS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int group = lane >> 2, tig = lane & 3;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const int ktiles = (g.K + GBK - 1) / GBK;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  auto issue = [&](int kt) {
+    if (kt < ktiles) {
+      const int s = kt % GSTAGES;
+      load_tile<AK>(As[s], g.A, g.sAm, g.sAk, g.M, g.K, m0, kt * GBK, tid);
+      load_tile<BK>(Bs[s], g.B, g.sBn, g.sBk, g.N, g.K, n0, kt * GBK, tid);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+#pragma unroll
+  for (int s = 0; s < GSTAGES - 1; ++s) issue(s);
+  const int j8 = lane >> 3, r8 = lane & 7;
+  for (int kt = 0; kt < ktiles; ++kt) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(GSTAGES - 2) : "memory");
+    __syncthreads();  // slice kt visible to all; slot of kt - 1 free again
+    issue(kt + GSTAGES - 1);
+    const __nv_bfloat16* a_s = As[kt % GSTAGES];
+    const __nv_bfloat16* b_s = Bs[kt % GSTAGES];
+#pragma unroll
+    for (int ks = 0; ks < GBK; ks += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // matrices in fragment order: (m 0-7, k 0-7), (m 8-15, k 0-7),
+        // (m 0-7, k 8-15), (m 8-15, k 8-15)
+        if (AK)
+          ldsm_x4(smem_addr(a_s + (wm + mt * 16 + (lane & 15)) * KM_LD + ks + (lane >> 4) * 8),
+                  a[mt]);
+        else
+          ldsm_x4_t(smem_addr(a_s + (ks + (j8 >> 1) * 8 + r8) * MM_LD + wm + mt * 16 +
+                              (j8 & 1) * 8),
+                    a[mt]);
+      }
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        // matrices: (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+        uint32_t t[4];
+        const int nb = wn + np * 16 + (j8 >> 1) * 8, kb = ks + (j8 & 1) * 8;
+        if (BK)
+          ldsm_x4(smem_addr(b_s + (nb + r8) * KM_LD + kb), t);
+        else
+          ldsm_x4_t(smem_addr(b_s + (kb + r8) * MM_LD + nb), t);
+        b[2 * np][0] = t[0];
+        b[2 * np][1] = t[1];
+        b[2 * np + 1][0] = t[2];
+        b[2 * np + 1][1] = t[3];
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+          mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[nt][0], b[nt][1]);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = m0 + wm + mt * 16 + group + (e >= 2 ? 8 : 0);
+        const int c = n0 + wn + nt * 8 + tig * 2 + (e & 1);
+        if (r < g.M && c < g.N) epi(r, c, acc[mt][nt][e]);
+      }
+}
+
 struct EpiBiasReluBf16 {  // C = bf16(relu(acc + bias[c]))
   const float* bias;
   __nv_bfloat16* C;
@@ -136,10 +279,26 @@ struct EpiF32 {  // C = acc
   __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v; }
 };
 
+// Operands whose rows along the contiguous dimension start on 16-byte
+// boundaries take the cp.async kernel; any other layout the element-wise one.
 template <class Epi>
 int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
   const dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM));
-  gemm_bf16_kernel<Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+  auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const bool ak = g.sAk == 1 && g.sAm % 8 == 0, am = g.sAm == 1 && g.sAk % 8 == 0;
+  const bool bk = g.sBk == 1 && g.sBn % 8 == 0, bn = g.sBn == 1 && g.sBk % 8 == 0;
+  if ((ak || am) && (bk || bn) && aligned16(g.A) && aligned16(g.B)) {
+    if (ak && bk)
+      gemm_bf16_async_kernel<true, true, Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+    else if (ak)
+      gemm_bf16_async_kernel<true, false, Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+    else if (bk)
+      gemm_bf16_async_kernel<false, true, Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+    else
+      gemm_bf16_async_kernel<false, false, Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+  } else {
+    gemm_bf16_kernel<Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
+  }
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }

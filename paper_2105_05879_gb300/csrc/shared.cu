@@ -100,14 +100,14 @@ __global__ void gather_rows_kernel(const RT* __restrict__ R, int64_t ldr, const 
 // A3[k][r] = P pieces of C[r][batch k] / J: float32 [c_hi | c_lo | c_hi],
 // bfloat16 [c_hi | c_lo].
 __global__ void split_coef_kernel(const float* __restrict__ C, int64_t q, int64_t N, int64_t J,
-                                  int64_t K, int P, float inv_J, __nv_bfloat16* A3) {
-  const int64_t PJ = P * J;
+                                  int64_t K, int P, int64_t lda3, float inv_J,
+                                  __nv_bfloat16* A3) {
   for (int64_t r = blockIdx.x; r < q; r += gridDim.x)
     for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
       const int64_t k = j / J, jj = j - k * J;
       __nv_bfloat16 hi, lo;
       split_bf16(C[r * N + j] * inv_J, hi, lo);
-      __nv_bfloat16* a = A3 + (k * q + r) * PJ;
+      __nv_bfloat16* a = A3 + (k * q + r) * lda3;
       a[jj] = hi;
       a[J + jj] = lo;
       if (P == 3) a[2 * J + jj] = hi;
@@ -149,6 +149,10 @@ __global__ void median_abs_kernel(const float* __restrict__ Y, int64_t q, int64_
   }
 }
 
+// Row stride of A3: P * J rounded up to 8 elements so that every row starts on
+// a 16-byte boundary (the padding is never read: the GEMM's K is P * J).
+int64_t a3_stride(int64_t P, int64_t J) { return (P * J + 7) / 8 * 8; }
+
 struct SharedLayout {
   size_t ells, S2, X2, C, A3, G3, Y, scores, total;
 };
@@ -167,7 +171,7 @@ SharedLayout shared_layout(const Plan& p, int64_t q) {
   s.S2 = take(size_t(N) * 2 * n * 2);
   s.X2 = take(size_t(q) * 2 * n * 2);
   s.C = take(size_t(q) * N * 4);
-  s.A3 = take(size_t(K) * q * P * J * 2);
+  s.A3 = take(size_t(K) * q * a3_stride(P, J) * 2);
   s.G3 = take(size_t(K) * P * J * ldr * 2);
   s.Y = take(size_t(K) * q * ldr * 4);
   s.scores = take(size_t(q) * m * 4);
@@ -233,11 +237,12 @@ extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int
   kd::GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
   int rc = kd::gemm_bf16_f32(g1, C, N, st);
   if (rc != KERDOCK_OK) return rc;
-  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(C, q, N, J, K, P,
+  const int64_t lda3 = kd::a3_stride(P, J);
+  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(C, q, N, J, K, P, lda3,
                                                                   1.0f / float(J), A3);
   KD_CUDA_TRY(cudaGetLastError());
   for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
-    kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * P * J, int64_t(P) * J, 1,
+    kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * lda3, lda3, 1,
                     G3 + k * P * J * ldr, 1, ldr};
     rc = kd::gemm_bf16_f32(g2, Y + k * q * ldr, ldr, st);
     if (rc != KERDOCK_OK) return rc;
