@@ -656,6 +656,97 @@ def run_fig1(args, K, torch, peak):
     }
 
 
+def run_shared(args, K, torch, peak):
+    """Shared-sample batched query on the n = m = 1024 workload (1000 queries,
+    J = 375, K = 2): one sample set for the whole batch, so the coefficients and
+    batch means are two dense products (split-bfloat16 on tensor cores), then
+    the median and the score-ranked refinement.  Each step is the Lemma 6
+    preprocessing plus one batched query, as in the main line; the per-query
+    mode is timed beside it on the same plan."""
+    wl = workloads.WORKLOADS[WORKLOAD]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    A_np = wl.make_A().astype(np.float32)
+    X_np = workloads.queries_from_codes(A_np.astype(np.float64), wl.make_codes()).astype(np.float32)
+    A = torch.from_numpy(A_np).to(dev)
+    X = torch.from_numpy(X_np).to(dev)
+    A64 = A.double()
+    q = X.shape[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lib = K.load_library()
+    bf16_peak = None
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            bf16_peak = json.load(fh).get("bf16_tflops")
+    res = {}
+    for dtype in ("f32", "bf16"):
+        plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S, dtype=dtype, device=dev)
+        idx, val, cnt = plan.alloc_outputs(q)
+        sptr = stream.cuda_stream
+        nb = lib.kerdock_apply_shared_workspace_bytes(plan.handle, q)
+        ws_sh = torch.empty(nb, dtype=torch.uint8, device=dev)
+        ws = plan.workspace(q)
+        wsp, wsb = (ws.data_ptr(), ws.numel()) if ws is not None else (None, 0)
+        pre = lambda: (K.kerdock_plan_bind(plan.handle, plan.repr.data_ptr(), plan.repr.numel(),
+                                           plan.table.data_ptr(), plan.table.numel(), sptr),
+                       K.kerdock_preprocess(plan.handle, A.data_ptr(), A.stride(0)))
+        shared = lambda: K.kerdock_apply_shared(plan.handle, X.data_ptr(), q, X.stride(0), wl.eps,
+                                                wl.seed_apply, 0, idx.data_ptr(), val.data_ptr(),
+                                                cnt.data_ptr(), ws_sh.data_ptr(), nb)
+        single = lambda: K.kerdock_apply(plan.handle, X.data_ptr(), q, X.stride(0), wl.eps,
+                                         wl.seed_apply, 0, idx.data_ptr(), val.data_ptr(),
+                                         cnt.data_ptr(), wsp, wsb)
+        for _ in range(args.warmup):
+            pre()
+            shared()
+        plan.sync()
+        ok = _support_match(torch, A64, X, idx, cnt, wl.eps)
+        times = {"pre": [], "shared": [], "single": []}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for _ in range(args.steps):
+            for key, fn in (("pre", pre), ("shared", shared), ("single", single)):
+                flush.zero_()
+                ev[0].record(stream)
+                fn()
+                ev[1].record(stream)
+                ev[1].synchronize()
+                times[key].append(ev[0].elapsed_time(ev[1]))
+        plan.sync()
+        pre_ms, sh_ms, one_ms = (float(np.mean(times[k])) for k in ("pre", "shared", "single"))
+        P = 2 if dtype == "bf16" else 3
+        N = wl.J * wl.K
+        flops = 2.0 * q * N * 2 * wl.n + wl.K * 2.0 * q * wl.m * P * wl.J
+        res[dtype] = {
+            "ms_per_step": round(pre_ms + sh_ms, 4),
+            "queries/s": round(q / ((pre_ms + sh_ms) / 1e3), 1),
+            "preprocess_ms": round(pre_ms, 4),
+            "shared_query": {"ms": round(sh_ms, 4), "queries/s": round(q / (sh_ms / 1e3), 1),
+                             "product_GFLOP": round(flops / 1e9, 3),
+                             "product_TFLOP/s_over_query": round(flops / sh_ms / 1e9, 1)},
+            "per_query_mode_ms": round(one_ms, 4),
+            "support_match_dense": f"{ok}/{q}",
+        }
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+    f = res["f32"]
+    return {
+        "metric": METRIC, "value": f["queries/s"], "unit": "queries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random orthogonal A, sparse codes; Sec. 4 recipe)",
+        "config": {"workload": (f"shared-sample form: n=m=1024, {q} queries sharing one sample "
+                                f"set, eps={wl.eps}, J={wl.J}, K={wl.K}, S={wl.S}"),
+                   "form": "shared", "l2": "256 MiB buffer written before every timed call"},
+        "f32": f, "bf16": res["bf16"], "bf16_peak_tflops": bf16_peak,
+        # per dtype and step: sign tables + preprocess (2), the shared query
+        # (samples, split, gather, product, split, K products, median, refine)
+        # and the per-query kernel (1)
+        "gpu_launches": 2 * args.steps * (2 + 7 + wl.K + 1),
+    }
+
+
 def run_form(args):
     import torch
     from paper_2105_05879_gb300 import build as kbuild
@@ -665,7 +756,7 @@ def run_form(args):
     K.load_library()
     peak, _ = measured_peaks()
     fn = {"n4096_bf16": run_precision, "mixed_batch": run_batch, "n2048_learned": run_learned,
-          "fig1": run_fig1}
+          "fig1": run_fig1, "n1024_shared": run_shared}
     line = fn[args.workload](args, K, torch, peak)
     print(json.dumps(line), flush=True)
 
@@ -762,7 +853,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1"])
+                    choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1",
+                             "n1024_shared"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_oracle_queries", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()

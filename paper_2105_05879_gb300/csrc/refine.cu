@@ -45,17 +45,19 @@ struct RefineArgs {
   int64_t ldx, Q;
   const float* scores;  // Q x m
   int S, flags, a_vec4;
+  int64_t xs_off;  // byte offset of the staged query in shared memory (16-aligned)
   float eps;
   int32_t* out_idx;
   float* out_val;
   int32_t* out_count;
 };
 
-__global__ void __launch_bounds__(kRThreads) score_refine_kernel(const RefineArgs a) {
+__global__ void __launch_bounds__(kRThreads, 4) score_refine_kernel(const RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* keys = reinterpret_cast<uint32_t*>(smem);
   int32_t* sel = reinterpret_cast<int32_t*>(keys + a.m);
   float* vals = reinterpret_cast<float*>(sel + a.S);
+  float* xs = reinterpret_cast<float*>(smem + a.xs_off);
   __shared__ uint32_t hist[256];
   __shared__ int scan[kRWarps];
   __shared__ uint32_t s_digit, s_remaining;
@@ -64,6 +66,10 @@ __global__ void __launch_bounds__(kRThreads) score_refine_kernel(const RefineArg
   for (int64_t q = blockIdx.x; q < a.Q; q += gridDim.x) {
     const float* sc = a.scores + q * a.m;
     for (int i = tid; i < m; i += kRThreads) keys[i] = ordered_key(sc[i]);
+    // the query is read from global memory once and kept next to the keys:
+    // every row group of the refinement below reads it again
+    const float* xg = a.X + q * a.ldx;
+    for (int64_t p = tid; p < a.n; p += kRThreads) xs[p] = xg[p];
     __syncthreads();
     uint32_t prefix = 0, mask = 0, remaining = uint32_t(a.S);
     for (int pass = 0; pass < 4; ++pass) {
@@ -142,17 +148,41 @@ __global__ void __launch_bounds__(kRThreads) score_refine_kernel(const RefineArg
       const uint32_t rbytes = uint32_t(a.n) * 4u;
       for (int r = tid; r < a.S; r += kRThreads) bulk_prefetch_l2(a.A + int64_t(sel[r]) * a.lda, rbytes);
     }
-    const float* x = a.X + q * a.ldx;
-    const bool xv4 = a.a_vec4 && (a.ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+    const float* x = xs;
+    const bool xv4 = a.a_vec4;
     for (int r0 = warp * 4; r0 < a.S; r0 += kRWarps * 4) {
       float racc[4] = {0.f, 0.f, 0.f, 0.f};
       const float* arow[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) arow[u] = a.A + int64_t(sel[r0 + u < a.S ? r0 + u : r0]) * a.lda;
       if (xv4) {
+        // four 16-byte pieces of each of the four rows requested before any
+        // is used (20 loads in flight per lane against the L2 latency), then
+        // the tail piece by piece; the sum order is p4 = lane, lane + 32, ...
         const int n4 = int(a.n >> 2);
-        for (int p4 = lane; p4 < n4; p4 += 32) {
-          const float4 xq = __ldg(reinterpret_cast<const float4*>(x) + p4);
+        const float4* xp = reinterpret_cast<const float4*>(x);
+        int p4 = lane;
+        for (; p4 + 96 < n4; p4 += 128) {
+          float4 xq[4], av[4][4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            xq[t] = xp[p4 + 32 * t];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              av[u][t] = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4 + 32 * t);
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              racc[u] = fmaf(av[u][t].x, xq[t].x, racc[u]);
+              racc[u] = fmaf(av[u][t].y, xq[t].y, racc[u]);
+              racc[u] = fmaf(av[u][t].z, xq[t].z, racc[u]);
+              racc[u] = fmaf(av[u][t].w, xq[t].w, racc[u]);
+            }
+        }
+        for (; p4 < n4; p4 += 32) {
+          const float4 xq = xp[p4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const float4 av = __ldg(reinterpret_cast<const float4*>(arow[u]) + p4);
@@ -164,9 +194,9 @@ __global__ void __launch_bounds__(kRThreads) score_refine_kernel(const RefineArg
         }
       } else {
         for (int64_t p = lane; p < a.n; p += 32) {
-          const float xs = __ldg(x + p);
+          const float xv = x[p];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xs, racc[u]);
+          for (int u = 0; u < 4; ++u) racc[u] = fmaf(__ldg(arow[u] + p), xv, racc[u]);
         }
       }
 #pragma unroll
@@ -233,7 +263,8 @@ extern "C" int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, in
   a.out_idx = out_idx;
   a.out_val = out_val;
   a.out_count = out_count;
-  const size_t smem = size_t(p.m) * 4 + size_t(S) * 8;
+  a.xs_off = int64_t((size_t(p.m) * 4 + size_t(S) * 8 + 15) / 16 * 16);
+  const size_t smem = size_t(a.xs_off) + size_t(p.n) * 4;
   KD_CUDA_TRY(cudaFuncSetAttribute(kd::score_refine_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int64_t grid = int64_t(p.num_sms) * 8;
