@@ -118,8 +118,21 @@ struct GemmArgs {
   int64_t sAm, sAk;
   const __nv_bfloat16* B;  // element (n, k) at B[n * sBn + k * sBk]
   int64_t sBn, sBk;
+  int kc;  // k range of one slice when K is split (a multiple of 32), 0: no split
 };
 int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream);
+
+// Split of K into slices so that a small M x N product still puts about four
+// 64 x 64 tiles on every SM: slice z covers k in [z kc, (z + 1) kc) and writes
+// its partial product to its own M x N plane; the reader sums the planes in
+// order z = 0, 1, ... (deterministic).
+struct GemmSplit {
+  int slices, kc;
+};
+GemmSplit gemm_split(int64_t M, int64_t N, int64_t K, int num_sms);
+// The split product: plane z at C + z * plane (row stride ldc).
+int gemm_bf16_f32_split(GemmArgs g, const GemmSplit& sp, float* C, int64_t ldc, int64_t plane,
+                        cudaStream_t stream);
 
 // Launchers (return KERDOCK_OK or a negative error code).
 int launch_signs(const Plan& p);

@@ -9,6 +9,7 @@
 //   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3.
 // Every product of the forward and backward passes is one strided GEMM kernel
 // C = op(A) op(B)^T with a fused epilogue (bias, ReLU, ReLU mask, FP32/BF16).
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -50,18 +51,20 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_kernel(const GemmArgs g, c
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-  for (int k0 = 0; k0 < g.K; k0 += GBK) {
+  const int kbeg = g.kc ? int(blockIdx.z) * g.kc : 0;
+  const int kend = g.kc ? min(g.K, kbeg + g.kc) : g.K;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
     for (int i = tid; i < GBM * GBK; i += GTHREADS) {
       int mm, kk;
       if (g.sAk == 1) { mm = i / GBK; kk = i % GBK; } else { mm = i % GBM; kk = i / GBM; }
       const int gm = m0 + mm, gk = k0 + kk;
-      As[mm][kk] = (gm < g.M && gk < g.K) ? g.A[int64_t(gm) * g.sAm + int64_t(gk) * g.sAk] : zero;
+      As[mm][kk] = (gm < g.M && gk < kend) ? g.A[int64_t(gm) * g.sAm + int64_t(gk) * g.sAk] : zero;
     }
     for (int i = tid; i < GBN * GBK; i += GTHREADS) {
       int nn, kk;
       if (g.sBk == 1) { nn = i / GBK; kk = i % GBK; } else { nn = i % GBN; kk = i / GBN; }
       const int gn = n0 + nn, gk = k0 + kk;
-      Bs[nn][kk] = (gn < g.N && gk < g.K) ? g.B[int64_t(gn) * g.sBn + int64_t(gk) * g.sBk] : zero;
+      Bs[nn][kk] = (gn < g.N && gk < kend) ? g.B[int64_t(gn) * g.sBn + int64_t(gk) * g.sBk] : zero;
     }
     __syncthreads();
 #pragma unroll
@@ -170,7 +173,9 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_async_kernel(const GemmArg
   const int group = lane >> 2, tig = lane & 3;
   const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
   const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
-  const int ktiles = (g.K + GBK - 1) / GBK;
+  const int kbeg = g.kc ? int(blockIdx.z) * g.kc : 0;
+  const int kend = g.kc ? min(g.K, kbeg + g.kc) : g.K;
+  const int ktiles = (kend - kbeg + GBK - 1) / GBK;
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -181,8 +186,8 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_async_kernel(const GemmArg
   auto issue = [&](int kt) {
     if (kt < ktiles) {
       const int s = kt % GSTAGES;
-      load_tile<AK>(As[s], g.A, g.sAm, g.sAk, g.M, g.K, m0, kt * GBK, tid);
-      load_tile<BK>(Bs[s], g.B, g.sBn, g.sBk, g.N, g.K, n0, kt * GBK, tid);
+      load_tile<AK>(As[s], g.A, g.sAm, g.sAk, g.M, kend, m0, kbeg + kt * GBK, tid);
+      load_tile<BK>(Bs[s], g.B, g.sBn, g.sBk, g.N, kend, n0, kbeg + kt * GBK, tid);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -273,17 +278,20 @@ struct EpiMaskBf16 {  // C = bf16(acc) where H > 0, else 0 (ReLU derivative, rel
     C[i] = __bfloat162float(H[i]) > 0.f ? __float2bfloat16_rn(v) : __float2bfloat16_rn(0.f);
   }
 };
-struct EpiF32 {  // C = acc
+struct EpiF32 {  // C = acc (slice z of a split product into plane z)
   float* C;
-  int64_t ldc;
-  __device__ void operator()(int r, int c, float v) const { C[int64_t(r) * ldc + c] = v; }
+  int64_t ldc, plane;
+  __device__ void operator()(int r, int c, float v) const {
+    C[int64_t(blockIdx.z) * plane + int64_t(r) * ldc + c] = v;
+  }
 };
 
 // Operands whose rows along the contiguous dimension start on 16-byte
 // boundaries take the cp.async kernel; any other layout the element-wise one.
 template <class Epi>
 int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
-  const dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM));
+  const unsigned slices = g.kc ? unsigned((g.K + g.kc - 1) / g.kc) : 1u;
+  const dim3 grid(unsigned((g.N + GBN - 1) / GBN), unsigned((g.M + GBM - 1) / GBM), slices);
   auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const bool ak = g.sAk == 1 && g.sAm % 8 == 0, am = g.sAm == 1 && g.sAk % 8 == 0;
   const bool bk = g.sBk == 1 && g.sBn % 8 == 0, bn = g.sBn == 1 && g.sBk % 8 == 0;
@@ -401,7 +409,28 @@ unsigned grid_for(int64_t count, int threads) {
 
 int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream) {
   if (g.M < 1 || g.N < 1 || g.K < 1) return KERDOCK_OK;
-  return gemm(g, EpiF32{C, ldc}, stream);
+  GemmArgs whole = g;
+  whole.kc = 0;
+  return gemm(whole, EpiF32{C, ldc, 0}, stream);
+}
+
+GemmSplit gemm_split(int64_t M, int64_t N, int64_t K, int num_sms) {
+  const int64_t tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  const int64_t ktiles = (K + GBK - 1) / GBK;
+  int64_t s = (4 * int64_t(num_sms) + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, std::max<int64_t>(1, ktiles / 4));  // >= 4 k-tiles per slice
+  s = std::max<int64_t>(1, std::min<int64_t>(s, 8));
+  GemmSplit sp;
+  sp.kc = int((ktiles + s - 1) / s) * GBK;
+  sp.slices = int((K + sp.kc - 1) / sp.kc);
+  return sp;
+}
+
+int gemm_bf16_f32_split(GemmArgs g, const GemmSplit& sp, float* C, int64_t ldc, int64_t plane,
+                        cudaStream_t stream) {
+  if (g.M < 1 || g.N < 1 || g.K < 1) return KERDOCK_OK;
+  g.kc = sp.slices > 1 ? sp.kc : 0;
+  return gemm(g, EpiF32{C, ldc, plane}, stream);
 }
 
 }  // namespace kd

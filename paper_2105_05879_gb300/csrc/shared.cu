@@ -99,14 +99,18 @@ __global__ void gather_rows_kernel(const RT* __restrict__ R, int64_t ldr, const 
 
 // A3[k][r] = P pieces of C[r][batch k] / J: float32 [c_hi | c_lo | c_hi],
 // bfloat16 [c_hi | c_lo].
-__global__ void split_coef_kernel(const float* __restrict__ C, int64_t q, int64_t N, int64_t J,
-                                  int64_t K, int P, int64_t lda3, float inv_J,
+// C arrives as `slices` partial planes of q x N (a split product), summed here
+// in plane order.
+__global__ void split_coef_kernel(const float* __restrict__ C, int slices, int64_t q, int64_t N,
+                                  int64_t J, int64_t K, int P, int64_t lda3, float inv_J,
                                   __nv_bfloat16* A3) {
   for (int64_t r = blockIdx.x; r < q; r += gridDim.x)
     for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
       const int64_t k = j / J, jj = j - k * J;
+      float c = 0.f;
+      for (int z = 0; z < slices; ++z) c += C[(z * q + r) * N + j];
       __nv_bfloat16 hi, lo;
-      split_bf16(C[r * N + j] * inv_J, hi, lo);
+      split_bf16(c * inv_J, hi, lo);
       __nv_bfloat16* a = A3 + (k * q + r) * lda3;
       a[jj] = hi;
       a[J + jj] = lo;
@@ -115,16 +119,22 @@ __global__ void split_coef_kernel(const float* __restrict__ C, int64_t q, int64_
 }
 
 // scores = |median over the K batch means| (mean of the two middle values for
-// even K), q x m.
-__global__ void median_abs_kernel(const float* __restrict__ Y, int64_t q, int64_t m, int64_t ldr,
-                                  int K, float* scores) {
+// even K), q x m.  Batch k's mean arrives as `slices` partial planes
+// Y[k * slices + z] of q x ldr, summed in plane order.
+__global__ void median_abs_kernel(const float* __restrict__ Y, int slices, int64_t q, int64_t m,
+                                  int64_t ldr, int K, float* scores) {
   const int64_t total = q * m;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = t / m, i = t - r * m;
     float v[kMaxK];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) v[k] = k < K ? Y[(int64_t(k) * q + r) * ldr + i] : 0.f;
+    for (int k = 0; k < kMaxK; ++k) {
+      float y = 0.f;
+      if (k < K)
+        for (int z = 0; z < slices; ++z) y += Y[((int64_t(k) * slices + z) * q + r) * ldr + i];
+      v[k] = y;
+    }
     float med;
     if (K == 1) {
       med = v[0];
@@ -155,12 +165,18 @@ int64_t a3_stride(int64_t P, int64_t J) { return (P * J + 7) / 8 * 8; }
 
 struct SharedLayout {
   size_t ells, S2, X2, C, A3, G3, Y, scores, total;
+  GemmSplit split_c, split_y;  // K splits of C = X S^T and of each Y_k = C_k R_k / J
 };
 
 SharedLayout shared_layout(const Plan& p, int64_t q) {
   const int64_t N = p.N, J = p.J, K = p.K, n = p.n, m = p.m, ldr = p.ldr;
   const int64_t P = p.dtype == KERDOCK_BF16 ? 2 : 3;
   SharedLayout s{};
+  s.split_c = gemm_split(q, N, 2 * n, p.num_sms);
+  // The batch-mean products stay whole: split three ways at q = 1000,
+  // m = 1024 they ran no faster (17.2 vs 18.0 us) and their partial planes
+  // tripled what the median reads.
+  s.split_y = GemmSplit{1, 0};
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -170,10 +186,10 @@ SharedLayout shared_layout(const Plan& p, int64_t q) {
   s.ells = take(size_t(N) * 8);
   s.S2 = take(size_t(N) * 2 * n * 2);
   s.X2 = take(size_t(q) * 2 * n * 2);
-  s.C = take(size_t(q) * N * 4);
+  s.C = take(size_t(s.split_c.slices) * q * N * 4);
   s.A3 = take(size_t(K) * q * a3_stride(P, J) * 2);
   s.G3 = take(size_t(K) * P * J * ldr * 2);
-  s.Y = take(size_t(K) * q * ldr * 4);
+  s.Y = take(size_t(K) * s.split_y.slices * q * ldr * 4);
   s.scores = take(size_t(q) * m * 4);
   s.total = off;
   return s;
@@ -235,20 +251,21 @@ extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int
   KD_CUDA_TRY(cudaGetLastError());
   // C = X S^T over [x_hi | x_lo] and [s | s]
   kd::GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
-  int rc = kd::gemm_bf16_f32(g1, C, N, st);
+  int rc = kd::gemm_bf16_f32_split(g1, lay.split_c, C, N, q * N, st);
   if (rc != KERDOCK_OK) return rc;
   const int64_t lda3 = kd::a3_stride(P, J);
-  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(C, q, N, J, K, P, lda3,
-                                                                  1.0f / float(J), A3);
+  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(
+      C, lay.split_c.slices, q, N, J, K, P, lda3, 1.0f / float(J), A3);
   KD_CUDA_TRY(cudaGetLastError());
   for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
     kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * lda3, lda3, 1,
                     G3 + k * P * J * ldr, 1, ldr};
-    rc = kd::gemm_bf16_f32(g2, Y + k * q * ldr, ldr, st);
+    rc = kd::gemm_bf16_f32_split(g2, lay.split_y, Y + k * lay.split_y.slices * q * ldr, ldr,
+                                 q * ldr, st);
     if (rc != KERDOCK_OK) return rc;
   }
   kd::median_abs_kernel<<<kd::grid_for((q * m + kd::kThreads - 1) / kd::kThreads), kd::kThreads,
-                          0, st>>>(Y, q, m, ldr, int(K), scores);
+                          0, st>>>(Y, lay.split_y.slices, q, m, ldr, int(K), scores);
   KD_CUDA_TRY(cudaGetLastError());
   return kerdock_refine_scores(plan, X_dev, q, ldx, scores, p.S, eps, flags, out_idx, out_val,
                                out_count);
