@@ -129,12 +129,11 @@ __global__ void median_abs_kernel(const float* __restrict__ Y, int slices, int64
     const int64_t r = t / m, i = t - r * m;
     float v[kMaxK];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-      float y = 0.f;
-      if (k < K)
-        for (int z = 0; z < slices; ++z) y += Y[((int64_t(k) * slices + z) * q + r) * ldr + i];
-      v[k] = y;
-    }
+    for (int k = 0; k < kMaxK; ++k) v[k] = k < K ? Y[(int64_t(k) * slices * q + r) * ldr + i] : 0.f;
+    for (int z = 1; z < slices; ++z)  // the other planes, added in plane order
+#pragma unroll
+      for (int k = 0; k < kMaxK; ++k)
+        if (k < K) v[k] += Y[((int64_t(k) * slices + z) * q + r) * ldr + i];
     float med;
     if (K == 1) {
       med = v[0];
