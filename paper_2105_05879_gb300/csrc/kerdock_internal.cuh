@@ -118,7 +118,8 @@ struct GemmArgs {
   int64_t sAm, sAk;
   const __nv_bfloat16* B;  // element (n, k) at B[n * sBn + k * sBk]
   int64_t sBn, sBk;
-  int kc;  // k range of one slice when K is split (a multiple of 32), 0: no split
+  int kc;  // k range of one slice when K is split (a multiple of 64), 0: no split
+  uint32_t* status = nullptr;  // device status word for a bounded wait that ran out
 };
 int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream);
 

@@ -9,6 +9,8 @@
 //   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3.
 // Every product of the forward and backward passes is one strided GEMM kernel
 // C = op(A) op(B)^T with a fused epilogue (bias, ReLU, ReLU mask, FP32/BF16).
+#include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
+
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -249,6 +251,189 @@ __global__ void __launch_bounds__(GTHREADS) gemm_bf16_async_kernel(const GemmArg
       }
 }
 
+// ---------------------------------------------------------------------------
+// The same product on the fifth-generation tensor cores for two k-major
+// operands (both 16-byte aligned with 16-byte row pitches): a 128 x 64 output
+// tile per CTA, accumulated in 64 columns of tensor memory by tcgen05.mma
+// (kind::f16, bfloat16 in, float32 out).  One thread streams 128 x 64 and
+// 64 x 64 operand blocks into a TC_STAGES-deep shared-memory ring with TMA
+// (128-byte swizzle, zero fill past the matrix edges), one thread issues the
+// MMAs (four K = 16 steps per block) and returns each slot with
+// tcgen05.commit, and the four warps read the accumulator back (warp w owns
+// tensor-memory lanes 32w .. 32w + 31 = tile rows) for the epilogue.  Every
+// wait is bounded; a wait that runs out records a timeout in the status word
+// (when the caller gives one) and the CTA drains its issued work before it
+// frees the tensor memory.
+constexpr int TC_M = 128, TC_N = 64, TC_K = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr uint32_t TC_A_BYTES = TC_M * TC_K * 2, TC_B_BYTES = TC_N * TC_K * 2;
+constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr uint32_t TC_SMEM = 1024 + TC_STAGES * TC_STAGE_BYTES + 256;
+constexpr uint32_t TC_TMEM_COLS = 64;
+// instruction descriptor (kind::f16): D float32, A and B bfloat16, both
+// k-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                              (uint32_t(TC_M >> 4) << 24);
+
+// Shared-memory matrix descriptor of a k-major operand block in the 128-byte
+// swizzled layout that TMA writes: rows of 128 bytes, 8-row groups 1024 bytes
+// apart (stride byte offset), block base 1024-byte aligned.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+__device__ __forceinline__ void tc_tma_load(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(TC_THREADS)
+    gemm_tc_kernel(const GemmArgs g, const Epi epi, const __grid_constant__ CUtensorMap tmA,
+                   const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const int kbeg = g.kc ? int(blockIdx.z) * g.kc : 0;
+  const int kend = g.kc ? min(g.K, kbeg + g.kc) : g.K;
+  const int ktiles = (kend - kbeg + TC_K - 1) / TC_K;
+  const uint32_t sbase = smem_addr(sm);
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+
+  bool ok = true;
+  if (tid == 0) {  // TMA producer
+    int issued = 0;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % TC_STAGES;
+      if (kt >= TC_STAGES && !mbar_wait_bounded(&empty[s], uint32_t((kt / TC_STAGES) - 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      mbar_arrive_expect_tx(&full[s], TC_STAGE_BYTES);
+      const uint32_t a_s = sbase + s * TC_STAGE_BYTES;
+      tc_tma_load(a_s, &tmA, kbeg + kt * TC_K, m0, &full[s]);
+      tc_tma_load(a_s + TC_A_BYTES, &tmB, kbeg + kt * TC_K, n0, &full[s]);
+      issued = kt + 1;
+    }
+    // the copies still in flight land before the CTA can leave
+    for (int kt = issued - TC_STAGES > 0 ? issued - TC_STAGES : 0; kt < issued; ++kt)
+      if (!mbar_wait_bounded(&full[kt % TC_STAGES], uint32_t(kt / TC_STAGES) & 1u)) ok = false;
+  } else if (tid == 32) {  // MMA issuer
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % TC_STAGES;
+      if (!mbar_wait_bounded(&full[s], uint32_t(kt / TC_STAGES) & 1u)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_s = sbase + s * TC_STAGE_BYTES;
+      const uint64_t ad = tc_desc(a_s), bd = tc_desc(a_s + TC_A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_K / 16; ++kk)  // +32 bytes per K = 16 step inside the swizzle row
+        tc_mma(tmem, ad + uint64_t(kk * 2), bd + uint64_t(kk * 2), (kt | kk) != 0 ? 1u : 0u);
+      tc_commit(&empty[s]);
+    }
+    tc_commit(done);  // fires when every MMA issued above has completed
+  }
+  __syncwarp();
+  const bool have = mbar_wait_bounded(done, 0);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have) {
+    // the ring is idle once every MMA has completed: each warp parks its 32
+    // accumulator rows there (row pitch 65 words, no bank conflicts) and
+    // writes them back row by row, 32 consecutive columns per instruction
+    float* park = reinterpret_cast<float*>(sm) + warp * 32 * (TC_N + 1);
+    const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
+#pragma unroll
+    for (int c0 = 0; c0 < TC_N; c0 += 16) {
+      uint32_t v[16];
+      tc_ld16(trow + uint32_t(c0), v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        park[lane * (TC_N + 1) + c0 + j] = ktiles > 0 ? __uint_as_float(v[j]) : 0.f;
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32; ++rr) {
+      const int r = m0 + warp * 32 + rr;
+      if (r >= g.M) break;
+#pragma unroll
+      for (int c = lane; c < TC_N; c += 32)
+        if (n0 + c < g.N) epi(r, n0 + c, park[rr * (TC_N + 1) + c]);
+    }
+  }
+  if ((!ok || !have) && g.status != nullptr) set_status(g.status, kStatusTimeout);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+}
+
 struct EpiBiasReluBf16 {  // C = bf16(relu(acc + bias[c]))
   const float* bias;
   __nv_bfloat16* C;
@@ -286,8 +471,66 @@ struct EpiF32 {  // C = acc (slice z of a split product into plane z)
   }
 };
 
-// Operands whose rows along the contiguous dimension start on 16-byte
-// boundaries take the cp.async kernel; any other layout the element-wise one.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// rows x K bfloat16 k-major operand (row pitch `pitch` elements) as a 2-D
+// tensor map with a K_block x rows_block box in the 128-byte swizzle
+bool encode_kmajor(CUtensorMap* map, const __nv_bfloat16* base, int rows, int K, int64_t pitch,
+                   uint32_t box_rows) {
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (enc == nullptr) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(pitch) * 2};
+  const cuuint32_t box[2] = {uint32_t(TC_K), box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tcgen05 kernel when both operands are k-major with 16-byte rows;
+// `used` is false when the tensor maps cannot be made (the caller falls back).
+template <class Epi>
+int gemm_tc(const GemmArgs& g, const Epi& epi, cudaStream_t stream, bool& used) {
+  used = false;
+  CUtensorMap ma, mb;
+  if (!encode_kmajor(&ma, g.A, g.M, g.K, g.sAm, TC_M) ||
+      !encode_kmajor(&mb, g.B, g.N, g.K, g.sBn, TC_N))
+    return KERDOCK_OK;
+  static bool attr_set = false;  // one per epilogue type
+  if (!attr_set) {
+    KD_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<Epi>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SMEM)));
+    attr_set = true;
+  }
+  const unsigned slices = g.kc ? unsigned((g.K + g.kc - 1) / g.kc) : 1u;
+  const dim3 grid(unsigned((g.N + TC_N - 1) / TC_N), unsigned((g.M + TC_M - 1) / TC_M), slices);
+  gemm_tc_kernel<Epi><<<grid, TC_THREADS, TC_SMEM, stream>>>(g, epi, ma, mb);
+  KD_CUDA_TRY(cudaGetLastError());
+  used = true;
+  return KERDOCK_OK;
+}
+
+// Two k-major operands with 16-byte rows take the tcgen05 kernel; other
+// operands whose rows along the contiguous dimension start on 16-byte
+// boundaries the cp.async kernel; any other layout the element-wise one.
 template <class Epi>
 int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
   const unsigned slices = g.kc ? unsigned((g.K + g.kc - 1) / g.kc) : 1u;
@@ -295,6 +538,11 @@ int gemm(const GemmArgs& g, const Epi& epi, cudaStream_t stream) {
   auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const bool ak = g.sAk == 1 && g.sAm % 8 == 0, am = g.sAm == 1 && g.sAk % 8 == 0;
   const bool bk = g.sBk == 1 && g.sBn % 8 == 0, bn = g.sBn == 1 && g.sBk % 8 == 0;
+  if (ak && bk && aligned16(g.A) && aligned16(g.B)) {
+    bool used = false;
+    const int rc = gemm_tc(g, epi, stream, used);
+    if (rc != KERDOCK_OK || used) return rc;
+  }
   if ((ak || am) && (bk || bn) && aligned16(g.A) && aligned16(g.B)) {
     if (ak && bk)
       gemm_bf16_async_kernel<true, true, Epi><<<grid, GTHREADS, 0, stream>>>(g, epi);
@@ -415,13 +663,14 @@ int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream)
 }
 
 GemmSplit gemm_split(int64_t M, int64_t N, int64_t K, int num_sms) {
-  const int64_t tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
-  const int64_t ktiles = (K + GBK - 1) / GBK;
-  int64_t s = (4 * int64_t(num_sms) + tiles - 1) / tiles;
-  s = std::min<int64_t>(s, std::max<int64_t>(1, ktiles / 4));  // >= 4 k-tiles per slice
+  // sized for the tcgen05 tiles (128 x 64, k blocks of 64; two CTAs per SM)
+  const int64_t tiles = ((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
+  const int64_t kblocks = (K + TC_K - 1) / TC_K;
+  int64_t s = (2 * int64_t(num_sms) + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, std::max<int64_t>(1, kblocks / 4));  // >= 4 k blocks per slice
   s = std::max<int64_t>(1, std::min<int64_t>(s, 8));
   GemmSplit sp;
-  sp.kc = int((ktiles + s - 1) / s) * GBK;
+  sp.kc = int((kblocks + s - 1) / s) * TC_K;
   sp.slices = int((K + sp.kc - 1) / sp.kc);
   return sp;
 }

@@ -72,27 +72,45 @@ __global__ void split_queries_kernel(const float* __restrict__ X, int64_t q, int
 }
 
 // Per batch k the P copies of its J gathered rows stacked along the
-// contraction index: float32 [R_hi; R_hi; R_lo], bfloat16 [R; R].
+// contraction index, stored k-major for the product (G3[k][i][t], t the
+// contraction index, row pitch lda3): float32 rows as [R_hi | R_hi | R_lo],
+// bfloat16 rows as [R | R].  A CTA moves 32 samples x 64 entries through
+// shared memory, reading each row run and writing each t run contiguously.
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 template <typename RT>
 __global__ void gather_rows_kernel(const RT* __restrict__ R, int64_t ldr, const int64_t* ells,
-                                   int64_t J, int64_t N, __nv_bfloat16* G3) {
+                                   int64_t J, int64_t m, int64_t lda3, __nv_bfloat16* G3) {
   constexpr int P = sizeof(RT) == 4 ? 3 : 2;
-  for (int64_t j = blockIdx.x; j < N; j += gridDim.x) {
-    const int64_t k = j / J, jj = j - k * J;
-    const RT* src = R + ells[j] * ldr;
-    __nv_bfloat16* dst = G3 + (k * P * J + jj) * ldr;
-    for (int64_t i = threadIdx.x; i < ldr; i += blockDim.x) {
-      if (P == 3) {
-        __nv_bfloat16 hi, lo;
-        split_bf16(float(src[i]), hi, lo);
-        dst[i] = hi;
-        dst[J * ldr + i] = hi;
-        dst[2 * J * ldr + i] = lo;
-      } else {
-        const __nv_bfloat16 v = *reinterpret_cast<const __nv_bfloat16*>(&src[i]);
-        dst[i] = v;
-        dst[J * ldr + i] = v;
-      }
+  __shared__ float tile[32][65];
+  __shared__ int64_t row_off[32];
+  const int64_t k = blockIdx.z, j0 = int64_t(blockIdx.y) * 32, i0 = int64_t(blockIdx.x) * 64;
+  if (threadIdx.x < 32)
+    row_off[threadIdx.x] = j0 + threadIdx.x < J ? ells[k * J + j0 + threadIdx.x] * ldr : -1;
+  __syncthreads();
+#pragma unroll 4
+  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+    const int jj = e >> 6, ii = e & 63;
+    const int64_t i = i0 + ii;
+    tile[jj][ii] = (row_off[jj] >= 0 && i < m) ? to_f32(R[row_off[jj] + i]) : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+    const int jj = e & 31, ii = e >> 5;
+    const int64_t j = j0 + jj, i = i0 + ii;
+    if (j >= J || i >= m) continue;
+    __nv_bfloat16* dst = G3 + (k * ldr + i) * lda3;
+    if (P == 3) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(tile[jj][ii], hi, lo);
+      dst[j] = hi;
+      dst[J + j] = hi;
+      dst[2 * J + j] = lo;
+    } else {
+      const __nv_bfloat16 v = __float2bfloat16_rn(tile[jj][ii]);  // exact: R is bfloat16
+      dst[j] = v;
+      dst[J + j] = v;
     }
   }
 }
@@ -173,7 +191,7 @@ SharedLayout shared_layout(const Plan& p, int64_t q) {
   SharedLayout s{};
   s.split_c = gemm_split(q, N, 2 * n, p.num_sms);
   // The batch-mean products stay whole: split three ways at q = 1000,
-  // m = 1024 they ran no faster (17.2 vs 18.0 us) and their partial planes
+  // m = 1024 they ran no faster (14.3 vs 14.0 us) and their partial planes
   // tripled what the median reads.
   s.split_y = GemmSplit{1, 0};
   size_t off = 0;
@@ -187,7 +205,7 @@ SharedLayout shared_layout(const Plan& p, int64_t q) {
   s.X2 = take(size_t(q) * 2 * n * 2);
   s.C = take(size_t(s.split_c.slices) * q * N * 4);
   s.A3 = take(size_t(K) * q * a3_stride(P, J) * 2);
-  s.G3 = take(size_t(K) * P * J * ldr * 2);
+  s.G3 = take(size_t(K) * ldr * a3_stride(P, J) * 2);
   s.Y = take(size_t(K) * s.split_y.slices * q * ldr * 4);
   s.scores = take(size_t(q) * m * 4);
   s.total = off;
@@ -241,24 +259,27 @@ extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int
   KD_CUDA_TRY(cudaGetLastError());
   kd::split_queries_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(X_dev, q, ldx, n, X2);
   KD_CUDA_TRY(cudaGetLastError());
+  const int64_t lda3 = kd::a3_stride(P, J);
+  const dim3 ggrid(unsigned((m + 63) / 64), unsigned((J + 31) / 32), unsigned(K));
   if (P == 3)
-    kd::gather_rows_kernel<float><<<kd::grid_for(N), kd::kThreads, 0, st>>>(
-        static_cast<const float*>(p.repr), ldr, ells, J, N, G3);
+    kd::gather_rows_kernel<float><<<ggrid, kd::kThreads, 0, st>>>(
+        static_cast<const float*>(p.repr), ldr, ells, J, m, lda3, G3);
   else
-    kd::gather_rows_kernel<__nv_bfloat16><<<kd::grid_for(N), kd::kThreads, 0, st>>>(
-        static_cast<const __nv_bfloat16*>(p.repr), ldr, ells, J, N, G3);
+    kd::gather_rows_kernel<__nv_bfloat16><<<ggrid, kd::kThreads, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(p.repr), ldr, ells, J, m, lda3, G3);
   KD_CUDA_TRY(cudaGetLastError());
   // C = X S^T over [x_hi | x_lo] and [s | s]
   kd::GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
+  g1.status = p.status();
   int rc = kd::gemm_bf16_f32_split(g1, lay.split_c, C, N, q * N, st);
   if (rc != KERDOCK_OK) return rc;
-  const int64_t lda3 = kd::a3_stride(P, J);
   kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(
       C, lay.split_c.slices, q, N, J, K, P, lda3, 1.0f / float(J), A3);
   KD_CUDA_TRY(cudaGetLastError());
   for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
     kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * lda3, lda3, 1,
-                    G3 + k * P * J * ldr, 1, ldr};
+                    G3 + k * ldr * lda3, lda3, 1};
+    g2.status = p.status();
     rc = kd::gemm_bf16_f32_split(g2, lay.split_y, Y + k * lay.split_y.slices * q * ldr, ldr,
                                  q * ldr, st);
     if (rc != KERDOCK_OK) return rc;
