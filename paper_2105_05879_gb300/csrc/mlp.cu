@@ -1,14 +1,18 @@
-// mlp.cu -- the learned-proposal network and the score-ranked refinement.
+// mlp.cu -- the learned-proposal network and the bfloat16 tensor-core GEMMs.
 //
 // Not in the paper: a project form that replaces the |mu| ranking of
 // Algorithm 1's top-S step by the scores of a small network fed with a cheap
 // sketch mu (reduced N), so that fewer samples and fewer refined rows reach the
 // same support.  The network is a three-layer perceptron in bfloat16 with FP32
-// accumulation on tensor cores (mma.sync m16n8k16), trained on the GPU with
+// accumulation on the tensor cores, trained on the GPU with
 // binary cross-entropy on logits and AdamW:
 //   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Z = H2 W3^T + b3.
-// Every product of the forward and backward passes is one strided GEMM kernel
+// Every product of the forward and backward passes is one strided GEMM
 // C = op(A) op(B)^T with a fused epilogue (bias, ReLU, ReLU mask, FP32/BF16).
+// Products of two k-major operands (the forward layers, the shared-sample
+// query's products) run on tcgen05 with TMA-fed operands and a tensor-memory
+// accumulator; the transposed operands of the backward pass take a cp.async +
+// ldmatrix + mma.sync kernel.
 #include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
 
 #include <algorithm>

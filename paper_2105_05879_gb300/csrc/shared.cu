@@ -136,43 +136,74 @@ __global__ void split_coef_kernel(const float* __restrict__ C, int slices, int64
     }
 }
 
+// Median of v[0 .. K) (mean of the two middle values for even K).
+template <int KM>
+__device__ __forceinline__ float median_of(const float (&v)[KM], int K) {
+  if (K == 1) return v[0];
+  if (K == 2) return 0.5f * (v[0] + v[1]);
+  const int r_lo = (K - 1) / 2, r_hi = K / 2;
+  float lo = 0.f, hi = 0.f;
+#pragma unroll
+  for (int a = 0; a < KM; ++a) {
+    if (a >= K) break;
+    int rank = 0;
+#pragma unroll
+    for (int c = 0; c < KM; ++c)
+      if (c < K && (v[c] < v[a] || (v[c] == v[a] && c < a))) ++rank;
+    if (rank == r_lo) lo = v[a];
+    if (rank == r_hi) hi = v[a];
+  }
+  return (K & 1) ? lo : 0.5f * (lo + hi);
+}
+
 // scores = |median over the K batch means| (mean of the two middle values for
-// even K), q x m.  Batch k's mean arrives as `slices` partial planes
-// Y[k * slices + z] of q x ldr, summed in plane order.
+// even K), q x m, four consecutive entries per thread (16-byte loads: the row
+// pitch ldr is a multiple of 8).  Batch k's mean arrives as `slices` partial
+// planes Y[k * slices + z] of q x ldr, summed in plane order.  KM >= K sizes
+// the per-thread arrays.
+template <int KM>
 __global__ void median_abs_kernel(const float* __restrict__ Y, int slices, int64_t q, int64_t m,
                                   int64_t ldr, int K, float* scores) {
-  const int64_t total = q * m;
+  const int64_t m4 = (m + 3) / 4, total = q * m4;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = t / m, i = t - r * m;
-    float v[kMaxK];
+    const int64_t r = t / m4, i = (t - r * m4) * 4;
+    float4 y[KM];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) v[k] = k < K ? Y[(int64_t(k) * slices * q + r) * ldr + i] : 0.f;
+    for (int k = 0; k < KM; ++k)
+      y[k] = k < K ? *reinterpret_cast<const float4*>(Y + (int64_t(k) * slices * q + r) * ldr + i)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int z = 1; z < slices; ++z)  // the other planes, added in plane order
 #pragma unroll
-      for (int k = 0; k < kMaxK; ++k)
-        if (k < K) v[k] += Y[((int64_t(k) * slices + z) * q + r) * ldr + i];
-    float med;
-    if (K == 1) {
-      med = v[0];
-    } else if (K == 2) {
-      med = 0.5f * (v[0] + v[1]);
+      for (int k = 0; k < KM; ++k)
+        if (k < K) {
+          const float4 w =
+              *reinterpret_cast<const float4*>(Y + ((int64_t(k) * slices + z) * q + r) * ldr + i);
+          y[k].x += w.x;
+          y[k].y += w.y;
+          y[k].z += w.z;
+          y[k].w += w.w;
+        }
+    float v[KM];
+    float4 out;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) v[k] = y[k].x;
+    out.x = fabsf(median_of(v, K));
+#pragma unroll
+    for (int k = 0; k < KM; ++k) v[k] = y[k].y;
+    out.y = fabsf(median_of(v, K));
+#pragma unroll
+    for (int k = 0; k < KM; ++k) v[k] = y[k].z;
+    out.z = fabsf(median_of(v, K));
+#pragma unroll
+    for (int k = 0; k < KM; ++k) v[k] = y[k].w;
+    out.w = fabsf(median_of(v, K));
+    if ((m & 3) == 0) {
+      *reinterpret_cast<float4*>(scores + r * m + i) = out;
     } else {
-      const int r_lo = (K - 1) / 2, r_hi = K / 2;
-      float lo = 0.f, hi = 0.f;
-#pragma unroll
-      for (int a = 0; a < kMaxK; ++a) {
-        if (a >= K) break;
-        int rank = 0;
-#pragma unroll
-        for (int c = 0; c < kMaxK; ++c)
-          if (c < K && (v[c] < v[a] || (v[c] == v[a] && c < a))) ++rank;
-        if (rank == r_lo) lo = v[a];
-        if (rank == r_hi) hi = v[a];
-      }
-      med = (K & 1) ? lo : 0.5f * (lo + hi);
+      const float o[4] = {out.x, out.y, out.z, out.w};
+      for (int c = 0; c < 4 && i + c < m; ++c) scores[r * m + i + c] = o[c];
     }
-    scores[t] = fabsf(med);
   }
 }
 
@@ -284,8 +315,19 @@ extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int
                                  q * ldr, st);
     if (rc != KERDOCK_OK) return rc;
   }
-  kd::median_abs_kernel<<<kd::grid_for((q * m + kd::kThreads - 1) / kd::kThreads), kd::kThreads,
-                          0, st>>>(Y, lay.split_y.slices, q, m, ldr, int(K), scores);
+  {
+    const unsigned mgrid = kd::grid_for((q * ((m + 3) / 4) + kd::kThreads - 1) / kd::kThreads);
+    const int sl = lay.split_y.slices;
+    if (K <= 2)
+      kd::median_abs_kernel<2><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+    else if (K <= 4)
+      kd::median_abs_kernel<4><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+    else if (K <= 8)
+      kd::median_abs_kernel<8><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+    else
+      kd::median_abs_kernel<kd::kMaxK>
+          <<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+  }
   KD_CUDA_TRY(cudaGetLastError());
   return kerdock_refine_scores(plan, X_dev, q, ldx, scores, p.S, eps, flags, out_idx, out_val,
                                out_count);
