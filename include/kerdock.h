@@ -347,6 +347,22 @@ int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_wor
  * no hang).  The next kerdock_sync reports it and clears it. */
 int kerdock_debug_wait_timeout(kerdock_plan_t plan, int32_t max_polls);
 
+/* Test entry for the library's bfloat16 tensor-core product (the products of
+ * the learned network and of kerdock_apply_shared).  Plane z of C (float32,
+ * device, row pitch ldc >= N, plane z at C + z * M * ldc) receives
+ *   C_z[m][n] = sum over k in slice z of A(m, k) B(n, k),
+ * with A(m, k) at A[m * sAm + k * sAk] and B(n, k) at B[n * sBn + k * sBk]
+ * (bfloat16, device).  kc = 0 sums the whole K into plane 0; kc > 0 (a
+ * multiple of 64) cuts K into ceil(K / kc) slices of kc.  Two k-major operands
+ * (unit k stride, row pitch a multiple of 8 elements, 16-byte aligned base)
+ * run on tcgen05, other layouts with 16-byte rows on the cp.async kernel, the
+ * rest on the element-wise kernel.  Enqueued on `stream` (NULL: the default
+ * stream); KERDOCK_ERR_INVALID_ARG for M, N or K < 1, ldc < N, kc < 0 or not a
+ * multiple of 64, or a NULL pointer. */
+int kerdock_debug_gemm(const void* A, int64_t sAm, int64_t sAk, const void* B, int64_t sBn,
+                            int64_t sBk, int32_t M, int32_t N, int32_t K, int32_t kc, float* C,
+                            int64_t ldc, void* stream);
+
 /* Destroy a plan (host metadata only; NULL is accepted). */
 int kerdock_plan_destroy(kerdock_plan_t plan);
 

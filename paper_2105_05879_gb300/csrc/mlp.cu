@@ -985,3 +985,15 @@ int kerdock_mlp_destroy(kerdock_mlp_t mlp) {
 }
 
 }  // extern "C"
+
+extern "C" int kerdock_debug_gemm(const void* A, int64_t sAm, int64_t sAk, const void* B,
+                                       int64_t sBn, int64_t sBk, int32_t M, int32_t N, int32_t K,
+                                       int32_t kc, float* C, int64_t ldc, void* stream) {
+  if (A == nullptr || B == nullptr || C == nullptr || M < 1 || N < 1 || K < 1 || ldc < N ||
+      kc < 0 || kc % 64 != 0)
+    return KERDOCK_ERR_INVALID_ARG;
+  kd::GemmArgs g{M, N, K, static_cast<const __nv_bfloat16*>(A), sAm, sAk,
+                 static_cast<const __nv_bfloat16*>(B), sBn, sBk};
+  g.kc = kc >= K ? 0 : kc;
+  return kd::gemm(g, kd::EpiF32{C, ldc, int64_t(M) * ldc}, static_cast<cudaStream_t>(stream));
+}
