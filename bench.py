@@ -44,10 +44,20 @@ def workload_config(wl):
     }
 
 
-def source_hash():
+# The source files that define each profiled kernel (its .cu and the shared
+# internal header): its committed DRAM counters stay valid while these are
+# unchanged.
+KERNEL_SOURCES = {
+    "query_kernel": ["query.cu", "kerdock_internal.cuh"],
+    "preprocess_small_kernel": ["preprocess.cu", "kerdock_internal.cuh"],
+}
+
+
+def source_hash(files=None):
+    """Hash of the CUDA sources (all of csrc/, or the named files)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2105_05879_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files if files is not None else os.listdir(csrc)):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -72,7 +82,8 @@ def profiled_traffic(kernel, workload):
     with open(path) as fh:
         t = json.load(fh)
     e = t.get(kernel)
-    if not e or e.get("source_hash") != source_hash() or e.get("workload") != workload:
+    if (not e or e.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel))
+            or e.get("workload") != workload):
         return None
     return e.get("dram_bytes_per_launch")
 
