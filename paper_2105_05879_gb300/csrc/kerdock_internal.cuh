@@ -121,10 +121,9 @@ struct GemmArgs {
   int kc;  // k range of one slice when K is split (a multiple of 64), 0: no split
   uint32_t* status = nullptr;  // device status word for a bounded wait that ran out
 };
-int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream);
 
-// Split of K into slices so that a small M x N product still puts about four
-// 64 x 64 tiles on every SM: slice z covers k in [z kc, (z + 1) kc) and writes
+// Split of K into slices so that a small M x N product still puts about two
+// 128 x 64 tiles on every SM: slice z covers k in [z kc, (z + 1) kc) and writes
 // its partial product to its own M x N plane; the reader sums the planes in
 // order z = 0, 1, ... (deterministic).
 struct GemmSplit {

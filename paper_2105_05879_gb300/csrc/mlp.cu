@@ -659,13 +659,6 @@ unsigned grid_for(int64_t count, int threads) {
 
 }  // namespace
 
-int gemm_bf16_f32(const GemmArgs& g, float* C, int64_t ldc, cudaStream_t stream) {
-  if (g.M < 1 || g.N < 1 || g.K < 1) return KERDOCK_OK;
-  GemmArgs whole = g;
-  whole.kc = 0;
-  return gemm(whole, EpiF32{C, ldc, 0}, stream);
-}
-
 GemmSplit gemm_split(int64_t M, int64_t N, int64_t K, int num_sms) {
   // sized for the tcgen05 tiles (128 x 64, k blocks of 64; two CTAs per SM)
   const int64_t tiles = ((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
