@@ -518,11 +518,13 @@ int gemm_tc(const GemmArgs& g, const Epi& epi, cudaStream_t stream, bool& used) 
   if (!encode_kmajor(&ma, g.A, g.M, g.K, g.sAm, TC_M) ||
       !encode_kmajor(&mb, g.B, g.N, g.K, g.sBn, TC_N))
     return KERDOCK_OK;
-  static bool attr_set = false;  // one per epilogue type
-  if (!attr_set) {
+  static int attr_device = -1;  // one per epilogue type, set on the device in use
+  int device = 0;
+  KD_CUDA_TRY(cudaGetDevice(&device));
+  if (attr_device != device) {
     KD_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<Epi>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SMEM)));
-    attr_set = true;
+    attr_device = device;
   }
   const unsigned slices = g.kc ? unsigned((g.K + g.kc - 1) / g.kc) : 1u;
   const dim3 grid(unsigned((g.N + TC_N - 1) / TC_N), unsigned((g.M + TC_M - 1) / TC_M), slices);
