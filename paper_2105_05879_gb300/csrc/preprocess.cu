@@ -7,7 +7,11 @@
 // R[d/2][w][i] = sqrt(d) A[i][w] (zero for w >= n).
 //
 // Kernels:
-//  * d <= 1024 (preprocess_small_kernel): a CTA owns a tile of 16 rows of A,
+//  * d = 1024 (preprocess_d1024_kernel): as below, but the 16-row tile of A
+//    sits in tensor memory (each thread's 64 words in its own lane), a thread
+//    transforms a row pair in phase 1 (one sign bit flips both rows) and one
+//    exchange of 8-byte row pairs replaces two rounds of 4-byte words.
+//  * d <= 256 (preprocess_small_kernel): a CTA owns a tile of 16 rows of A,
 //    kept in shared memory across all the bases it processes, so A is read
 //    from HBM once.  Per basis each thread flips the signs of its p range from
 //    its own sign words (one shift and one XOR per element).  Phase 1: a
@@ -889,6 +893,206 @@ int launch_d4096_tc(const Plan& p) {
   return KERDOCK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// d = 1024, float32 or bfloat16 representation.  Write p = 32 s + k and
+// w = 32 w_hi + w_lo, so W_1024 = W_32 (over s) (x) W_32 (over k).  The CTA's
+// 16-row tile of A lives in tensor memory: thread (row pair rp, source s)
+// keeps rows 2 rp and 2 rp + 1 at p in [32 s, 32 s + 32) as 64 words of its
+// own lane, so shared memory holds only the exchange buffer.  Per basis:
+// phase 1 reads the 64 words back (tcgen05.ld), flips both rows of a p with
+// the same sign bit (step (i) of Lemma 6; the two rows share the sign word)
+// and runs the five stages over k packed across the row pair; one exchange
+// of 8-byte row pairs X[s][w_lo][row] (conflict-free); phase 2, thread
+// (rp, w_lo), runs the five stages over s and stores 16 x 2-row runs as the
+// other kernels do.  Two barriers per basis, and a thread's phase 1 of the
+// next basis overlaps the other warps' phase 2.
+namespace k10 {
+
+constexpr int TI = 16, THREADS = 256, D = 1024, NS = 32;
+constexpr int XST = 32 * TI + 16;  // floats per source: [w_lo][row] + 16 (bank shift)
+constexpr size_t SMEM = size_t(NS) * XST * 4 + 16;
+constexpr uint32_t TMEM_COLS = 128;  // 256 threads x 64 words = 128 lanes x 128 columns
+
+// Asynchronous: the registers are valid after tmem_wait16 has named them.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+// One wait for all loads issued so far; each group of 16 registers is then
+// named so that no read of them moves above the wait.
+__device__ __forceinline__ void tmem_wait64(uint32_t (&v)[64]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; i += 16)
+    asm volatile(""
+                 : "+r"(v[i + 0]), "+r"(v[i + 1]), "+r"(v[i + 2]), "+r"(v[i + 3]), "+r"(v[i + 4]),
+                   "+r"(v[i + 5]), "+r"(v[i + 6]), "+r"(v[i + 7]), "+r"(v[i + 8]), "+r"(v[i + 9]),
+                   "+r"(v[i + 10]), "+r"(v[i + 11]), "+r"(v[i + 12]), "+r"(v[i + 13]),
+                   "+r"(v[i + 14]), "+r"(v[i + 15]));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15])
+      : "memory");
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreArgs a) {
+  constexpr int64_t B = D / 2 + 1;
+  extern __shared__ __align__(16) float smem[];
+  float* X = smem;  // [NS][XST]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + NS * XST);
+  OutT* R = static_cast<OutT*>(a.R);
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int rp = lane & 7;              // rows 2 rp, 2 rp + 1 of the tile (both phases)
+  const int s = (lane >> 3) + 4 * g;    // phase 1: source s; phase 2: w_lo = s
+  const float sqrt_d = 32.f;
+
+  if (g == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  // warp g reaches lanes 32 (g mod 4) ..; warps 4..7 use columns 64 .. 127
+  const uint32_t tme = tmem + (uint32_t((g & 3) * 32) << 16) + uint32_t((g >> 2) * 64);
+
+  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  int64_t cur_tile = -1;
+  for (int64_t item = ir.beg; item < ir.end; ++item) {
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
+    const int64_t i0 = t * TI;
+    const bool ident = b == D / 2;
+    if (t != cur_tile) {  // this thread's 64 words: (row 2 rp, row 2 rp + 1) per p
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        uint32_t w[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int p = 32 * s + 8 * c + e;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int64_t row = i0 + 2 * rp + h;
+            const float v = (row < a.m && p < a.n) ? a.A[row * a.lda + p] : 0.f;
+            w[2 * e + h] = __float_as_uint(v);
+          }
+        }
+        tmem_st16(tme + uint32_t(16 * c), w);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      cur_tile = t;
+    }
+    // Phase 1: k in registers, (row 2 rp, row 2 rp + 1) packed; the four
+    // tensor-memory loads and the sign word are in flight together.
+    uint32_t w[64];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld16(tme + uint32_t(16 * c), w + 16 * c);
+    const uint32_t sw = ident ? 0u : __ldg(a.signs + int64_t(b) * a.sign_words + s);
+    tmem_wait64(w);
+    float2 v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const uint32_t f = (sw << (31 - k)) & 0x80000000u;
+      v[k] = make_float2(__uint_as_float(w[2 * k] ^ f), __uint_as_float(w[2 * k + 1] ^ f));
+    }
+    if (!ident) fwht_across<32>(v);
+    __syncthreads();  // every warp is done reading X for the previous basis
+#pragma unroll
+    for (int k = 0; k < 32; ++k) *reinterpret_cast<float2*>(&X[s * XST + k * TI + 2 * rp]) = v[k];
+    __syncthreads();
+
+    // Phase 2: thread (rp, w_lo = s) combines the 32 sources.
+    float2 y[32];
+#pragma unroll
+    for (int h = 0; h < 32; ++h) y[h] = *reinterpret_cast<const float2*>(&X[h * XST + s * TI + 2 * rp]);
+    if (!ident) {
+      fwht_across<32>(y);
+    } else {
+#pragma unroll
+      for (int h = 0; h < 32; ++h) y[h] = make_float2(y[h].x * sqrt_d, y[h].y * sqrt_d);
+    }
+    const int64_t orow = i0 + 2 * rp;
+    if (orow < a.ldr) {
+      OutT* rb = R + (int64_t(b) * D + s) * a.ldr + orow;  // w = 32 h + s
+#pragma unroll
+      for (int h = 0; h < 32; ++h) store_pair<OutT>(rb + int64_t(h) * 32 * a.ldr, y[h]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (g == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+}  // namespace k10
+
+template <typename OutT>
+int launch_d1024(const Plan& p) {
+  auto kern = k10::preprocess_d1024_kernel<OutT>;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(k10::SMEM)));
+  // the whole unified L1 as shared memory, so that two CTAs fit beside each other
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   int(cudaSharedmemCarveoutMaxShared)));
+  // CTAs per SM from the kernel's registers and shared memory (the runtime's
+  // occupancy query reports one for this kernel, though two fit), at most four
+  // for the 4 x 128 tensor-memory columns of an SM
+  cudaFuncAttributes fa;
+  KD_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0;
+  KD_CUDA_TRY(cudaGetDevice(&dev));
+  KD_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  KD_CUDA_TRY(
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  KD_CUDA_TRY(cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * k10::THREADS;  // 8-register granules
+  int occ = regs_cta > 0 ? regs_sm / regs_cta : 1;
+  const int by_smem = smem_sm / int(k10::SMEM + size_t(fa.sharedSizeBytes) + size_t(smem_rsv));
+  if (by_smem < occ) occ = by_smem;
+  if (occ > 4) occ = 4;
+  if (occ < 1) return KERDOCK_ERR_UNSUPPORTED;
+  PreArgs a;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.m = p.m;
+  a.n = p.n;
+  a.signs = p.signs();
+  a.sign_words = p.sign_words;
+  a.R = p.repr;
+  a.ldr = p.ldr;
+  a.status = p.status();
+  a.num_tiles = (p.ldr + k10::TI - 1) / k10::TI;
+  // groups of up to 16 CTAs on adjacent 16-row tiles (256 consecutive rows)
+  a.group = pick_group(a.num_tiles, 16);
+  int64_t ngrp = int64_t(p.num_sms) * occ / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  if (ngrp < 1) ngrp = 1;
+  kern<<<unsigned(ngrp * a.group), k10::THREADS, k10::SMEM, p.stream>>>(a);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
 template <typename OutT>
 int launch_typed(const Plan& p) {
   switch (p.k) {
@@ -896,7 +1100,7 @@ int launch_typed(const Plan& p) {
     case 4: return launch_small<4, OutT>(p);
     case 6: return launch_small<6, OutT>(p);
     case 8: return launch_small<8, OutT>(p);
-    case 10: return launch_small<10, OutT>(p);
+    case 10: return launch_d1024<OutT>(p);
     case 12:
       if (sizeof(OutT) == 2) return launch_d4096_tc(p);
       return launch_d4096<OutT>(p);
