@@ -49,7 +49,7 @@ def workload_config(wl):
 # unchanged.
 KERNEL_SOURCES = {
     "query_kernel": ["query.cu", "kerdock_internal.cuh"],
-    "preprocess_small_kernel": ["preprocess.cu", "kerdock_internal.cuh"],
+    "preprocess_d1024_kernel": ["preprocess.cu", "kerdock_internal.cuh"],
 }
 
 
@@ -314,9 +314,9 @@ def run_ours(args):
                 "traffic": profiled_traffic("query_kernel", WORKLOAD),
                 "algorithmic_bytes_per_launch": app_bytes, "peak_source": peak_kind}
     else:
-        roof = {"kernel": "preprocess_small_kernel", "bound": "hbm", "achieved": round(pre_gbs, 1),
+        roof = {"kernel": "preprocess_d1024_kernel", "bound": "hbm", "achieved": round(pre_gbs, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(pre_gbs / peak, 4),
-                "traffic": profiled_traffic("preprocess_small_kernel", WORKLOAD),
+                "traffic": profiled_traffic("preprocess_d1024_kernel", WORKLOAD),
                 "algorithmic_bytes_per_launch": pre_bytes, "peak_source": peak_kind}
 
     result = {
