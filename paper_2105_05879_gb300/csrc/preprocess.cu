@@ -973,6 +973,11 @@ __global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreA
   const uint32_t tme = tmem + (uint32_t((g & 3) * 32) << 16) + uint32_t((g >> 2) * 64);
 
   const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  // sign word of basis b for this thread's p range (zero for the identity basis)
+  auto sign_word = [&](int b) {
+    return b == D / 2 ? 0u : __ldg(a.signs + int64_t(b) * a.sign_words + s);
+  };
+  uint32_t sw_next = ir.beg < ir.end ? sign_word(int(ir.beg % B)) : 0u;
   int64_t cur_tile = -1;
   for (int64_t item = ir.beg; item < ir.end; ++item) {
     const int64_t tg = item / B;
@@ -1004,7 +1009,9 @@ __global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreA
     uint32_t w[64];
 #pragma unroll
     for (int c = 0; c < 4; ++c) tmem_ld16(tme + uint32_t(16 * c), w + 16 * c);
-    const uint32_t sw = ident ? 0u : __ldg(a.signs + int64_t(b) * a.sign_words + s);
+    // this basis's sign word was requested one basis ahead; request the next
+    const uint32_t sw = sw_next;
+    if (item + 1 < ir.end) sw_next = sign_word(b + 1 == int(B) ? 0 : b + 1);
     tmem_wait64(w);
     float2 v[32];
 #pragma unroll
