@@ -908,10 +908,17 @@ int launch_d4096_tc(const Plan& p) {
 // next basis overlaps the other warps' phase 2.
 namespace k10 {
 
-constexpr int TI = 16, THREADS = 256, D = 1024, NS = 32;
-constexpr int XST = 32 * TI + 16;  // floats per source: [w_lo][row] + 16 (bank shift)
-constexpr size_t SMEM = size_t(NS) * XST * 4 + 16;
-constexpr uint32_t TMEM_COLS = 128;  // 256 threads x 64 words = 128 lanes x 128 columns
+constexpr int D = 1024, NS = 32;
+
+// TI-row tiles: TI / 2 row pairs x 32 sources = one thread each.
+template <int TI>
+struct Cfg {
+  static constexpr int RP = TI / 2;
+  static constexpr int THREADS = RP * NS;
+  static constexpr int XST = 32 * TI + 16;  // floats per source: [w_lo][row] + 16 (bank shift)
+  static constexpr size_t SMEM = size_t(NS) * XST * 4 + 16;
+  static constexpr uint32_t TMEM_COLS = uint32_t(THREADS) * 64 / 128;  // 64 words per thread
+};
 
 // Asynchronous: the registers are valid after tmem_wait16 has named them.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
@@ -946,16 +953,20 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
       : "memory");
 }
 
-template <typename OutT>
-__global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreArgs a) {
+template <typename OutT, int TI>
+__global__ void __launch_bounds__(Cfg<TI>::THREADS, TI == 16 ? 2 : 1)
+    preprocess_d1024_kernel(const PreArgs a) {
+  using C = Cfg<TI>;
+  constexpr int XST = C::XST, RP = C::RP;
+  constexpr uint32_t TMEM_COLS = C::TMEM_COLS;
   constexpr int64_t B = D / 2 + 1;
   extern __shared__ __align__(16) float smem[];
   float* X = smem;  // [NS][XST]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + NS * XST);
   OutT* R = static_cast<OutT*>(a.R);
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int rp = lane & 7;              // rows 2 rp, 2 rp + 1 of the tile (both phases)
-  const int s = (lane >> 3) + 4 * g;    // phase 1: source s; phase 2: w_lo = s
+  const int rp = lane % RP;                       // rows 2 rp, 2 rp + 1 (both phases)
+  const int s = lane / RP + (32 / RP) * g;        // phase 1: source s; phase 2: w_lo = s
   const float sqrt_d = 32.f;
 
   if (g == 0) {
@@ -969,7 +980,7 @@ __global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreA
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
-  // warp g reaches lanes 32 (g mod 4) ..; warps 4..7 use columns 64 .. 127
+  // warp g reaches lanes 32 (g mod 4) ..; warps 4 j .. 4 j + 3 use columns 64 j ..
   const uint32_t tme = tmem + (uint32_t((g & 3) * 32) << 16) + uint32_t((g >> 2) * 64);
 
   const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
@@ -1055,15 +1066,21 @@ __global__ void __launch_bounds__(THREADS, 2) preprocess_d1024_kernel(const PreA
 
 template <typename OutT>
 int launch_d1024(const Plan& p) {
-  auto kern = k10::preprocess_d1024_kernel<OutT>;
+  // 16-row tiles, two CTAs per SM.  32-row tiles (one CTA of 16 warps per SM,
+  // twice the run length per output row) measured slower for both types:
+  // 0.495 vs 0.437 ms (float32) and 0.435 vs 0.420 ms (bfloat16), the SM
+  // idling at the CTA's two barriers per basis.
+  constexpr int TI = 16;
+  using C = k10::Cfg<TI>;
+  auto kern = k10::preprocess_d1024_kernel<OutT, TI>;
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(k10::SMEM)));
-  // the whole unified L1 as shared memory, so that two CTAs fit beside each other
+                                   int(C::SMEM)));
+  // the whole unified L1 as shared memory
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                    int(cudaSharedmemCarveoutMaxShared)));
   // CTAs per SM from the kernel's registers and shared memory (the runtime's
-  // occupancy query reports one for this kernel, though two fit), at most four
-  // for the 4 x 128 tensor-memory columns of an SM
+  // occupancy query reported one for the 16-row kernel, though two fit), and at
+  // most what the SM's 512 tensor-memory columns hold
   cudaFuncAttributes fa;
   KD_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
   int dev = 0, regs_sm = 0, smem_sm = 0, smem_rsv = 0;
@@ -1072,11 +1089,11 @@ int launch_d1024(const Plan& p) {
   KD_CUDA_TRY(
       cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   KD_CUDA_TRY(cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-  const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * k10::THREADS;  // 8-register granules
+  const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * C::THREADS;  // 8-register granules
   int occ = regs_cta > 0 ? regs_sm / regs_cta : 1;
-  const int by_smem = smem_sm / int(k10::SMEM + size_t(fa.sharedSizeBytes) + size_t(smem_rsv));
+  const int by_smem = smem_sm / int(C::SMEM + size_t(fa.sharedSizeBytes) + size_t(smem_rsv));
   if (by_smem < occ) occ = by_smem;
-  if (occ > 4) occ = 4;
+  if (occ > int(512 / C::TMEM_COLS)) occ = int(512 / C::TMEM_COLS);  // 512 columns per SM
   if (occ < 1) return KERDOCK_ERR_UNSUPPORTED;
   PreArgs a;
   a.A = p.A;
@@ -1088,14 +1105,14 @@ int launch_d1024(const Plan& p) {
   a.R = p.repr;
   a.ldr = p.ldr;
   a.status = p.status();
-  a.num_tiles = (p.ldr + k10::TI - 1) / k10::TI;
-  // groups of up to 16 CTAs on adjacent 16-row tiles (256 consecutive rows)
-  a.group = pick_group(a.num_tiles, 16);
+  a.num_tiles = (p.ldr + TI - 1) / TI;
+  // groups of CTAs on adjacent tiles covering 256 consecutive rows
+  a.group = pick_group(a.num_tiles, 256 / TI);
   int64_t ngrp = int64_t(p.num_sms) * occ / a.group;
   const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
   if (ngrp > items) ngrp = items;
   if (ngrp < 1) ngrp = 1;
-  kern<<<unsigned(ngrp * a.group), k10::THREADS, k10::SMEM, p.stream>>>(a);
+  kern<<<unsigned(ngrp * a.group), C::THREADS, C::SMEM, p.stream>>>(a);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }
