@@ -350,8 +350,7 @@ int kerdock_plan_set_tuning(kerdock_plan_t plan, int32_t ring_kb, int32_t crows)
   kd::Tuning tu;
   tu.ring_kb = ring_kb;
   tu.crows = crows;
-  kd::Dims dm;
-  kd::dims_add(dm, p, p.K, p.S);
+  const kd::Dims dm = kd::plan_dims(p);
   kd::LaunchCfg cfg{};
   if (!kd::make_cfg(dm, tu, kd::means_fit_smem(dm), cfg)) return KERDOCK_ERR_UNSUPPORTED;
   p.tuning = tu;

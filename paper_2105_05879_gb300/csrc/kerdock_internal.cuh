@@ -96,10 +96,12 @@ struct Dims {
   int64_t ldr = 0;         // representation row stride (elements)
   int64_t S = 0;           // candidate-set size
   int64_t KL = 0;          // K * ldr
+  int coef_warps = 3;      // coefficient warps of the kernel that runs (3: batch kernel)
 };
 
 size_t align_up(size_t v, size_t al);
 void dims_add(Dims& dm, const Plan& p, int64_t K, int64_t S);
+Dims plan_dims(const Plan& p);  // one plan's dims with its single-plan kernel's split
 bool means_fit_smem(const Dims& dm);
 bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c);
 QueryDesc plan_desc(const Plan& p);

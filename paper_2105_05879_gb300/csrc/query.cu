@@ -40,16 +40,26 @@ namespace {
 // sign-adds and a gathered row m multiply-adds, so the best split follows n/m:
 // measured on GB300 with m = n = 4096 (bfloat16), CW = 3 took 17.3 ms for 4096
 // queries against 19.3 ms (CW = 4) and 20.0 ms (CW = 5), while with m = 256,
-// n = 4096 CW = 5 was 1.7x faster than CW = 3.  The library's workloads have
-// m = n, so both constants are 3; the split stays a template parameter.
+// n = 4096 CW = 5 was 1.7x faster than CW = 3.  At m = n = 1024 a float32 row
+// is cheap to gather per byte and the coefficients set the pace: CW = 5 took
+// 0.573 ms for 1000 queries against 0.578 (CW = 4) and 0.631 ms (CW = 3); a
+// bfloat16 row costs the gather warps an unpacking step per element, and there
+// CW = 3 is best (0.655 ms against 0.696 and 0.687).
 constexpr int kFinalWarps = 4;
 constexpr int kFirstCoefWarp = 1;
 constexpr int kFirstFinalWarp = 12;
 constexpr int kWarps = kFirstFinalWarp + kFinalWarps;  // 16
 constexpr int kThreads = kWarps * 32;                   // 512
 constexpr int kFinalThreads = kFinalWarps * 32;
-constexpr int kCoefWarpsSmall = 3;  // n <= 1024
-constexpr int kCoefWarpsLarge = 3;  // n > 1024
+constexpr int kCoefWarpsSmallF32 = 5;   // n <= 1024, float32 rows
+constexpr int kCoefWarpsSmallBf16 = 3;  // n <= 1024, bfloat16 rows
+constexpr int kCoefWarpsLarge = 3;      // n > 1024
+constexpr int kCoefWarpsBatch = 3;      // mixed plans
+// the split of a single-plan kernel
+template <typename RT, bool XREG>
+constexpr int coef_warps() {
+  return !XREG ? kCoefWarpsLarge : sizeof(RT) == 4 ? kCoefWarpsSmallF32 : kCoefWarpsSmallBf16;
+}
 template <int CW>
 struct Roles {
   static constexpr int kCoefWarps = CW;
@@ -60,8 +70,9 @@ struct Roles {
 constexpr int kMaxSlots = 64;  // ring rows
 constexpr int kMaxChunks = 64;
 // > every CW: each coefficient warp steps CW chunks and starts at chunk cw < CW
-constexpr int kMinChunks =
-    (kCoefWarpsSmall > kCoefWarpsLarge ? kCoefWarpsSmall : kCoefWarpsLarge) + 1;
+// The ring must hold more chunks than the kernel's coefficient warps: each
+// coefficient warp steps CW chunks and starts at chunk cw < CW (Dims::coef_warps).
+static_assert(Dims{}.coef_warps == kCoefWarpsBatch, "the batch kernel's split is the default");
 constexpr int kXBufs = 3;
 constexpr int kMBufs = 2;
 constexpr int kFinalBarrier = 1;  // named barrier id of the finalizer warps
@@ -441,7 +452,7 @@ template <class Seq, int XMODE, int CW>
 __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
   const int lane = threadIdx.x & 31;
   const int cw = (threadIdx.x >> 5) - kFirstCoefWarp;
-  CoefState st{uint32_t(cw), 0u, uint64_t(cw), 0};  // nchunk >= kMinChunks > CW
+  CoefState st{uint32_t(cw), 0u, uint64_t(cw), 0};  // nchunk > CW (make_cfg)
   const int64_t nq = seq.size();
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
@@ -770,8 +781,8 @@ __global__ void __launch_bounds__(kThreads, 1) query_kernel(const QueryArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Shared sh;
   SingleSeq seq{a};
-  run_roles<SingleSeq, RT, GPT, false, XREG ? 0 : 1, XREG ? kCoefWarpsSmall : kCoefWarpsLarge>(
-      seq, a.cfg, sh, smem);
+  run_roles<SingleSeq, RT, GPT, false, XREG ? 0 : 1, coef_warps<RT, XREG>()>(seq, a.cfg, sh,
+                                                                              smem);
 }
 
 // Batch kernel: any mix of plans (types and sizes), one descriptor per query.
@@ -779,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1) query_batch_kernel(const BatchArg
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ Shared sh;
   BatchSeq seq{a};
-  run_roles<BatchSeq, float, 4, true, 2, kCoefWarpsSmall>(seq, a.cfg, sh, smem);
+  run_roles<BatchSeq, float, 4, true, 2, kCoefWarpsBatch>(seq, a.cfg, sh, smem);
 }
 
 }  // namespace
@@ -803,7 +814,7 @@ bool means_fit_smem(const Dims& dm) {
 // Shared-memory layout for a launch.  ring_kb caps the row ring (0 = default
 // 160 KiB), crows forces the rows per chunk (0 = four when the ring holds at
 // least eight such chunks, else two, else one).  Returns false when the ring
-// cannot hold kMinChunks chunks.
+// cannot hold more chunks than the kernel has coefficient warps.
 bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c) {
   c = LaunchCfg{};
   c.slot_bytes = dm.row_bytes;
@@ -820,11 +831,12 @@ bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c
   if (avail > cap) avail = cap;
   int ns = int(avail / per_slot);
   if (ns > kMaxSlots) ns = kMaxSlots;
-  int cr = tu.crows > 0 ? tu.crows : (ns >= 32 ? 4 : ns >= 2 * kMinChunks ? 2 : 1);
+  const int min_chunks = dm.coef_warps + 1;
+  int cr = tu.crows > 0 ? tu.crows : (ns >= 32 ? 4 : ns >= 2 * min_chunks ? 2 : 1);
   if (cr != 1 && cr != 2 && cr != 4) return false;
   c.crows = cr;
   c.nchunk = ns / cr;
-  if (c.nchunk < kMinChunks) return false;
+  if (c.nchunk < min_chunks) return false;
   if (c.nchunk > kMaxChunks) c.nchunk = kMaxChunks;
   ns = c.nchunk * cr;
   int g = 1;  // chunks per producer step: g * crows <= 32 lanes, g <= nchunk / 2
@@ -899,8 +911,10 @@ int launch_single(const QueryArgs& a, int64_t grid, cudaStream_t stream) {
 int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
   const int64_t granule = 16 / int64_t(p.elem_bytes());
   const bool xreg = p.n <= 1024;
-  const int64_t gthreads = xreg ? Roles<kCoefWarpsSmall>::kGatherThreads
-                                : Roles<kCoefWarpsLarge>::kGatherThreads;
+  const int64_t gthreads =
+      !xreg ? Roles<kCoefWarpsLarge>::kGatherThreads
+            : p.dtype == KERDOCK_BF16 ? Roles<coef_warps<__nv_bfloat16, true>()>::kGatherThreads
+                                      : Roles<coef_warps<float, true>()>::kGatherThreads;
   const int64_t gpt = (p.ldr / granule + gthreads - 1) / gthreads;
   if (p.dtype == KERDOCK_BF16) {
     if (gpt <= 1) return xreg ? launch_single<__nv_bfloat16, 1, true>(a, grid, p.stream)
@@ -924,6 +938,9 @@ int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
 Dims plan_dims(const Plan& p) {
   Dims dm;
   dims_add(dm, p, p.K, p.S);
+  dm.coef_warps = p.n > 1024                 ? kCoefWarpsLarge
+                  : p.dtype == KERDOCK_BF16 ? coef_warps<__nv_bfloat16, true>()
+                                            : coef_warps<float, true>();
   return dm;
 }
 
