@@ -44,7 +44,8 @@ namespace {
 // is cheap to gather per byte and the coefficients set the pace: CW = 5 took
 // 0.573 ms for 1000 queries against 0.578 (CW = 4) and 0.631 ms (CW = 3); a
 // bfloat16 row costs the gather warps an unpacking step per element, and there
-// CW = 3 is best (0.655 ms against 0.696 and 0.687).
+// CW = 3 is best (0.655 ms against 0.696 and 0.687, and 0.841 ms with CW = 2;
+// at n = 4096, CW = 2 took 22.3 ms against 17.3 ms).
 constexpr int kFinalWarps = 4;
 constexpr int kFirstCoefWarp = 1;
 constexpr int kFirstFinalWarp = 12;
@@ -53,12 +54,14 @@ constexpr int kThreads = kWarps * 32;                   // 512
 constexpr int kFinalThreads = kFinalWarps * 32;
 constexpr int kCoefWarpsSmallF32 = 5;   // n <= 1024, float32 rows
 constexpr int kCoefWarpsSmallBf16 = 3;  // n <= 1024, bfloat16 rows
-constexpr int kCoefWarpsLarge = 3;      // n > 1024
+constexpr int kCoefWarpsLarge = 3;      // n > 1024, float32 rows
+constexpr int kCoefWarpsLargeBf16 = 3;  // n > 1024, bfloat16 rows
 constexpr int kCoefWarpsBatch = 3;      // mixed plans
 // the split of a single-plan kernel
 template <typename RT, bool XREG>
 constexpr int coef_warps() {
-  return !XREG ? kCoefWarpsLarge : sizeof(RT) == 4 ? kCoefWarpsSmallF32 : kCoefWarpsSmallBf16;
+  return sizeof(RT) == 2 ? (XREG ? kCoefWarpsSmallBf16 : kCoefWarpsLargeBf16)
+                         : (XREG ? kCoefWarpsSmallF32 : kCoefWarpsLarge);
 }
 template <int CW>
 struct Roles {
@@ -911,10 +914,12 @@ int launch_single(const QueryArgs& a, int64_t grid, cudaStream_t stream) {
 int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
   const int64_t granule = 16 / int64_t(p.elem_bytes());
   const bool xreg = p.n <= 1024;
+  const bool bf = p.dtype == KERDOCK_BF16;
   const int64_t gthreads =
-      !xreg ? Roles<kCoefWarpsLarge>::kGatherThreads
-            : p.dtype == KERDOCK_BF16 ? Roles<coef_warps<__nv_bfloat16, true>()>::kGatherThreads
-                                      : Roles<coef_warps<float, true>()>::kGatherThreads;
+      xreg ? (bf ? Roles<coef_warps<__nv_bfloat16, true>()>::kGatherThreads
+                 : Roles<coef_warps<float, true>()>::kGatherThreads)
+           : (bf ? Roles<coef_warps<__nv_bfloat16, false>()>::kGatherThreads
+                 : Roles<coef_warps<float, false>()>::kGatherThreads);
   const int64_t gpt = (p.ldr / granule + gthreads - 1) / gthreads;
   if (p.dtype == KERDOCK_BF16) {
     if (gpt <= 1) return xreg ? launch_single<__nv_bfloat16, 1, true>(a, grid, p.stream)
@@ -938,9 +943,9 @@ int dispatch_single(const Plan& p, const QueryArgs& a, int64_t grid) {
 Dims plan_dims(const Plan& p) {
   Dims dm;
   dims_add(dm, p, p.K, p.S);
-  dm.coef_warps = p.n > 1024                 ? kCoefWarpsLarge
-                  : p.dtype == KERDOCK_BF16 ? coef_warps<__nv_bfloat16, true>()
-                                            : coef_warps<float, true>();
+  const bool bf = p.dtype == KERDOCK_BF16;
+  dm.coef_warps = p.n > 1024 ? (bf ? coef_warps<__nv_bfloat16, false>() : coef_warps<float, false>())
+                             : (bf ? coef_warps<__nv_bfloat16, true>() : coef_warps<float, true>());
   return dm;
 }
 
