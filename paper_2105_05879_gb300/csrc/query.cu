@@ -48,8 +48,8 @@ namespace {
 // at n = 4096, CW = 2 took 22.3 ms against 17.3 ms).
 constexpr int kFinalWarps = 4;
 constexpr int kFirstCoefWarp = 1;
-constexpr int kFirstFinalWarp = 12;
-constexpr int kWarps = kFirstFinalWarp + kFinalWarps;  // 16
+constexpr int kWarps = 16;
+constexpr int kFirstFinalWarp = kWarps - kFinalWarps;
 constexpr int kThreads = kWarps * 32;                   // 512
 constexpr int kFinalThreads = kFinalWarps * 32;
 constexpr int kCoefWarpsSmallF32 = 5;   // n <= 1024, float32 rows
@@ -619,8 +619,7 @@ __device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& 
     uint32_t prefix = 0, mask = 0, remaining = uint32_t(qd.S);
     for (int pass = 0; pass < 4; ++pass) {
       const int shift = 24 - 8 * pass;
-      sh.hist[ft] = 0;
-      sh.hist[ft + kFinalThreads] = 0;
+      for (int i = ft; i < 256; i += kFinalThreads) sh.hist[i] = 0;
       named_barrier_sync(kFinalBarrier, kFinalThreads);
       for (int i = ft; i < m; i += kFinalThreads) {
         const uint32_t key = abs_key(mus[i]);
