@@ -676,6 +676,24 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 
   const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  // This thread's eight sign words of basis b (mask words k = 8 tid + u), as
+  // loaded from the p-order table; requested one basis ahead.
+  constexpr int MW = MASK_WORDS / THREADS;
+  auto mask_p = [&](int u) {
+    const int k = tid * MW + u;
+    const int p2 = k >> 7, l = (k >> 2) & 31, j = k & 3;
+    return p2 * 256 + ((l >> 2) + 8 * (j >> 1)) * 16 + 2 * (l & 3) + 8 * (j & 1);
+  };
+  auto load_words = [&](int b, uint32_t (&wd)[MW]) {
+    const uint32_t* srow = a.signs + int64_t(b == D / 2 ? 0 : b) * a.sign_words;
+#pragma unroll
+    for (int u = 0; u < MW; ++u) {
+      const int p = mask_p(u);
+      wd[u] = b == D / 2 ? 0u : __ldg(srow + (p >> 5)) >> (p & 31);
+    }
+  };
+  uint32_t wnext[MW];
+  if (ir.beg < ir.end) load_words(int(ir.beg % B), wnext);
   int64_t cur_tile = -1;
   for (int64_t item = ir.beg; item < ir.end; ++item) {
     const int64_t tg = item / B;
@@ -707,21 +725,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       cur_tile = t;
     }
 
-    // Step (i) of Lemma 6 as bfloat16 sign masks in the threads' word order.
+    // Step (i) of Lemma 6 as bfloat16 sign masks in the threads' word order,
+    // from the words requested during the previous basis; then request the
+    // next basis's words.
     {
-      const uint32_t* srow = a.signs + int64_t(ident ? 0 : b) * a.sign_words;
+      uint32_t wcur[MW];
 #pragma unroll
-      for (int u = 0; u < MASK_WORDS / THREADS; ++u) {
-        const int k = tid * (MASK_WORDS / THREADS) + u;
-        const int p2 = k >> 7, l = (k >> 2) & 31, j = k & 3;
-        const int p = p2 * 256 + ((l >> 2) + 8 * (j >> 1)) * 16 + 2 * (l & 3) + 8 * (j & 1);
-        uint32_t mk = 0u;
-        if (!ident) {
-          const uint32_t wd = __ldg(srow + (p >> 5)) >> (p & 31);
-          mk = ((wd & 1u) << 15) | ((wd & 2u) << 30);
-        }
-        maskt[k] = mk;
-      }
+      for (int u = 0; u < MW; ++u) wcur[u] = wnext[u];
+      if (item + 1 < ir.end) load_words(b + 1 == int(B) ? 0 : b + 1, wnext);
+#pragma unroll
+      for (int u = 0; u < MW; ++u)
+        maskt[tid * MW + u] = ((wcur[u] & 1u) << 15) | ((wcur[u] & 2u) << 30);
     }
     __syncthreads();  // masks ready; every warp is done reading E for the previous item
 
