@@ -97,3 +97,27 @@ def test_fig1_errors_worst_case_over_trials():
     assert mu_err == pytest.approx(0.25)
     assert h_err == pytest.approx(np.sqrt(0.5 ** 2 + 0.1 ** 2))
     assert exact == pytest.approx(2 / 3)
+
+
+def test_profiled_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    # committed DRAM counters count only while the profiled kernel's own source
+    # files are unchanged, and only for the workload they were taken on
+    import json
+    import bench
+    csrc = tmp_path / "paper_2105_05879_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "query.cu").write_text("kernel v1")
+    (csrc / "kerdock_internal.cuh").write_text("header")
+    (csrc / "other.cu").write_text("unrelated")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.source_hash(bench.KERNEL_SOURCES["query_kernel"])
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"query_kernel": {"source_hash": h, "workload": "n1024", "dram_bytes_per_launch": 123}}))
+    assert bench.profiled_traffic("query_kernel", "n1024") == 123
+    assert bench.profiled_traffic("query_kernel", "n64") is None
+    assert bench.profiled_traffic("preprocess_d1024_kernel", "n1024") is None
+    (csrc / "other.cu").write_text("changed elsewhere")      # not one of the kernel's files
+    assert bench.profiled_traffic("query_kernel", "n1024") == 123
+    (csrc / "query.cu").write_text("kernel v2")               # the kernel changed
+    assert bench.profiled_traffic("query_kernel", "n1024") is None
