@@ -430,6 +430,7 @@ class KerdockPlan:
                           self.table.data_ptr(), self.table.numel(), self._stream_ptr())
         self.A = None
         self._ws = None
+        self._ws_shared = None
 
     def _stream_ptr(self):
         s = self._stream if self._stream is not None else self.torch.cuda.current_stream(self.device)
@@ -465,8 +466,21 @@ class KerdockPlan:
         if nb == 0:
             return None
         if self._ws is None or self._ws.numel() < nb:
+            if self._ws is not None:
+                self.sync()  # the plan's stream may still read the old buffer
             self._ws = self.torch.empty(nb, dtype=self.torch.uint8, device=self.device)
         return self._ws
+
+    def shared_workspace(self, q):
+        """Workspace of kerdock_apply_shared for q queries, kept by the plan
+        (the library's kernels read it after the call returns)."""
+        nb = load_library().kerdock_apply_shared_workspace_bytes(self.handle, q)
+        if self._ws_shared is None or self._ws_shared.numel() < nb:
+            if self._ws_shared is not None:
+                self.sync()
+            self._ws_shared = self.torch.empty(max(nb, 1), dtype=self.torch.uint8,
+                                               device=self.device)
+        return self._ws_shared, nb
 
     def alloc_outputs(self, q):
         t = self.torch
@@ -505,8 +519,7 @@ class KerdockPlan:
         assert X.dtype == t.float32 and X.is_cuda and X.dim() == 2 and X.stride(1) == 1
         q = X.shape[0]
         idx, val, cnt = out if out is not None else self.alloc_outputs(q)
-        nb = load_library().kerdock_apply_shared_workspace_bytes(self.handle, q)
-        ws = t.empty(max(nb, 1), dtype=t.uint8, device=self.device)
+        ws, nb = self.shared_workspace(q)
         self._sync_stream()
         kerdock_apply_shared(self.handle, X.data_ptr(), q, X.stride(0), float(eps), int(seed), flags,
                              idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), ws.data_ptr(), nb)
@@ -519,6 +532,7 @@ class KerdockPlan:
         c.handle = kerdock_plan_clone(self.handle, J, K, S)
         c.info = kerdock_plan_info(c.handle)
         c.repr, c.table, c._stream, c.A, c._ws = self.repr, self.table, self._stream, self.A, None
+        c._ws_shared = None
         c._parent = self
         return c
 
