@@ -106,6 +106,10 @@ def test_theory_parameters_match_theorem3(lib):
                                   (0.7, 0.6, 0.1, 0.9, 1000), (1.0, 0.9, 0.2, 1.0, 2048)]:
         J, Kb = K.kerdock_theory_parameters(a, eps, delta, eta, m)
         assert (J, Kb) == oq.theorem3_parameters(a, eps, delta, eta, m)
+    # and against values worked by hand from Theorem 3's statement
+    assert K.kerdock_theory_parameters(1.0, 0.5, 0.0, 0.2, 16) == (473, 9)
+    assert K.kerdock_theory_parameters(2.0, 1.0, 0.5, 0.2, 16) == (1892, 9)
+    assert K.kerdock_theory_parameters(0.5, 0.5, 0.0, 0.5, 2) == (119, 3)
 
 
 def test_theory_parameters_errors(lib):

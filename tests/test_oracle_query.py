@@ -148,3 +148,21 @@ def test_lazy_apply_equals_materialised():
     r2 = query.apply_one(A, None, x, 0.25, 3, 5, 32, 3, 40, k, lazy=True, return_mu=True)
     np.testing.assert_array_equal(r1[0], r2[0])
     np.testing.assert_allclose(r1[2], r2[2], atol=1e-12)
+
+
+def test_theorem3_parameters_hand_values():
+    # Theorem 3: J >= 4 e^2 |A|_{2->inf}^2 / gamma^2 and K >= 2 log(m / eta), with
+    # gamma = (eps - delta) / 2.  Worked by hand (e^2 = 7.38905...):
+    #   a = 1, eps = 0.5, delta = 0:   gamma = 1/4, J = ceil(64 e^2) = ceil(472.90) = 473
+    #   m = 1024, eta = 0.01:          K = ceil(2 ln 102400) = ceil(23.07) = 24
+    #   a = 2, eps = 1, delta = 0.5:   gamma = 1/4, J = ceil(256 e^2) = ceil(1891.6) = 1892
+    #   m = 16, eta = 0.2:             K = ceil(2 ln 80) = ceil(8.76) = 9
+    #   m = 1, eta = 1:                K = max(1, ceil(0)) = 1
+    #   a = 1/2, eps = 1/2, delta = 0: J = ceil(16 e^2) = ceil(118.2) = 119;
+    #   m = 2, eta = 1/2:              K = ceil(2 ln 4) = ceil(2.77) = 3
+    # A J from gamma instead of gamma^2 (119 and 473), or from eps instead of
+    # gamma (119), or K from log10 (11 and 4), fails one of them.
+    assert query.theorem3_parameters(1.0, 0.5, 0.0, 0.01, 1024) == (473, 24)
+    assert query.theorem3_parameters(2.0, 1.0, 0.5, 0.2, 16) == (1892, 9)
+    assert query.theorem3_parameters(1.0, 0.5, 0.0, 1.0, 1)[1] == 1
+    assert query.theorem3_parameters(0.5, 0.5, 0.0, 0.5, 2) == (119, 3)
