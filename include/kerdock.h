@@ -98,7 +98,7 @@ typedef struct {
 } kerdock_plan_info_t;
 
 /* Create a plan for an m x n matrix.  dtype: KERDOCK_F32 or KERDOCK_BF16.
- * J >= 1, 1 <= K <= 16, 1 <= S; S is clamped to m.  N = J*K <= 2^24.
+ * J >= 1, 1 <= K <= 32, 1 <= S; S is clamped to m.  N = J*K <= 2^24.
  * Host only (no CUDA call).  *plan is set to NULL on failure. */
 int kerdock_plan_create(kerdock_plan_t* plan, int64_t m, int64_t n, int32_t dtype,
                         int32_t J, int32_t K, int32_t S);
@@ -174,6 +174,10 @@ int kerdock_apply_debug(kerdock_plan_t plan, const float* X_dev, int64_t q, int6
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     streams, other plans) race with each other.  Nothing in it needs to
  *     be cleared between calls.
+ *   - The current device must be the plan's device (KERDOCK_ERR_INVALID_ARG
+ *     otherwise).  The looked-up address belongs to the device's current
+ *     context: do not use this entry point after cudaDeviceReset in the
+ *     same process.
  *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
 int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
                           float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
@@ -189,7 +193,7 @@ int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, in
 typedef struct {
   kerdock_plan_t plan;  /* a bound, preprocessed plan on the current device */
   const float* x;       /* device pointer to this query's n floats */
-  int32_t J, K;         /* batch size and number of batches of the median of means (K <= 16) */
+  int32_t J, K;         /* batch size and number of batches of the median of means (K <= 32) */
   int32_t S;            /* candidate-set size, 1 <= S <= m (Sec. 4 uses S = 10 s) */
   int32_t flags;        /* KERDOCK_FLAG_FULL_OUTPUT or 0 */
   float eps;            /* threshold (> 0 unless full output) */
@@ -326,7 +330,7 @@ int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q, int
  * Then for unit x with Ax in Sigma(A, s, delta), ||mu - Ax||_inf < gamma with
  * probability >= 1 - eta.  Host only; no plan needed.
  * Errors: INVALID_ARG unless a > 0, eps > delta >= 0, 0 < eta <= 1, m >= 1;
- * UNSUPPORTED when K exceeds the library's 16 batches or J*K its sample
+ * UNSUPPORTED when K exceeds the library's 32 batches or J*K its sample
  * limit (J and K are still written). */
 int kerdock_theory_parameters(double a_row_norm_max, double eps, double delta, double eta,
                               int64_t m, int32_t* J, int32_t* K);
@@ -346,6 +350,15 @@ int kerdock_debug_signs(kerdock_plan_t plan, uint32_t* host_out, size_t host_wor
  * KERDOCK_ERR_DEVICE_TIMEOUT in the plan's status word and returns (no trap,
  * no hang).  The next kerdock_sync reports it and clears it. */
 int kerdock_debug_wait_timeout(kerdock_plan_t plan, int32_t max_polls);
+
+/* Test of the query kernel's own failure path: later kerdock_apply /
+ * kerdock_apply_noalloc launches of this plan give up a wait after max_polls
+ * unsuccessful mbarrier polls (0 restores the default of 2^22).  With a tiny
+ * limit the waits run out during normal operation: every role of the kernel
+ * stops, the CTA waits (boundedly) for the row copies it issued, and
+ * KERDOCK_ERR_DEVICE_TIMEOUT is recorded for kerdock_sync; outputs of such a
+ * launch are unspecified.  Host only. */
+int kerdock_debug_set_poll_limit(kerdock_plan_t plan, uint32_t max_polls);
 
 /* Test entry for the library's bfloat16 tensor-core product (the products of
  * the learned network and of kerdock_apply_shared).  Plane z of C (float32,

@@ -12,7 +12,9 @@
 namespace kd {
 
 constexpr int kMaxLogD = 12;          // d <= 4096
-constexpr int kMaxK = 16;             // number of median-of-means batches
+constexpr int kMaxK = 32;             // number of median-of-means batches
+constexpr int kRegK = 16;             // batches whose means a finalizer thread holds in registers
+constexpr uint32_t kDefaultPollLimit = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr int64_t kMaxN = 1 << 24;    // samples per query
 constexpr size_t kStatusBytes = 256;  // status word area at the start of the table buffer
 
@@ -45,6 +47,7 @@ struct Plan {
   int device = -1;
   int num_sms = 0;
   Tuning tuning;
+  uint32_t poll_limit = kDefaultPollLimit;  // query-kernel waits (lowered only by a test hook)
 
   uint32_t* status() const { return reinterpret_cast<uint32_t*>(table); }
   uint32_t* signs() const {
@@ -68,6 +71,7 @@ struct LaunchCfg {
   uint32_t off_coef, off_x, off_means, off_mu, off_sel, off_vals, total;
   float* means_gmem;     // per-CTA batch means in global memory when non-null
   uint32_t* status;
+  uint32_t poll_limit;   // mbarrier polls before a wait gives up (kDefaultPollLimit)
 };
 
 // Everything one query needs, with pointers already offset to that query.

@@ -314,6 +314,11 @@ int kerdock_apply_noalloc(kerdock_plan_t plan, const float* X_dev, int64_t q, in
   if (ldx < p.n || flags < 0 || flags > KERDOCK_FLAG_FULL_OUTPUT) return KERDOCK_ERR_INVALID_ARG;
   if (!(flags & KERDOCK_FLAG_FULL_OUTPUT) && !(eps > 0.0f)) return KERDOCK_ERR_INVALID_ARG;
   if (q > (int64_t(1) << 31) / (p.S > 0 ? p.S : 1)) return KERDOCK_ERR_UNSUPPORTED;
+  // the scratch array is looked up for the current device: it must be the
+  // device the plan's memory lives on
+  int dev = 0;
+  KD_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != p.device) return KERDOCK_ERR_INVALID_ARG;
   return kd::launch_apply_noalloc(p, X_dev, q, ldx, eps, seed, flags, out_idx, out_val,
                                   out_count);
 }
@@ -368,6 +373,12 @@ int kerdock_debug_wait_timeout(kerdock_plan_t plan, int32_t max_polls) {
   if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
   kd::wait_timeout_kernel<<<1, 32, 0, p.stream>>>(p.status(), uint32_t(max_polls));
   KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+int kerdock_debug_set_poll_limit(kerdock_plan_t plan, uint32_t max_polls) {
+  if (plan == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  plan->p.poll_limit = max_polls == 0 ? kd::kDefaultPollLimit : max_polls;
   return KERDOCK_OK;
 }
 

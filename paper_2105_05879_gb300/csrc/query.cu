@@ -223,23 +223,36 @@ struct Shared {
   uint32_t hist[256];
   int scan[kFinalWarps];
   uint32_t digit, remaining;
-  int abort_flag;
+  int abort_flag;       // a wait ran out: every role stops
+  int final_abort;      // the finalizer warps' shared decision to stop
+  uint64_t filled;      // ring chunks the producer armed (for the drain after an abort)
 };
 
-// Bounded wait that also gives up once another role has aborted.
+// Bounded wait that also gives up once another role has aborted.  After
+// cfg.poll_limit unsuccessful polls it records a timeout in the status word
+// and raises the CTA's abort flag.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, Shared& sh,
-                                           uint32_t* status) {
+                                           const LaunchCfg& cfg) {
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
+    const bool limit = it >= cfg.poll_limit;
+    if ((it & 255u) == 255u || limit) {
       if (*reinterpret_cast<volatile int*>(&sh.abort_flag)) return false;
-      if (it > (1u << 22)) {
-        set_status(status, kStatusTimeout);
+      if (limit) {
+        set_status(cfg.status, kStatusTimeout);
         *reinterpret_cast<volatile int*>(&sh.abort_flag) = 1;
         return false;
       }
     }
   }
+}
+
+// A wait whose outcome the whole warp shares: if any lane gave up, every lane
+// returns false, so a warp never splits between stopping and going on to its
+// next warp-wide instruction.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, Shared& sh,
+                                          const LaunchCfg& cfg) {
+  return __all_sync(0xffffffffu, wait_phase(bar, parity, sh, cfg));
 }
 
 // Single-plan launch: the plan-wide descriptor plus the query batch shape.
@@ -325,6 +338,8 @@ __device__ __forceinline__ void init_barriers(Shared& sh, const LaunchCfg& c) {
       mbar_init(&sh.means_empty[b], 1);
     }
     sh.abort_flag = 0;
+    sh.final_abort = 0;
+    sh.filled = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -339,13 +354,19 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
   uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
   uint64_t filled = 0;             // chunks filled so far
   const int ci = lane / CR, r = lane % CR;
+  // every exit publishes how many chunks were armed (their copies may still
+  // be in flight after an abort; the CTA waits for them before it exits)
+  auto publish = [&]() {
+    if (lane == 0) sh.filled = filled;
+  };
   const int64_t nq = seq.size();
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
     const int xb = int(qs % kXBufs);
-    if (qs >= kXBufs &&
-        !wait_phase(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, cfg.status))
+    if (qs >= kXBufs && !warp_wait(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, cfg)) {
+      publish();
       return;
+    }
     float* xq = rg.xbuf + xb * cfg.xpad;
     for (int64_t p = lane; p < cfg.xpad; p += 32) xq[p] = p < qd.n ? qd.x[p] : 0.f;
     __syncwarp();
@@ -355,27 +376,32 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
     for (int64_t c0 = 0; c0 < qchunks; c0 += cfg.pgroup) {
       const int cnt = int(qchunks - c0 < cfg.pgroup ? qchunks - c0 : cfg.pgroup);
       bool ok = true;
+      uint32_t cs = cslot + uint32_t(ci), ph = cphase;
+      if (cs >= nchunk) {
+        cs -= nchunk;
+        ph ^= 1u;
+      }
+      if (ci < cnt && filled + uint64_t(ci) >= nchunk)
+        ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, cfg);
+      // copies are issued only when every chunk of the step is free, so an
+      // abort leaves no chunk partly armed
+      if (!__all_sync(0xffffffffu, ok)) {
+        publish();
+        return;
+      }
       if (ci < cnt) {
-        uint32_t cs = cslot + uint32_t(ci), ph = cphase;
-        if (cs >= nchunk) {
-          cs -= nchunk;
-          ph ^= 1u;
-        }
-        if (filled + uint64_t(ci) >= nchunk)
-          ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, cfg.status);
         const int64_t j = (c0 + ci) * CR + r;
-        if (ok && j < qd.N) {
+        if (j < qd.N) {
           const uint64_t ell =
               sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j), uint64_t(qd.L));
           if (qd.ells_out) qd.ells_out[j] = int64_t(ell);
           mbar_arrive_expect_tx(&sh.row_full[cs], qd.row_bytes);
           bulk_g2s(rg.ring + (size_t(cs) * CR + r) * cfg.slot_bytes,
                    R + int64_t(ell) * qd.row_bytes, qd.row_bytes, &sh.row_full[cs]);
-        } else if (ok) {
+        } else {
           mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
         }
       }
-      if (__any_sync(0xffffffffu, !ok)) return;
       filled += uint64_t(cnt);
       cslot += uint32_t(cnt);
       if (cslot >= nchunk) {
@@ -384,6 +410,7 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
       }
     }
   }
+  publish();
 }
 
 // ---------------------------------------------------------------- coefficients
@@ -426,8 +453,7 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
     else
       kerdock_coefficients<XREG, 1>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr, xq, c);
     // the gather warps must be done with this chunk's previous samples
-    if (st.cc >= nchunk && !wait_phase(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg.status))
-      return false;
+    if (st.cc >= nchunk && !warp_wait(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg)) return false;
     if (lane == 0) {
 #pragma unroll
       for (int s2 = 0; s2 < 4; ++s2) {
@@ -460,7 +486,7 @@ __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& r
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
     const int xb = int(qs % kXBufs);
-    if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg.status)) return;
+    if (!warp_wait(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg)) return;
     const float* xq = rg.xbuf + xb * cfg.xpad;
     bool ok;
     if (XMODE == 0) {
@@ -497,8 +523,8 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
   int batch_left = qd.J, batch = 0;
   for (int64_t j0 = 0; j0 < qd.N; j0 += CR) {
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
-    if (!wait_phase(&sh.row_full[cs], ph, sh, cfg.status)) return false;
-    if (!wait_phase(&sh.coef_full[cs], ph, sh, cfg.status)) return false;
+    if (!warp_wait(&sh.row_full[cs], ph, sh, cfg)) return false;
+    if (!warp_wait(&sh.coef_full[cs], ph, sh, cfg)) return false;
 #pragma unroll
     for (int s2 = 0; s2 < 4; ++s2) {
       if (s2 >= cnt) break;
@@ -513,7 +539,7 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
       }
       if (--batch_left == 0) {
         if (batch == 0 && qs >= kMBufs &&
-            !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg.status))
+            !warp_wait(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg))
           return false;
         float* mrow = means + int64_t(batch) * qd.ldr;
 #pragma unroll
@@ -580,8 +606,16 @@ __device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& 
     const QueryDesc qd = seq.get(qs);
     const int m = int(qd.m);
     const int mb = int(qs % kMBufs), xb = int(qs % kXBufs);
-    if (!wait_phase(&sh.means_full[mb], uint32_t(qs / kMBufs) & 1u, sh, cfg.status)) return;
-    if (!wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg.status)) return;
+    {
+      // the four finalizer warps stop together or go on together: each thread
+      // waits, any that gave up raises the shared flag, and all read it after
+      // the barrier (the flag is never lowered within a launch)
+      bool ok = wait_phase(&sh.means_full[mb], uint32_t(qs / kMBufs) & 1u, sh, cfg);
+      if (ok) ok = wait_phase(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg);
+      if (!ok) *reinterpret_cast<volatile int*>(&sh.final_abort) = 1;
+      named_barrier_sync(kFinalBarrier, kFinalThreads);
+      if (*reinterpret_cast<volatile int*>(&sh.final_abort)) return;
+    }
     const float* means = rg.means_base + int64_t(mb) * cfg.mstride;
     const float* xq = rg.xbuf + xb * cfg.xpad;
     // a6: median over the K batch means.
@@ -591,21 +625,39 @@ __device__ void final_role(const Seq& seq, const LaunchCfg& cfg, const Regions& 
         med = means[col];
       } else if (qd.K == 2) {
         med = 0.5f * (means[col] + means[qd.ldr + col]);
-      } else {
-        float v[kMaxK];
+      } else if (qd.K <= kRegK) {
+        float v[kRegK];
 #pragma unroll
-        for (int kk = 0; kk < kMaxK; ++kk) v[kk] = kk < qd.K ? means[kk * qd.ldr + col] : 0.f;
+        for (int kk = 0; kk < kRegK; ++kk) v[kk] = kk < qd.K ? means[kk * qd.ldr + col] : 0.f;
         const int r_lo = (qd.K - 1) / 2, r_hi = qd.K / 2;
         float lo = 0.f, hi = 0.f;
 #pragma unroll
-        for (int i = 0; i < kMaxK; ++i) {
+        for (int i = 0; i < kRegK; ++i) {
           if (i >= qd.K) break;
           int rank = 0;
 #pragma unroll
-          for (int j = 0; j < kMaxK; ++j)
+          for (int j = 0; j < kRegK; ++j)
             if (j < qd.K && (v[j] < v[i] || (v[j] == v[i] && j < i))) ++rank;
           if (rank == r_lo) lo = v[i];
           if (rank == r_hi) hi = v[i];
+        }
+        med = (qd.K & 1) ? lo : 0.5f * (lo + hi);
+      } else {
+        // more batches than registers (Theorem 3's K at large m / eta): the
+        // same rank selection, reading the means where they are
+        const int r_lo = (qd.K - 1) / 2, r_hi = qd.K / 2;
+        float lo = 0.f, hi = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < qd.K; ++i) {
+          const float vi = means[int64_t(i) * qd.ldr + col];
+          int rank = 0;
+#pragma unroll 4
+          for (int j = 0; j < qd.K; ++j) {
+            const float vj = means[int64_t(j) * qd.ldr + col];
+            if (vj < vi || (vj == vi && j < i)) ++rank;
+          }
+          if (rank == r_lo) lo = vi;
+          if (rank == r_hi) hi = vi;
         }
         med = (qd.K & 1) ? lo : 0.5f * (lo + hi);
       }
@@ -774,6 +826,20 @@ __device__ __forceinline__ void run_roles(const Seq& seq, const LaunchCfg& cfg, 
   } else {
     final_role(seq, cfg, rg, sh);
   }
+  // Every role has returned (all waits are bounded).  After an abort, row
+  // copies the producer issued may still be in flight: wait, boundedly, for
+  // the last arming of every ring chunk to land before the CTA's shared
+  // memory is released.
+  __syncthreads();
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&sh.abort_flag)) {
+    const uint64_t filled = sh.filled, nchunk = uint64_t(cfg.nchunk);
+    for (uint64_t c = 0; c < nchunk && c < filled; ++c) {
+      const uint64_t last = filled - 1 - (filled - 1 - c) % nchunk;  // last fill of chunk c
+      const uint32_t parity = uint32_t(last / nchunk) & 1u;
+      for (uint32_t it = 0; it < kDefaultPollLimit; ++it)
+        if (mbar_try_wait(&sh.row_full[c], parity)) break;
+    }
+  }
 }
 
 // Single-plan kernel: the representation type, granules per gather thread and
@@ -819,6 +885,7 @@ bool means_fit_smem(const Dims& dm) {
 // cannot hold more chunks than the kernel has coefficient warps.
 bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c) {
   c = LaunchCfg{};
+  c.poll_limit = kDefaultPollLimit;
   c.slot_bytes = dm.row_bytes;
   c.xpad = dm.xpad;
   c.mstride = dm.KL;
@@ -965,6 +1032,7 @@ int launch_apply(const Plan& p, const float* X, int64_t q, int64_t ldx, float ep
   if (!make_cfg(dm, p.tuning, smem_means, a.cfg)) return KERDOCK_ERR_UNSUPPORTED;
   a.cfg.means_gmem = smem_means ? nullptr : static_cast<float*>(ws);
   a.cfg.status = p.status();
+  a.cfg.poll_limit = p.poll_limit;
   a.base = plan_desc(p);
   set_query_params(a.base, p.J, p.K, p.S, eps, seed, flags);
   a.base.x = X;
@@ -1040,6 +1108,7 @@ int launch_apply_noalloc(const Plan& p, const float* X, int64_t q, int64_t ldx, 
   if (rc != KERDOCK_OK) return rc;
   a.cfg.means_gmem = static_cast<float*>(scratch);
   a.cfg.status = p.status();
+  a.cfg.poll_limit = p.poll_limit;
   a.base = plan_desc(p);
   set_query_params(a.base, p.J, p.K, p.S, eps, seed, flags);
   a.base.x = X;

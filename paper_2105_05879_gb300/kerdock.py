@@ -40,7 +40,7 @@ EXPORTED = [
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
     "kerdock_mlp_set_skip", "kerdock_theory_parameters", "kerdock_apply_shared_workspace_bytes",
-    "kerdock_apply_shared", "kerdock_debug_gemm",
+    "kerdock_apply_shared", "kerdock_debug_gemm", "kerdock_debug_set_poll_limit",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -151,6 +151,7 @@ def load_library(path=None):
                                                      ctypes.POINTER(c_i32)]),
         "kerdock_plan_clone": (ctypes.c_int, [ctypes.POINTER(P), P, c_i32, c_i32, c_i32]),
         "kerdock_debug_wait_timeout": (ctypes.c_int, [P, c_i32]),
+        "kerdock_debug_set_poll_limit": (ctypes.c_int, [P, ctypes.c_uint32]),
         "kerdock_debug_gemm": (ctypes.c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_i64, c_i32,
                                                    c_i32, c_i32, c_i32, c_vp, c_i64, c_vp]),
         "kerdock_sync": (ctypes.c_int, [P]),
@@ -373,6 +374,11 @@ def kerdock_mlp_destroy(mlp):
 
 def kerdock_debug_wait_timeout(plan, max_polls):
     _check(load_library().kerdock_debug_wait_timeout(plan, max_polls), "kerdock_debug_wait_timeout")
+
+
+def kerdock_debug_set_poll_limit(plan, max_polls):
+    _check(load_library().kerdock_debug_set_poll_limit(plan, max_polls),
+           "kerdock_debug_set_poll_limit")
 
 
 def kerdock_debug_gemm(A, sAm, sAk, B, sBn, sBk, M, N, K, kc, C, ldc, stream=None):

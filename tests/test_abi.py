@@ -57,7 +57,7 @@ def test_plan_info_sizes(lib):
 @pytest.mark.parametrize("args,code", [
     ((0, 4, 0, 1, 1, 1), -1), ((4, 0, 0, 1, 1, 1), -1), ((4, 4, 2, 1, 1, 1), -1),
     ((4, 4, 0, 0, 1, 1), -1), ((4, 4, 0, 1, 0, 1), -1), ((4, 4, 0, 1, 1, 0), -1),
-    ((4097, 4, 0, 1, 1, 1), -2), ((4, 4097, 0, 1, 1, 1), -2), ((4, 4, 0, 1, 17, 1), -2),
+    ((4097, 4, 0, 1, 1, 1), -2), ((4, 4097, 0, 1, 1, 1), -2), ((4, 4, 0, 1, 33, 1), -2),
     ((4, 4, 0, 1 << 21, 16, 1), -2),
 ])
 def test_create_rejects_bad_arguments(lib, args, code):
@@ -118,7 +118,9 @@ def test_theory_parameters_errors(lib):
         with pytest.raises(K.KerdockError) as ei:
             K.kerdock_theory_parameters(*args)
         assert ei.value.code == -1  # KERDOCK_ERR_INVALID_ARG
-    # the guarantee at n = 1024, eps = 0.125, eta = 0.01 needs K = 24 > 16 batches
+    # the guarantee at n = 1024, eps = 0.125, eta = 0.01 needs K = 24 batches,
+    # within the library's 32; eta = 1e-9 at m = 4096 needs K = 59 > 32
+    assert K.kerdock_theory_parameters(1.0, 0.125, 0.0, 0.01, 1024)[1] == 24
     with pytest.raises(K.KerdockError) as ei:
-        K.kerdock_theory_parameters(1.0, 0.125, 0.0, 0.01, 1024)
+        K.kerdock_theory_parameters(1.0, 0.125, 0.0, 1e-9, 4096)
     assert ei.value.code == -2  # KERDOCK_ERR_UNSUPPORTED

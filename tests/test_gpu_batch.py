@@ -14,7 +14,7 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
-def _setup(K, torch, shapes, counts, rng):
+def _setup(K, torch, shapes, counts, rng, s_range=(2, 9)):
     plans, mats, reps = [], [], []
     for (n, dtype), seed in zip(shapes, range(71, 71 + len(shapes))):
         A = workloads.random_orthogonal(n, seed).astype(np.float32)
@@ -28,7 +28,7 @@ def _setup(K, torch, shapes, counts, rng):
     for pi, cnt in enumerate(counts):
         n = shapes[pi][0]
         for r in range(cnt):
-            s = int(rng.integers(2, 9))
+            s = int(min(rng.integers(*s_range), max(2, n // 8)))
             z = workloads.sparse_codes(n, 1, s, 1 / math.sqrt(s), int(rng.integers(1 << 30)))[0]
             x = (z @ f32(mats[pi])).astype(np.float32)
             Kb = 2 if r % 3 else 3
@@ -40,7 +40,7 @@ def _setup(K, torch, shapes, counts, rng):
     return plans, mats, reps, specs, meta
 
 
-def _check(batch, specs, meta, mats, reps, shapes, oracle_limit):
+def _check(batch, specs, meta, mats, reps, shapes, oracle_limit, oracle_dtypes=("f32",)):
     got = batch.results()
     checked_oracle = {}
     for qi, ((pi, x), sp) in enumerate(zip(meta, specs)):
@@ -50,7 +50,7 @@ def _check(batch, specs, meta, mats, reps, shapes, oracle_limit):
         tidx, tval = oq.dense_truth(A64, x64, sp["eps"])
         np.testing.assert_array_equal(idx, tidx)           # the method recovers h_eps(Ax)
         np.testing.assert_allclose(val, A64[idx] @ x64, atol=1e-5)
-        if dtype == "f32" and checked_oracle.get(pi, 0) < oracle_limit:
+        if dtype in oracle_dtypes and checked_oracle.get(pi, 0) < oracle_limit:
             k = batch.specs[qi]["plan"].info["k"]
             ridx, rval = oq.apply_one(A64, reps[pi], x64, sp["eps"], sp["seed"], sp["index"],
                                       sp["J"], sp["K"], sp["S"], k, lazy=reps[pi] is None)
@@ -115,7 +115,31 @@ def test_batch_rejects_bad_queries():
     with pytest.raises(K.KerdockError) as e:  # S > m
         K.KerdockBatch([dict(spec, S=65)])
     assert e.value.code == -1
-    with pytest.raises(K.KerdockError) as e:  # K > 16
-        K.KerdockBatch([dict(spec, K=17)])
+    with pytest.raises(K.KerdockError) as e:  # K > 32
+        K.KerdockBatch([dict(spec, K=33)])
     assert e.value.code == -2
     plan.close()
+
+
+def test_batch_n4096_plan_and_large_sparsities():
+    # The batching workload's ranges: the precision workload's plan (n = 4096,
+    # bfloat16, 68.75 GB: x in shared memory, rows of several granules per
+    # gather thread) next to float32 plans, with s ~ U{4..64} (s <= n/8),
+    # J = 24 s, S = 10 s, eps = 0.5/sqrt(s).  Every query against the dense
+    # truth; some of every plan against the oracle's streaming step (rows of
+    # the representation computed lazily for n >= 1024).
+    torch = torch_cuda()
+    K = build_and_load()
+    rng = np.random.default_rng(17)
+    shapes = [(4096, "bf16"), (1024, "f32"), (256, "f32"), (1024, "bf16")]
+    counts = [21, 13, 6, 4]
+    plans, mats, reps, specs, meta = _setup(K, torch, shapes, counts, rng, s_range=(4, 65))
+    assert max(sp["S"] // 10 for sp in specs) > 32  # large sparsities are in the batch
+    batch = K.KerdockBatch(specs, graph=True)
+    batch.launch()
+    batch.sync()
+    _check(batch, specs, meta, mats, reps, shapes, oracle_limit=1, oracle_dtypes=("f32", "bf16"))
+    batch.close()
+    for p in plans:
+        p.close()
+    torch.cuda.empty_cache()

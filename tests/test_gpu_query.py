@@ -90,9 +90,11 @@ def test_query_n64_workload(K):
     plan.close()
 
 
-@pytest.mark.parametrize("Kb", [1, 3, 4, 5])
+@pytest.mark.parametrize("Kb", [1, 3, 4, 5, 17, 24, 32])
 def test_query_median_variants(K, Kb):
-    # K = 1 (plain mean), odd K (middle value), even K > 2 (two middle values)
+    # K = 1 (plain mean), odd K (middle value), even K > 2 (two middle values);
+    # K > 16 takes the finalizer's median from memory instead of registers
+    # (K = 24 is Theorem 3's K at m = 1024, eta = 0.01)
     n = 64
     A = workloads.random_orthogonal(n, 21).astype(np.float32)
     Z = workloads.sparse_codes(n, 24, 4, 0.5, 22)
@@ -272,4 +274,35 @@ def test_device_wait_timeout_is_reported_and_recoverable(K):
     idx, val, cnt = plan.apply(X, 0.5, 0)
     plan.sync()
     assert cnt.cpu().tolist() == [1, 0] and idx[0, 0].item() == 3
+    plan.close()
+
+
+def test_query_kernel_waits_run_out_and_recover(K):
+    # With the poll limit lowered to one poll the query kernel's own waits run
+    # out in the middle of normal operation: every role stops (the finalizer
+    # warps together), the CTA waits for the row copies it issued, the launch
+    # records a timeout that kerdock_sync reports once, and the next launch
+    # with the default limit answers exactly as before.
+    torch = torch_cuda()
+    n = 256
+    A = workloads.random_orthogonal(n, 81).astype(np.float32)
+    Z = workloads.sparse_codes(n, 64, 8, 0.35, 82)
+    X = torch.from_numpy(workloads.queries_from_codes(f32(A), Z).astype(np.float32)).cuda()
+    plan = K.KerdockPlan(n, n, J=120, K=2, S=80)
+    plan.preprocess(torch.from_numpy(A).cuda())
+    ref = [t.cpu().numpy() for t in plan.apply(X, 0.15, 5)]
+    plan.sync()
+    K.kerdock_debug_set_poll_limit(plan.handle, 1)
+    plan.apply(X, 0.15, 5)
+    with pytest.raises(K.KerdockError) as e:
+        plan.sync()
+    assert e.value.code == -7  # KERDOCK_ERR_DEVICE_TIMEOUT
+    plan.sync()  # reported once, then cleared
+    K.kerdock_debug_set_poll_limit(plan.handle, 0)
+    got = [t.cpu().numpy() for t in plan.apply(X, 0.15, 5)]
+    plan.sync()
+    np.testing.assert_array_equal(got[2], ref[2])
+    for q in range(X.shape[0]):
+        np.testing.assert_array_equal(got[0][q, :ref[2][q]], ref[0][q, :ref[2][q]])
+        np.testing.assert_array_equal(got[1][q, :ref[2][q]], ref[1][q, :ref[2][q]])
     plan.close()
