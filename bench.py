@@ -243,6 +243,13 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # clock soak: the same step, untimed, for about 1.5 s, so that the clock
+    # record covers sustained load and not only the short timed region
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 1.5:
+        for _ in range(50):
+            step()
+        torch.cuda.synchronize()
     t_tab, t_pre, t_app = [], [], []
     for _ in range(args.steps):
         flush.zero_()
@@ -309,10 +316,15 @@ def run_ours(args):
     app_gbs = app_bytes / (app_ms * 1e6)
     gather_gbs = gather_bytes / (app_ms * 1e6)
     if app_ms >= pre_ms:
+        traffic = profiled_traffic("query_kernel", WORKLOAD)
         roof = {"kernel": "query_kernel", "bound": "hbm", "achieved": round(app_gbs, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(app_gbs / peak, 4),
-                "traffic": profiled_traffic("query_kernel", WORKLOAD),
-                "algorithmic_bytes_per_launch": app_bytes, "peak_source": peak_kind}
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": app_bytes, "peak_source": peak_kind,
+                "note": ("algorithmic bytes = gathered representation rows + refined rows of A "
+                         "(4 MiB, L2-resident, so they cost L2 and not HBM reads) + x"),
+                "gather_only_frac": round(gather_gbs / peak, 4),
+                "dram_frac": (round(traffic / (app_ms * 1e6) / peak, 4) if traffic else None)}
     else:
         roof = {"kernel": "preprocess_d1024_kernel", "bound": "hbm", "achieved": round(pre_gbs, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(pre_gbs / peak, 4),
@@ -350,9 +362,18 @@ def run_ours(args):
     }
     if rank == 0 and args.cpu_baseline and world == 1:
         result["cpu_baseline"] = cpu_baseline(wl, budget_s=args.cpu_seconds)
+        dense = result["cpu_baseline"].get("dense_cpu")
+        if dense:
+            # Sec. 4 compares the method's query time with the naive product
+            result["query"]["ratio_vs_dense_cpu_all_cores"] = round(
+                (app_ms / q) / (dense["ms_for_all_queries"] / q), 4)
+    plan.close()
+    del plan, ws, idx, val, cnt, A, X, A_d, X_d, flush
+    torch.cuda.empty_cache()
+    if world == 1 and args.forms:
+        result["forms"] = collect_forms(args, K, torch, peak)
     if rank == 0:
         print(json.dumps(result), flush=True)
-    plan.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -381,6 +402,30 @@ def _support_match(torch, A64_dev, X, idx, cnt, eps):
     for r in range(X.shape[0]):
         ok += np.array_equal(idx[r, :cnt[r]], np.nonzero(Vh[r])[0])
     return ok
+
+
+def collect_forms(args, K, torch, peak):
+    """The three forms on this GPU, each summarised as a sub-object of the
+    main line: precision (n = 4096, bfloat16 beside plain float32), batching
+    (2048 mixed queries, one graph-captured launch) and the learned proposal
+    (n = 2048) against the plain method at equal support recall."""
+    fargs = argparse.Namespace(**vars(args))
+    fargs.steps, fargs.warmup = min(args.steps, 5), 3
+    out = {}
+    for name, fn in (("precision_n4096", run_precision), ("batching_mixed_2048", run_batch),
+                     ("learned_n2048", run_learned)):
+        t0 = time.perf_counter()
+        try:
+            line = fn(fargs, K, torch, peak)
+            keep = {k: v for k, v in line.items()
+                    if k not in ("metric", "n_gpus", "steps", "warmup", "higher_is_better",
+                                 "scaling", "vs_baseline", "data")}
+            keep["wall_s"] = round(time.perf_counter() - t0, 1)
+            out[name] = keep
+        except Exception as exc:  # a form that fails is reported, not fatal
+            out[name] = {"error": repr(exc)[:400]}
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_precision(args, K, torch, peak):
@@ -510,21 +555,24 @@ def run_learned(args, K, torch, peak):
     """Learned form: n = 2048 (d = 4096, float32 representation), supports of
     4 runs of 8; the network (2 x 512, bfloat16) is trained on 200k
     method-generated pairs and evaluated on 10k queries against the plain
-    method."""
-    import math
+    method.  The learned pipeline's candidate count S' sets its operating
+    point: a recall-vs-throughput curve over S', and the smallest S' whose
+    support recall reaches the plain method's (equal support accuracy)."""
     from paper_2105_05879_gb300.learned import LearnedProposal, support_recall
     wl = workloads.WORKLOADS["n2048_blocks"]
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     A_np = wl.make_A().astype(np.float32)
     A = torch.from_numpy(A_np).to(dev)
-    A64 = A_np.astype(np.float64)
+    A64_dev = A.double()
     plan = K.KerdockPlan(wl.m, wl.n, J=wl.J, K=wl.K, S=wl.S, dtype="f32", device=dev)
     plan.preprocess(A)
 
     def queries(q, seed):
+        # x = A^T z of the float32 A, formed in float64 on the GPU (inputs only)
         Z = workloads.sparse_codes(wl.n, q, wl.s, wl.amp, seed, blocks=wl.blocks)
-        return torch.from_numpy((Z @ A64).astype(np.float32)).to(dev), Z
+        Zd = torch.from_numpy(Z).to(dev)
+        return (Zd @ A64_dev).float(), Z
 
     lp = LearnedProposal(plan, J_sketch=128, K_sketch=2, S_prime=96, hidden=512, max_batch=4096,
                          seed=3, residual=True)
@@ -538,35 +586,50 @@ def run_learned(args, K, torch, peak):
     del mu, Y, Xtr
     Xev, Zev = queries(10000, 901)
     truth = [np.nonzero(np.abs(z) >= wl.eps)[0] for z in Zev]
-    ms_plain = _timed(torch, stream, lambda: plan.apply(Xev, wl.eps, 51), max(1, args.steps))
+    reps = max(1, args.steps)
+    ms_plain = _timed(torch, stream, lambda: plan.apply(Xev, wl.eps, 51), reps)
     pi, pv, pc = plan.apply(Xev, wl.eps, 51)
-    ms_learn = _timed(torch, stream, lambda: lp.apply(Xev, wl.eps, 51), max(1, args.steps))
-    li, lv, lc = lp.apply(Xev, wl.eps, 51)
-    ms_sk = _timed(torch, stream, lambda: lp.apply_plain_sketch(Xev, wl.eps, 51), max(1, args.steps))
-    si, sv, sc = lp.apply_plain_sketch(Xev, wl.eps, 51)
-    torch.cuda.synchronize()
     rp = support_recall(pi, pc, truth)
-    rl = support_recall(li, lc, truth)
-    rs = support_recall(si, sc, truth)
+    curve = []
+    for Sp in (96, 128, 160, 224, 320):
+        lp.S_prime = Sp
+        ms_l = _timed(torch, stream, lambda: lp.apply(Xev, wl.eps, 51), reps)
+        li, lv, lc = lp.apply(Xev, wl.eps, 51)
+        ms_s = _timed(torch, stream, lambda: lp.apply_plain_sketch(Xev, wl.eps, 51), reps)
+        si, sv, sc = lp.apply_plain_sketch(Xev, wl.eps, 51)
+        torch.cuda.synchronize()
+        rl, rs = support_recall(li, lc, truth), support_recall(si, sc, truth)
+        curve.append({"S_prime": Sp, "learned_queries/s": round(Xev.shape[0] / (ms_l / 1e3), 1),
+                      "learned_recall": round(rl[0], 5), "learned_exact": round(rl[1], 4),
+                      "sketch_only_queries/s": round(Xev.shape[0] / (ms_s / 1e3), 1),
+                      "sketch_only_recall": round(rs[0], 5)})
     q = Xev.shape[0]
+    eq = next((c for c in curve if c["learned_recall"] >= round(rp[0], 5)), None)
+    head = eq or curve[0]
     line = {
-        "metric": METRIC, "value": round(q / (ms_learn / 1e3), 1), "unit": "queries/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_learn, 3),
+        "metric": METRIC, "value": head["learned_queries/s"], "unit": "queries/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * q / head["learned_queries/s"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
         "data": "synthetic (seeded random orthogonal A, block-sparse codes; Sec. 4 recipe)",
         "config": {"workload": ("learned form: n=m=2048 (d=4096, 2049 bases, f32), z 32-sparse in "
                                 "4 runs of 8, eps=0.5/sqrt(32); plain J=375,K=2,S=320 vs learned "
-                                "sketch J=128,K=2 + residual MLP 2x512 bf16 (input |mu|) + S'=96; "
-                                "200k training pairs, 10 epochs, 10k eval"), "form": "learned"},
-        "learned": {"queries/s": round(q / (ms_learn / 1e3), 1), "recall": round(rl[0], 4),
-                    "exact": round(rl[1], 4), "train_s": round(train_s, 1),
-                    "loss_first_last": [round(losses[0], 3), round(losses[-1], 3)]},
-        "plain": {"queries/s": round(q / (ms_plain / 1e3), 1), "recall": round(rp[0], 4),
+                                "sketch J=128,K=2 + residual MLP 2x512 bf16 (input |mu|) + top-S' "
+                                "refine; 200k training pairs, 10 epochs, 10k eval"),
+                   "form": "learned"},
+        "plain": {"queries/s": round(q / (ms_plain / 1e3), 1), "recall": round(rp[0], 5),
                   "exact": round(rp[1], 4)},
-        "plain_same_budget": {"queries/s": round(q / (ms_sk / 1e3), 1), "recall": round(rs[0], 4),
-                              "exact": round(rs[1], 4),
-                              "note": "top-S' of |mu| from the same sketch, no network"},
-        "gpu_launches": max(1, args.steps) * lp.launches_per_apply(q),
+        "equal_recall": ({"S_prime": eq["S_prime"], "learned_queries/s": eq["learned_queries/s"],
+                          "learned_recall": eq["learned_recall"],
+                          "speedup_vs_plain": round(eq["learned_queries/s"] /
+                                                    (q / (ms_plain / 1e3)), 3)}
+                         if eq else None),
+        "curve": curve,
+        "train": {"pairs": 200000, "epochs": 10, "s": round(train_s, 1),
+                  "loss_first_last": [round(losses[0], 3), round(losses[-1], 3)]},
+        # plain: one query kernel; learned: sketch, network, refine; sketch
+        # only: sketch and refine
+        "gpu_launches": reps * (1 + len(curve) * (lp.launches_per_apply(q) + -(-q // 65536) + 1)),
     }
     plan.close()
     return line
@@ -772,73 +835,145 @@ def run_form(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(wl, budget_s=20.0, queries=None):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the
-    workload: the Lemma 6 preprocessing of a subset of bases and the streaming
-    step for a few queries; scaled to queries/s for one full step."""
+def host_cores():
+    """Host cores this process may use (the affinity mask, else os.cpu_count())."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, budget_s=20.0, steps=None):
+    """The FP64 oracle as it stands, on all host cores (one single-threaded
+    worker process per core, started with spawn), on a bounded sample of the
+    workload; also the naive dense product A x on the same cores.  Runs in a
+    child process so that no worker is forked from a process that has touched
+    the GPU.  With steps, returns one value per step (the reference arm)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--_oracle_sample", str(budget_s)]
-    if queries:
-        cmd += ["--_oracle_queries", str(queries)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if steps:
+        cmd += ["--_oracle_steps", str(steps)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         return {"value": None, "error": out.stderr[-400:]}
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def oracle_sample(budget_s, queries=None):
+# Oracle workers (spawned processes, one thread each).  Each builds the
+# workload's A and X itself, so the timed calls carry no data transfer.
+_W = {}
+
+
+def _oracle_worker_init(name):
     from oracle import kerdock as okd
     from oracle import query as oq
-
-    wl = workloads.WORKLOADS[WORKLOAD]
+    wl = workloads.WORKLOADS[name]
     A = wl.make_A().astype(np.float32).astype(np.float64)
     X = workloads.queries_from_codes(A, wl.make_codes()).astype(np.float32).astype(np.float64)
-    k = int(round(math.log2(wl.n)))
+    _W.update(wl=wl, A=A, X=X, okd=okd, oq=oq, k=int(round(math.log2(wl.n))))
+
+
+def _oracle_basis(b):
+    _W["okd"].representation_lemma6(_W["A"], _W["k"], bases=[b])
+    return b
+
+
+def _oracle_query(q):
+    wl = _W["wl"]
+    _W["oq"].apply_one(_W["A"], None, _W["X"][q], wl.eps, wl.seed_apply, q, wl.J, wl.K, wl.S,
+                       _W["k"], lazy=True)
+    return q
+
+
+def _dense_queries(rows):
+    A, X, wl = _W["A"], _W["X"], _W["wl"]
+    for q in rows:
+        v = A @ X[q]
+        np.nonzero(np.abs(v) >= wl.eps)
+    return len(rows)
+
+
+def oracle_sample(budget_s, steps=None):
+    """One step of the workload (Lemma 6 preprocessing of every basis, then
+    the streaming step for every query) timed on a bounded sample: all bases
+    when they fit in 40 % of the budget, and as many queries as fit in the
+    rest, both spread over one worker per core and scaled to the full step.
+    The naive dense product h_eps(Ax) is timed on the same workers."""
+    import multiprocessing as mp
+    wl = workloads.WORKLOADS[WORKLOAD]
     nb = wl.n // 2 + 1
-    # preprocessing: as many bases as fit in ~40% of the budget (at least 4)
-    t0 = time.perf_counter()
-    done = 0
-    while done < nb:
-        okd.representation_lemma6(A, k, bases=[done])
-        done += 1
-        if done >= 4 and time.perf_counter() - t0 > 0.4 * budget_s:
-            break
-    t_pre = (time.perf_counter() - t0) / done * nb
-    # streaming step: rows computed lazily (the full FP64 representation is
-    # 4.3 GB; the per-query arithmetic is the same as with it materialised)
-    t1 = time.perf_counter()
-    nq = 0
-    while nq < (queries or wl.queries):
-        oq.apply_one(A, None, X[nq], wl.eps, wl.seed_apply, nq, wl.J, wl.K, wl.S, k, lazy=True)
-        nq += 1
-        if queries is None and nq >= 2 and time.perf_counter() - t1 > 0.6 * budget_s:
-            break
-    t_q = (time.perf_counter() - t1) / nq
+    C = host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(C, initializer=_oracle_worker_init, initargs=(WORKLOAD,)) as pool:
+        pool.map(_oracle_basis, range(C))                  # workers up and warm
+
+        def one_step(bud):
+            t0 = time.perf_counter()
+            done = 0
+            while done < nb:
+                chunk = list(range(done, min(nb, done + C)))
+                pool.map(_oracle_basis, chunk, chunksize=1)
+                done += len(chunk)
+                if time.perf_counter() - t0 > 0.4 * bud:
+                    break
+            t_pre = (time.perf_counter() - t0) / done * nb
+            t1 = time.perf_counter()
+            nq = 0
+            while nq < wl.queries:
+                chunk = list(range(nq, min(wl.queries, nq + C)))
+                pool.map(_oracle_query, chunk, chunksize=1)
+                nq += len(chunk)
+                if time.perf_counter() - t1 > 0.6 * bud:
+                    break
+            t_q = (time.perf_counter() - t1) / nq            # wall seconds per query on C cores
+            return t_pre, t_q, done, nq
+
+        per_step = []
+        if steps:
+            for _ in range(steps):
+                t_pre, t_q, done, nq = one_step(budget_s)
+                per_step.append(wl.queries / (t_pre + wl.queries * t_q))
+        else:
+            t_pre, t_q, done, nq = one_step(budget_s)
+        # the naive dense product for every query of the step, on the same cores
+        parts = [list(range(i, wl.queries, C)) for i in range(C)]
+        pool.map(_dense_queries, parts)
+        t2 = time.perf_counter()
+        pool.map(_dense_queries, parts)
+        t_dense = time.perf_counter() - t2
+        t3 = time.perf_counter()
+        pool.map(_dense_queries, [list(range(200))])          # one core, one query at a time
+        dense_1core = (time.perf_counter() - t3) / 200
     step_s = t_pre + wl.queries * t_q
-    return {"value": round(wl.queries / step_s, 4), "unit": "queries/s", "cores": 1,
-            "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, 1 thread: Lemma 6 preprocessing of {done}/{nb} bases "
-                       f"and {nq}/{wl.queries} queries (lazy rows), scaled to one step "
-                       f"(preprocess + {wl.queries} queries)"),
-            "preprocess_s_est": round(t_pre, 2), "query_s": round(t_q, 3)}
+    res = {"value": round(wl.queries / step_s, 4), "unit": "queries/s", "cores": C,
+           "kind": "oracle",
+           "sample": (f"FP64 numpy oracle, {C} single-threaded worker processes (one per host "
+                      f"core): Lemma 6 preprocessing of {done}/{nb} bases and {nq}/{wl.queries} "
+                      f"queries (lazy rows), scaled to one step (preprocess + {wl.queries} "
+                      f"queries)"),
+           "preprocess_s_est": round(t_pre, 3), "query_s_per_query_wall": round(t_q, 5),
+           "dense_cpu": {"ms_for_all_queries": round(1e3 * t_dense, 3),
+                         "queries/s": round(wl.queries / t_dense, 1),
+                         "ms_per_query_1core": round(1e3 * dense_1core, 4),
+                         "what": "naive h_eps(Ax): FP64 A @ x and the threshold, per query"}}
+    if steps:
+        res["per_step"] = [round(v, 4) for v in per_step]
+    return res
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle, single-threaded, each step a bounded
-    sample (a few Lemma 6 bases + one query) scaled to the same metric."""
+    """The reference arm: the FP64 oracle on all host cores, each step a
+    bounded sample (all Lemma 6 bases when they fit, a round of queries per
+    core) scaled to the same metric."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
     wl = workloads.WORKLOADS[WORKLOAD]
-    vals = []
-    res = None
-    for i in range(args.warmup + args.steps):
-        res = cpu_baseline(wl, budget_s=4.0, queries=1)
-        if res.get("value") is None:
-            print(json.dumps({"impl": "reference", "unavailable": res.get("error", "oracle failed")}))
-            return
-        if i >= args.warmup:
-            vals.append(res["value"])
+    res = cpu_baseline(wl, budget_s=2.0, steps=args.warmup + args.steps)
+    if res.get("value") is None:
+        print(json.dumps({"impl": "reference", "unavailable": res.get("error", "oracle failed")}))
+        return
+    vals = res["per_step"][args.warmup:]
     value = float(np.mean(vals))
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "queries/s",
@@ -846,9 +981,10 @@ def run_reference(args):
         "ms_per_step": round(1e3 * wl.queries / value, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random orthogonal A, sparse codes; Sec. 4 recipe)",
-        "config": dict(workload_config(wl), parallelism="cpu oracle"),
-        "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": 1,
+        "config": dict(workload_config(wl), parallelism=f"cpu oracle, {res['cores']} cores"),
+        "cpu_baseline": {"value": round(value, 4), "unit": "queries/s", "cores": res["cores"],
                          "kind": "oracle", "sample": res["sample"]},
+        "dense_cpu": res["dense_cpu"],
         "e2e": {"value": round(value, 4), "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -863,14 +999,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the precision / batching / learned sub-objects of the main line")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1",
                              "n1024_shared"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--_oracle_queries", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--_oracle_steps", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args._oracle_sample is not None:
-        print(json.dumps(oracle_sample(args._oracle_sample, args._oracle_queries)))
+        print(json.dumps(oracle_sample(args._oracle_sample, args._oracle_steps)))
         return
     if args.warmup < 3:
         args.warmup = 3

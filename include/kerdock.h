@@ -335,6 +335,40 @@ int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q, int
 int kerdock_theory_parameters(double a_row_norm_max, double eps, double delta, double eta,
                               int64_t m, int32_t* J, int32_t* K);
 
+/* ------------------------------------------------------------------------
+ * FP64 checks of a preprocessed representation against A, on the GPU (the
+ * precision form keeps float64 for these checks only).  Both read the plan's
+ * A (the matrix given to kerdock_preprocess) and the device representation;
+ * both are asynchronous on the plan's stream and allocate nothing.
+ * ------------------------------------------------------------------------ */
+
+/* Reconstruction (Lemma 6 read backwards: W W = d I, so the slab T_b = A Pi
+ * D_b W gives back A Pi D_b = T_b W / d).  For each basis b in [b0, b0 + nb)
+ * err_dev[b - b0] receives, in float64,
+ *     max over i < ldr, p < d of | (1/d) (T_b W)[i][p] (-1)^{Q_b(p)} - Apad[i][p] |
+ * (for the identity basis b = d/2: | R[d/2][p][i] / sqrt(d) - Apad[i][p] |),
+ * where Apad[i][p] = A[i][p] for i < m, p < n and 0 elsewhere (padding
+ * columns p >= n and padding rows i in [m, ldr) must come back as 0).
+ * err_dev: nb doubles, device, 8-byte aligned (overwritten).
+ * Errors: INVALID_ARG for a NULL pointer, b0 < 0, nb < 1, b0 + nb > d/2 + 1 or
+ * a current device other than the plan's; NOT_BOUND, NOT_PREPROCESSED;
+ * UNSUPPORTED for nb > 65535 (check in pieces); ALIGNMENT. */
+int kerdock_check_reconstruction(kerdock_plan_t plan, int64_t b0, int64_t nb, double* err_dev);
+
+/* Tight frame (Prop. 2 through the design: each basis is orthonormal, so
+ * sum_w s_{b,w} s_{b,w}^T = d I_n and sum_{l in bases} R[l] <R[l], y> =
+ * nb d A A^T y; over all d/2 + 1 bases this is sum_j B_j B_j^T = (d/2+1) I).
+ * For P probe vectors y_p (Y_dev: P x m float64, row-major, 1 <= P <= 4):
+ *     frame_dev[p][i] = sum over rows l = (b, w), b in [b0, b0 + nb), of
+ *                       R[l][i] <R[l], y_p>            (float64 accumulation)
+ *     ref_dev[p][i]   = nb d (A A^T y_p)_i             (float64, from A)
+ * frame_dev and ref_dev: P x m doubles, device, 8-byte aligned (overwritten).
+ * The residual frame - ref is zero for an exact representation.
+ * Errors as kerdock_check_reconstruction, and INVALID_ARG for P outside
+ * [1, 4]. */
+int kerdock_check_tight_frame(kerdock_plan_t plan, const double* Y_dev, int32_t P, int64_t b0,
+                              int64_t nb, double* frame_dev, double* ref_dev);
+
 /* Synchronise the plan's stream and report the first error any kernel of
  * this plan recorded in the device status word (then clear it). */
 int kerdock_sync(kerdock_plan_t plan);

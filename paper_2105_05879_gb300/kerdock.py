@@ -41,6 +41,7 @@ EXPORTED = [
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
     "kerdock_mlp_set_skip", "kerdock_theory_parameters", "kerdock_apply_shared_workspace_bytes",
     "kerdock_apply_shared", "kerdock_debug_gemm", "kerdock_debug_set_poll_limit",
+    "kerdock_check_reconstruction", "kerdock_check_tight_frame",
 ]
 
 KERDOCK_MLP_INPUT_LINEAR = 0
@@ -152,6 +153,8 @@ def load_library(path=None):
         "kerdock_plan_clone": (ctypes.c_int, [ctypes.POINTER(P), P, c_i32, c_i32, c_i32]),
         "kerdock_debug_wait_timeout": (ctypes.c_int, [P, c_i32]),
         "kerdock_debug_set_poll_limit": (ctypes.c_int, [P, ctypes.c_uint32]),
+        "kerdock_check_reconstruction": (ctypes.c_int, [P, c_i64, c_i64, c_vp]),
+        "kerdock_check_tight_frame": (ctypes.c_int, [P, c_vp, c_i32, c_i64, c_i64, c_vp, c_vp]),
         "kerdock_debug_gemm": (ctypes.c_int, [c_vp, c_i64, c_i64, c_vp, c_i64, c_i64, c_i32,
                                                    c_i32, c_i32, c_i32, c_vp, c_i64, c_vp]),
         "kerdock_sync": (ctypes.c_int, [P]),
@@ -381,6 +384,16 @@ def kerdock_debug_set_poll_limit(plan, max_polls):
            "kerdock_debug_set_poll_limit")
 
 
+def kerdock_check_reconstruction(plan, b0, nb, err_dev):
+    _check(load_library().kerdock_check_reconstruction(plan, b0, nb, err_dev),
+           "kerdock_check_reconstruction")
+
+
+def kerdock_check_tight_frame(plan, Y_dev, P, b0, nb, frame_dev, ref_dev):
+    _check(load_library().kerdock_check_tight_frame(plan, Y_dev, P, b0, nb, frame_dev, ref_dev),
+           "kerdock_check_tight_frame")
+
+
 def kerdock_debug_gemm(A, sAm, sAk, B, sBn, sBk, M, N, K, kc, C, ldc, stream=None):
     _check(load_library().kerdock_debug_gemm(A, sAm, sAk, B, sBn, sBk, M, N, K, kc, C, ldc,
                                                   stream), "kerdock_debug_gemm")
@@ -530,6 +543,29 @@ class KerdockPlan:
         kerdock_apply_shared(self.handle, X.data_ptr(), q, X.stride(0), float(eps), int(seed), flags,
                              idx.data_ptr(), val.data_ptr(), cnt.data_ptr(), ws.data_ptr(), nb)
         return idx, val, cnt
+
+    def check_reconstruction(self, b0=0, nb=None):
+        """Float64 reconstruction error per basis (kerdock_check_reconstruction),
+        as a float64 CUDA tensor of nb entries."""
+        t = self.torch
+        nb = self.info["num_bases"] - b0 if nb is None else nb
+        err = t.empty(nb, dtype=t.float64, device=self.device)
+        self._sync_stream()
+        kerdock_check_reconstruction(self.handle, b0, nb, err.data_ptr())
+        return err
+
+    def check_tight_frame(self, Y, b0=0, nb=None):
+        """(frame, ref) of kerdock_check_tight_frame for the probes Y (P x m
+        float64 CUDA tensor, P <= 4)."""
+        t = self.torch
+        assert Y.dtype == t.float64 and Y.is_cuda and Y.is_contiguous() and Y.dim() == 2
+        nb = self.info["num_bases"] - b0 if nb is None else nb
+        frame = t.empty_like(Y)
+        ref = t.empty_like(Y)
+        self._sync_stream()
+        kerdock_check_tight_frame(self.handle, Y.data_ptr(), Y.shape[0], b0, nb, frame.data_ptr(),
+                                  ref.data_ptr())
+        return frame, ref
 
     def clone(self, J, K, S):
         """A plan over the same representation with other (J, K, S)."""
