@@ -821,6 +821,45 @@ def run_shared(args, K, torch, peak):
     }
 
 
+def run_profile_case(args):
+    """Small, bounded cases of single kernels for a profiler (ncu): a few GB on
+    the device at most, each kernel run --steps + 2 times (two warm-up
+    launches first), so a profiler can skip the warm-up launches and capture
+    one or two launches that end by themselves.
+      profile_pre4096  kerdock_preprocess, m = 256, n = 4096, bfloat16 (4.3 GB)
+      profile_q4096    kerdock_apply, m = 256, n = 4096, bfloat16, 512 queries,
+                       J = 1000, K = 2
+      profile_pre1024  kerdock_preprocess, m = n = 1024, float32 (2.15 GB)"""
+    import torch
+    from paper_2105_05879_gb300 import build as kbuild
+    from paper_2105_05879_gb300 import kerdock as K
+    torch.cuda.set_device(0)
+    kbuild.build()
+    K.load_library()
+    torch.manual_seed(0)
+    case = args.workload
+    if case == "profile_pre1024":
+        m = n = 1024
+        dtype = "f32"
+    else:
+        m, n, dtype = 256, 4096, "bf16"
+    A = (torch.randn(m, n, device="cuda") / n ** 0.5).contiguous()
+    plan = K.KerdockPlan(m, n, J=1000, K=2, S=32, dtype=dtype)
+    if case in ("profile_pre4096", "profile_pre1024"):
+        for _ in range(args.steps + 2):
+            plan.preprocess(A)
+    else:
+        plan.preprocess(A)
+        X = torch.randn(512, n, device="cuda")
+        X /= X.norm(dim=1, keepdim=True)
+        for _ in range(args.steps + 2):
+            plan.apply(X, 0.1, 3)
+    plan.sync()
+    torch.cuda.synchronize()
+    plan.close()
+    print(json.dumps({"profile_case": case, "launches": args.steps + 2}))
+
+
 def run_form(args):
     import torch
     from paper_2105_05879_gb300 import build as kbuild
@@ -1003,7 +1042,8 @@ def main():
                     help="skip the precision / batching / learned sub-objects of the main line")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1",
-                             "n1024_shared"])
+                             "n1024_shared", "profile_pre4096", "profile_q4096",
+                             "profile_pre1024"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_oracle_steps", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -1014,6 +1054,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("profile_"):
+        run_profile_case(args)
     elif args.workload != WORKLOAD:
         run_form(args)
     else:
