@@ -225,7 +225,7 @@ struct Shared {
   uint32_t digit, remaining;
   int abort_flag;       // a wait ran out: every role stops
   int final_abort;      // the finalizer warps' shared decision to stop
-  uint64_t filled;      // ring chunks the producer armed (for the drain after an abort)
+  uint32_t armed[kMaxChunks];  // 1 + global fill number of each chunk's last arming (0: never)
 };
 
 // Bounded wait that also gives up once another role has aborted.  After
@@ -339,7 +339,7 @@ __device__ __forceinline__ void init_barriers(Shared& sh, const LaunchCfg& c) {
     }
     sh.abort_flag = 0;
     sh.final_abort = 0;
-    sh.filled = 0;
+    for (int s = 0; s < kMaxChunks; ++s) sh.armed[s] = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -354,19 +354,14 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
   uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
   uint64_t filled = 0;             // chunks filled so far
   const int ci = lane / CR, r = lane % CR;
-  // every exit publishes how many chunks were armed (their copies may still
-  // be in flight after an abort; the CTA waits for them before it exits)
-  auto publish = [&]() {
-    if (lane == 0) sh.filled = filled;
-  };
+  // the CR lanes that fill one chunk
+  const uint32_t chunk_mask = ((CR == 32 ? 0u : (1u << CR)) - 1u) << (ci * CR);
   const int64_t nq = seq.size();
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
     const int xb = int(qs % kXBufs);
-    if (qs >= kXBufs && !warp_wait(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, cfg)) {
-      publish();
+    if (qs >= kXBufs && !warp_wait(&sh.x_empty[xb], uint32_t(qs / kXBufs - 1) & 1u, sh, cfg))
       return;
-    }
     float* xq = rg.xbuf + xb * cfg.xpad;
     for (int64_t p = lane; p < cfg.xpad; p += 32) xq[p] = p < qd.n ? qd.x[p] : 0.f;
     __syncwarp();
@@ -383,13 +378,11 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
       }
       if (ci < cnt && filled + uint64_t(ci) >= nchunk)
         ok = wait_phase(&sh.slot_empty[cs], ph ^ 1u, sh, cfg);
-      // copies are issued only when every chunk of the step is free, so an
-      // abort leaves no chunk partly armed
-      if (!__all_sync(0xffffffffu, ok)) {
-        publish();
-        return;
-      }
-      if (ci < cnt) {
+      // the lanes of one chunk arm it together or not at all, so an abort
+      // leaves no chunk partly armed; each armed chunk records its fill number
+      ok = __all_sync(chunk_mask, ok);
+      if (ci < cnt && ok) {
+        if (r == 0) sh.armed[cs] = uint32_t(filled + uint64_t(ci) + 1);
         const int64_t j = (c0 + ci) * CR + r;
         if (j < qd.N) {
           const uint64_t ell =
@@ -402,6 +395,7 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
           mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
         }
       }
+      if (__any_sync(0xffffffffu, !ok)) return;
       filled += uint64_t(cnt);
       cslot += uint32_t(cnt);
       if (cslot >= nchunk) {
@@ -410,7 +404,6 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
       }
     }
   }
-  publish();
 }
 
 // ---------------------------------------------------------------- coefficients
@@ -523,8 +516,9 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
   int batch_left = qd.J, batch = 0;
   for (int64_t j0 = 0; j0 < qd.N; j0 += CR) {
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
-    if (!warp_wait(&sh.row_full[cs], ph, sh, cfg)) return false;
-    if (!warp_wait(&sh.coef_full[cs], ph, sh, cfg)) return false;
+    bool ok = wait_phase(&sh.row_full[cs], ph, sh, cfg);
+    if (ok) ok = wait_phase(&sh.coef_full[cs], ph, sh, cfg);
+    if (!__all_sync(0xffffffffu, ok)) return false;
 #pragma unroll
     for (int s2 = 0; s2 < 4; ++s2) {
       if (s2 >= cnt) break;
@@ -832,10 +826,10 @@ __device__ __forceinline__ void run_roles(const Seq& seq, const LaunchCfg& cfg, 
   // memory is released.
   __syncthreads();
   if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&sh.abort_flag)) {
-    const uint64_t filled = sh.filled, nchunk = uint64_t(cfg.nchunk);
-    for (uint64_t c = 0; c < nchunk && c < filled; ++c) {
-      const uint64_t last = filled - 1 - (filled - 1 - c) % nchunk;  // last fill of chunk c
-      const uint32_t parity = uint32_t(last / nchunk) & 1u;
+    for (int c = 0; c < cfg.nchunk; ++c) {
+      const uint32_t f = sh.armed[c];
+      if (f == 0) continue;
+      const uint32_t parity = ((f - 1u) / uint32_t(cfg.nchunk)) & 1u;  // phase of its last arming
       for (uint32_t it = 0; it < kDefaultPollLimit; ++it)
         if (mbar_try_wait(&sh.row_full[c], parity)) break;
     }
