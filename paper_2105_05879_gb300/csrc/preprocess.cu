@@ -30,6 +30,8 @@
 #include <cooperative_groups.h>
 #include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
 
+#include <cuda_fp16.h>
+
 #include "kerdock_internal.cuh"
 
 namespace kd {
@@ -1131,6 +1133,360 @@ int launch_d1024(const Plan& p) {
   return KERDOCK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// d = 1024, bfloat16 representation on the tensor cores.  Write
+// p = 256 p2 + 16 p1 + p0 and w = 256 w2 + 16 w1 + w0, so that
+// W_1024 = W_4 (over p2) (x) W_16 (over p1) (x) W_16 (over p0).  A CTA owns a
+// 64-row tile of A, kept in tensor memory as float16 (each row scaled by a
+// power of two into [1/2, 1)) across all the bases it processes.  Per basis
+// each warp takes 8 rows: step (i) of Lemma 6 is an XOR of the float16 sign
+// bits, the 4-point stage over p2 runs on the input in packed float16 and goes
+// back to tensor memory.  Then, for each output quarter w2, two mma.sync
+// stages (float16 operands, float32 accumulation) over p0 and p1 -- the first
+// stage's accumulators are exactly the second stage's B fragments -- give the
+// quarter's 256 outputs of a row; the row's power-of-two scale is undone in
+// the second stage's A operand.  Eight rows are packed per 16-byte store into
+// a staging buffer [w][64 rows] (128-byte swizzle), and one TMA store writes
+// 64 rows x 256 w, i.e. 128-byte runs of every output row R[b][w][.].
+// Float16 keeps 11 significant bits, so the stages add only a few 2^-11
+// ||a_i|| to the final bfloat16 rounding (2^-9 |R|).
+// ---------------------------------------------------------------------------
+namespace k10tc {
+
+constexpr int D = 1024, TI = 64, WARPS = 8, THREADS = WARPS * 32, RPW = TI / WARPS;
+constexpr int QW = 256;                         // outputs w per quarter
+constexpr int FBUF = QW * TI * 2;               // 32 KiB staging buffer
+constexpr int NBUF = 4;                         // staging ring
+constexpr int MASKW = 512;                      // float16 sign masks per basis (16 per lane)
+constexpr size_t OFF_MASK = size_t(NBUF) * FBUF;
+constexpr size_t OFF_FRAG = OFF_MASK + 2 * MASKW * 4;                    // [warp][row][lane] uint4
+constexpr size_t OFF_ER = OFF_FRAG + size_t(WARPS) * RPW * 32 * 16;     // [warp][row] int
+constexpr size_t OFF_SLOT = OFF_ER + size_t(WARPS) * RPW * 4;
+constexpr size_t SMEM = OFF_SLOT + 16 + 1024;  // + slack for 1024-byte alignment
+constexpr uint32_t TMEM_COLS = 512;             // per warp: 128 columns of x, 128 of y
+
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t pack_b2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t hadd2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t hsub2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                        uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(src)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    preprocess_d1024_tc_kernel(const PreArgs a, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int64_t B = D / 2 + 1;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  uint32_t* masks = reinterpret_cast<uint32_t*>(smem + OFF_MASK);  // [2][4][32 lanes][4]
+  uint4* frag = reinterpret_cast<uint4*>(smem + OFF_FRAG);         // [warp][row][lane]
+  int* erem = reinterpret_cast<int*>(smem + OFF_ER);                // [warp][row]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_SLOT);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  // warp w reaches lanes 32 (w mod 4) ..; warps 4 .. 7 use columns 256 ..
+  const uint32_t tx = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t((warp >> 2) * 256);
+  const uint32_t ty = tx + 128;
+
+  // A fragment of W_16 in float16 (rows g, g + 8; columns 2q, 2q + 1, 2q + 8, 2q + 9)
+  uint32_t w16[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int r = g + 8 * (e & 1), c = 2 * q + 8 * (e >> 1);
+    const uint32_t lo = (__popc(r & c) & 1) ? 0xBC00u : 0x3C00u;
+    const uint32_t hi = (__popc(r & (c + 1)) & 1) ? 0xBC00u : 0x3C00u;
+    w16[e] = lo | (hi << 16);
+  }
+
+  // Float16 sign masks of basis b in the lanes' fragment order: mask word
+  // (lane, reg) flips the elements p and p + 1 of B-fragment register reg =
+  // 4 p2 + 2 nt + j, p = 256 p2 + 16 (g + 8 nt) + 2 q + 8 j.
+  auto build_masks = [&](int b, int mb) {
+    uint32_t* mk = masks + mb * MASKW;
+    for (int idx = tid; idx < MASKW; idx += THREADS) {
+      const int l = idx >> 4, reg = idx & 15;
+      const int p = 256 * (reg >> 2) + 16 * ((l >> 2) + 8 * ((reg >> 1) & 1)) + 2 * (l & 3) +
+                    8 * (reg & 1);
+      uint32_t m = 0;
+      if (b != D / 2) {
+        const uint32_t wd = __ldg(a.signs + int64_t(b) * a.sign_words + (p >> 5)) >> (p & 31);
+        m = ((wd & 1u) << 15) | ((wd & 2u) << 30);
+      }
+      mk[((reg >> 2) * 32 + l) * 4 + (reg & 3)] = m;
+    }
+  };
+
+  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  if (ir.beg < ir.end) build_masks(int(ir.beg % B), 0);
+  __syncthreads();
+  int mb = 0;
+  uint32_t kq = 0;  // quarters stored so far (staging ring position)
+  int64_t cur_tile = -1;
+  for (int64_t item = ir.beg; item < ir.end; ++item) {
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
+    const int64_t i0 = t * TI;
+    const bool ident = b == D / 2;
+
+    if (t != cur_tile) {  // this warp's 8 rows into tensor memory, scaled, as B fragments
+#pragma unroll 1
+      for (int r = 0; r < RPW; ++r) {
+        const int64_t row = i0 + warp * RPW + r;
+        const bool rv = row < a.m;
+        const float* arow = a.A + (rv ? row : 0) * a.lda;
+        float mx = 0.f;
+        if (rv)
+          for (int64_t p = lane; p < a.n; p += 32) mx = fmaxf(mx, fabsf(arow[p]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int ex = 0;
+        if (mx > 0.f) frexpf(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
+        const int e = -ex;              // mx 2^e in [1/2, 1)
+        const float sc = ldexpf(1.f, e);
+        uint32_t v[16];
+#pragma unroll
+        for (int idx = 0; idx < 16; ++idx) {
+          const int p = 256 * (idx >> 2) + 16 * (g + 8 * ((idx >> 1) & 1)) + 2 * q + 8 * (idx & 1);
+          const float x0 = (rv && p < a.n) ? arow[p] * sc : 0.f;
+          const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] * sc : 0.f;
+          v[idx] = pack_h2(x0, x1);
+        }
+        k10::tmem_st16(tx + uint32_t(16 * r), v);
+        // second-stage A operand: W_16 times 2^-e, exact in float16 for e in
+        // [-15, 24]; any remainder is undone in float32 on the outputs
+        const int ef = e < -15 ? -15 : (e > 24 ? 24 : e);
+        const uint32_t mag = ef <= 14 ? uint32_t(15 - ef) << 10 : 1u << (24 - ef);
+        frag[(warp * RPW + r) * 32 + lane] =
+            make_uint4((w16[0] & 0x80008000u) | mag | (mag << 16),
+                       (w16[1] & 0x80008000u) | mag | (mag << 16),
+                       (w16[2] & 0x80008000u) | mag | (mag << 16),
+                       (w16[3] & 0x80008000u) | mag | (mag << 16));
+        if (lane == 0) erem[warp * RPW + r] = e - ef;
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      __syncwarp();
+      cur_tile = t;
+    }
+
+    if (!ident) {
+      // sign flip and the 4-point stage over p2, row by row, back to tensor memory
+      uint32_t mk[16];
+      {
+        const uint4* m4 = reinterpret_cast<const uint4*>(masks + mb * MASKW);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint4 u = m4[c * 32 + lane];
+          mk[4 * c] = u.x;
+          mk[4 * c + 1] = u.y;
+          mk[4 * c + 2] = u.z;
+          mk[4 * c + 3] = u.w;
+        }
+      }
+#pragma unroll 1
+      for (int r = 0; r < RPW; ++r) {
+        uint32_t v[16];
+        k10::tmem_ld16(tx + uint32_t(16 * r), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile(""
+                     : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                       "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                       "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
+        uint32_t y[16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {  // register c of each p2 unit: (nt, j)
+          const uint32_t a0 = v[c] ^ mk[c], a1 = v[4 + c] ^ mk[4 + c];
+          const uint32_t a2 = v[8 + c] ^ mk[8 + c], a3 = v[12 + c] ^ mk[12 + c];
+          const uint32_t s01 = hadd2(a0, a1), d01 = hsub2(a0, a1);
+          const uint32_t s23 = hadd2(a2, a3), d23 = hsub2(a2, a3);
+          y[c] = hadd2(s01, s23);       // w2 = 0
+          y[4 + c] = hadd2(d01, d23);   // w2 = 1
+          y[8 + c] = hsub2(s01, s23);   // w2 = 2
+          y[12 + c] = hsub2(d01, d23);  // w2 = 3
+        }
+        k10::tmem_st16(ty + uint32_t(16 * r), y);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+
+#pragma unroll 1
+    for (int q2 = 0; q2 < 4; ++q2) {
+      unsigned char* Fb = smem + size_t(kq % NBUF) * FBUF;
+      if (!ident) {
+        uint32_t yv[RPW][4];
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) tmem_ld4(ty + uint32_t(16 * r + 4 * q2), yv[r]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int r = 0; r < RPW; ++r)
+          asm volatile("" : "+r"(yv[r][0]), "+r"(yv[r][1]), "+r"(yv[r][2]), "+r"(yv[r][3]));
+        uint32_t out[8][4];
+        float lo[8];
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+          float d1[2][4];
+          mma_f16(d1[0], w16, yv[r][0], yv[r][1]);  // [w0][p1 0..7]
+          mma_f16(d1[1], w16, yv[r][2], yv[r][3]);  // [w0][p1 8..15]
+          const uint4 f4 = frag[(warp * RPW + r) * 32 + lane];
+          const uint32_t fr[4] = {f4.x, f4.y, f4.z, f4.w};
+          float d2[2][4];
+          mma_f16(d2[0], fr, pack_h2(d1[0][0], d1[0][1]), pack_h2(d1[1][0], d1[1][1]));  // w0 0..7
+          mma_f16(d2[1], fr, pack_h2(d1[0][2], d1[0][3]), pack_h2(d1[1][2], d1[1][3]));  // w0 8..15
+          const int er = erem[warp * RPW + r];
+          if (er != 0) {
+            const float s2 = ldexpf(1.f, -er);
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) d2[m][e] *= s2;
+          }
+#pragma unroll
+          for (int pos = 0; pos < 8; ++pos) {
+            const float val = d2[pos >> 2][pos & 3];
+            if (r & 1)
+              out[pos][r >> 1] = pack_b2(lo[pos], val);
+            else
+              lo[pos] = val;
+          }
+        }
+        // position pos: w1 = g + 8 ((pos & 3) >> 1), w0 = 2q + 8 (pos >> 2) + (pos & 1);
+        // the warp's 8 rows are 16-byte chunk `warp` of the 128-byte row w
+#pragma unroll
+        for (int pos = 0; pos < 8; ++pos) {
+          const int w = 16 * (g + 8 * ((pos & 3) >> 1)) + 2 * q + 8 * (pos >> 2) + (pos & 1);
+          const uint32_t addr = smem_addr(Fb + w * (TI * 2) + ((warp ^ (w & 7)) << 4));
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(out[pos][0]),
+                       "r"(out[pos][1]), "r"(out[pos][2]), "r"(out[pos][3])
+                       : "memory");
+        }
+      } else {
+        // identity basis: R[d/2][w][i] = sqrt(d) A[i][w] straight from A
+#pragma unroll 1
+        for (int c = tid; c < QW * 8; c += THREADS) {
+          const int w = c >> 3, ch = c & 7;
+          const int64_t col = int64_t(QW) * q2 + w;
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int64_t row = i0 + 8 * ch + k;
+            v[k] = (row < a.m && col < a.n) ? 32.f * a.A[row * a.lda + col] : 0.f;
+          }
+          const uint32_t addr = smem_addr(Fb + w * (TI * 2) + ((ch ^ (w & 7)) << 4));
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                       "r"(pack_b2(v[0], v[1])), "r"(pack_b2(v[2], v[3])),
+                       "r"(pack_b2(v[4], v[5])), "r"(pack_b2(v[6], v[7]))
+                       : "memory");
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the staging buffer of the next quarter was last stored NBUF - 1 quarters
+      // ago: at most NBUF - 2 later stores may still be reading
+      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
+      if (q2 == 3 && item + 1 < ir.end) build_masks(b + 1 == int(B) ? 0 : b + 1, mb ^ 1);
+      __syncthreads();
+      if (tid == 0) {
+        tma_store_2d(&tmap, smem_addr(Fb), int(i0), b * D + QW * q2);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+      ++kq;
+    }
+    mb ^= 1;
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+}  // namespace k10tc
+
+int launch_d1024_tc(const Plan& p) {
+  tc::EncodeTiledFn enc = tc::encoder();
+  if (enc == nullptr) return KERDOCK_ERR_UNSUPPORTED;
+  // R[b][w][i] (bfloat16) as rows (b, w) of ldr elements: box 64 rows x 256 w
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {cuuint64_t(p.ldr), cuuint64_t(p.B) * cuuint64_t(p.d)};
+  const cuuint64_t strides[1] = {cuuint64_t(p.ldr) * 2};
+  const cuuint32_t box[2] = {k10tc::TI, k10tc::QW};
+  const cuuint32_t es[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p.repr, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return KERDOCK_ERR_UNSUPPORTED;
+  auto kern = k10tc::preprocess_d1024_tc_kernel;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(k10tc::SMEM)));
+  PreArgs a;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.m = p.m;
+  a.n = p.n;
+  a.signs = p.signs();
+  a.sign_words = p.sign_words;
+  a.R = p.repr;
+  a.ldr = p.ldr;
+  a.status = p.status();
+  a.num_tiles = (p.ldr + k10tc::TI - 1) / k10tc::TI;
+  // one CTA per SM (its shared memory and all 512 tensor-memory columns);
+  // groups of up to 8 CTAs on adjacent tiles walk the bases in step
+  a.group = pick_group(a.num_tiles, 8);
+  int64_t ngrp = int64_t(p.num_sms) / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  if (ngrp < 1) ngrp = 1;
+  kern<<<unsigned(ngrp * a.group), k10tc::THREADS, k10tc::SMEM, p.stream>>>(a, map);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
 template <typename OutT>
 int launch_typed(const Plan& p) {
   switch (p.k) {
@@ -1138,7 +1494,9 @@ int launch_typed(const Plan& p) {
     case 4: return launch_small<4, OutT>(p);
     case 6: return launch_small<6, OutT>(p);
     case 8: return launch_small<8, OutT>(p);
-    case 10: return launch_d1024<OutT>(p);
+    case 10:
+      if (sizeof(OutT) == 2) return launch_d1024_tc(p);
+      return launch_d1024<OutT>(p);
     case 12:
       if (sizeof(OutT) == 2) return launch_d4096_tc(p);
       return launch_d4096<OutT>(p);

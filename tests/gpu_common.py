@@ -40,28 +40,34 @@ def representation_slice(plan, b):
     return R[b, :, :m].float().cpu().numpy().astype(np.float64)
 
 
-# Precision form at d = 4096: the three 16-point stages run on the tensor cores
-# with bfloat16 stage inputs, so besides the final rounding of each entry, the
-# rounding of A and of the two intermediate stages perturbs every entry of
-# R[b][:, i] by a few 2^-9 times its rms over w, which is ||a_i|| (W/sqrt(d) is
-# orthogonal).  Measured worst case over 8 bases x 4096 w x 256 rows: 0.016.
-TC_ABS = 2.0 ** -5
+# Tensor-core preprocessing of a bfloat16 representation.  Besides the final
+# rounding of each entry (2^-8 |R|), the rounding of the stage inputs perturbs
+# every entry of R[b][:, i] by a small multiple of its rms over w, which is
+# ||a_i|| (W / sqrt(d) is orthogonal):
+#   d = 4096: three 16-point stages with bfloat16 inputs (A and two
+#             intermediates, 8 significant bits); measured worst case 0.016
+#             over 8 bases x 4096 w x 256 rows;
+#   d = 1024: float16 stage inputs (11 significant bits, rows scaled by a power
+#             of two): the input, the 4-point stage's two additions and the
+#             first 16-point stage's output are rounded, each ~2^-12 ||a_i||
+#             in rms over w.
+TC_ABS = {12: 2.0 ** -5, 10: 2.0 ** -8}
 
 
-def repr_bound_bf16(R_ref, row_norms=None):
+def repr_bound_bf16(R_ref, row_norms=None, k=12):
     """Per-entry bound on |R_bf16 - R_exact|: 2^-8 |R| (final rounding), plus
-    TC_ABS * ||a_i|| for the tensor-core stages (row_norms given)."""
+    TC_ABS[k] * ||a_i|| for the tensor-core stages (row_norms given)."""
     bound = 2.0 ** -8 * np.abs(R_ref)
     if row_norms is not None:
-        bound = bound + TC_ABS * np.asarray(row_norms)[None, :]
+        bound = bound + TC_ABS[k] * np.asarray(row_norms)[None, :]
     return bound
 
 
-def oracle_mu_bound_bf16(rows, c, J, K, row_norms=None):
+def oracle_mu_bound_bf16(rows, c, J, K, row_norms=None, k=12):
     """Per-entry bound on |mu_bf16 - mu_exact| from the representation bound
     above: |d ybar_k| <= (1/J) sum_j |c_j| bound(R_j), and the median is
     1-Lipschitz in the sup norm, so max_k bounds mu."""
-    contrib = np.abs(c)[:, None] * repr_bound_bf16(rows, row_norms)
+    contrib = np.abs(c)[:, None] * repr_bound_bf16(rows, row_norms, k)
     per_batch = contrib.reshape(K, J, -1).sum(axis=1) / J
     return per_batch.max(axis=0)
 

@@ -57,7 +57,8 @@ def _oracle_check(A64, X64, res, wl, k, q, dtype, tc_stages):
         np.testing.assert_allclose(mu[q], mu_ref, rtol=0, atol=tol)
     else:
         norms = np.linalg.norm(A64, axis=1) if tc_stages else None
-        tol_vec = oracle_mu_bound_bf16(rows, c_ref, wl.J, wl.K, norms) + 1e-5 * np.abs(mu_ref).max()
+        tol_vec = (oracle_mu_bound_bf16(rows, c_ref, wl.J, wl.K, norms, k) +
+                   1e-5 * np.abs(mu_ref).max())
         assert (np.abs(mu[q] - mu_ref) <= tol_vec).all()
         tol = tol_vec.max()
     ref_idx, ref_val = oq.apply_one(A64, None, x, wl.eps, wl.seed_apply, q, wl.J, wl.K, wl.S, k,

@@ -121,5 +121,44 @@ def test_preprocess_d4096_parity(K, m, n, dtype):
             assert np.abs(Rg - Rref[t_]).max() <= 1e-4 * scale, b
         else:
             norms = np.linalg.norm(f32(A), axis=1)
-            assert (np.abs(Rg - Rref[t_]) <= repr_bound_bf16(Rref[t_], norms) + 1e-6 * scale).all(), b
+            assert (np.abs(Rg - Rref[t_]) <= repr_bound_bf16(Rref[t_], norms, 12) +
+                    1e-6 * scale).all(), b
+    plan.close()
+
+
+@pytest.mark.parametrize("m,n,scaled", [(1024, 1024, False), (100, 1000, True), (70, 513, False),
+                                        (200, 300, True)])
+def test_preprocess_d1024_bf16_tensor_cores(K, m, n, scaled):
+    # d = 1024 (k = 10), bfloat16: the tensor-core kernel (64-row tiles, float16
+    # stages with a power-of-two scale per row).  Ragged m (a partial last
+    # tile, padding rows m..ldr), n < d, and -- with `scaled` -- rows of very
+    # different magnitudes and an all-zero row.  Every basis for the smaller
+    # cases, a spread of bases at m = n = 1024.
+    torch = torch_cuda()
+    rng = np.random.default_rng(m * 13 + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    if scaled:
+        A[0] *= 1e-6
+        A[1] *= 3e4
+        A[2] = 0.0
+        A[3] *= 2.0 ** -30
+    plan = K.KerdockPlan(m, n, J=1, K=1, S=1, dtype="bf16")
+    assert plan.info["d"] == 1024
+    plan.preprocess(torch.from_numpy(A).cuda())
+    plan.sync()
+    ldr = plan.info["ldr"]
+    Rdev = plan.representation()
+    bases = [0, 1, 2, 77, 255, 256, 400, 511, 512] if m == 1024 else list(range(513))
+    Rref = okd.representation_lemma6(f32(A), 10, bases=bases)
+    norms = np.linalg.norm(f32(A), axis=1)
+    worst = 0.0
+    for t_, b in enumerate(bases):
+        Rg = Rdev[b].float().cpu().numpy().astype(np.float64)
+        assert not np.any(Rg[:, m:ldr]), "padding entries must be zero"
+        Rg = Rg[:, :m]
+        err = np.abs(Rg - Rref[t_])
+        assert (err <= repr_bound_bf16(Rref[t_], norms, 10)).all(), b
+        rel = err - 2.0 ** -8 * np.abs(Rref[t_])
+        worst = max(worst, float((rel / np.maximum(norms, 1e-300)[None, :]).max()))
+    print(f"d=1024 bf16 tensor cores m={m} n={n}: worst (err - 2^-8|R|)/||a_i|| = {worst:.3e}")
     plan.close()

@@ -6,8 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import (build_and_load, check_topS_valid, f32, okd, oq, oracle_mu_bound_bf16,
-                        torch_cuda)
+from gpu_common import (TC_ABS, build_and_load, check_topS_valid, f32, okd, oq,
+                        oracle_mu_bound_bf16, torch_cuda)
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -50,8 +50,9 @@ def check_query(A64, R, X64, plan, res, eps, seed, J, Kb, S, k, dtype="f32", laz
             tol = 1e-4 * max(np.abs(mu_ref).max(), 1e-30)
             np.testing.assert_allclose(mu[q], mu_ref, rtol=0, atol=tol)
         else:
-            norms = np.linalg.norm(A64, axis=1) if k == 12 else None  # tensor-core stages
-            tol_vec = oracle_mu_bound_bf16(rows, c_ref, J, Kb, norms) + 1e-5 * np.abs(mu_ref).max()
+            norms = np.linalg.norm(A64, axis=1) if k in TC_ABS else None  # tensor-core stages
+            tol_vec = (oracle_mu_bound_bf16(rows, c_ref, J, Kb, norms, k) +
+                       1e-5 * np.abs(mu_ref).max())
             assert (np.abs(mu[q] - mu_ref) <= tol_vec).all()
             tol = tol_vec.max()
         v_ref_all = A64 @ x
