@@ -518,10 +518,9 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
     bool ok = wait_phase(&sh.row_full[cs], ph, sh, cfg);
     if (ok) ok = wait_phase(&sh.coef_full[cs], ph, sh, cfg);
-    if (!__all_sync(0xffffffffu, ok)) return false;
 #pragma unroll
     for (int s2 = 0; s2 < 4; ++s2) {
-      if (s2 >= cnt) break;
+      if (s2 >= cnt || !ok) break;
       const float c = rg.coef_s[cs * CR + s2];
       const unsigned char* row = rg.ring + (size_t(cs) * CR + s2) * cfg.slot_bytes;
 #pragma unroll
@@ -533,8 +532,10 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
       }
       if (--batch_left == 0) {
         if (batch == 0 && qs >= kMBufs &&
-            !warp_wait(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg))
-          return false;
+            !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg)) {
+          ok = false;
+          break;
+        }
         float* mrow = means + int64_t(batch) * qd.ldr;
 #pragma unroll
         for (int u = 0; u < GPT; ++u) {
@@ -552,6 +553,9 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
         ++batch;
       }
     }
+    // the chunk's one warp-wide agreement (also where the warp reconverges
+    // before the slot is freed): every lane goes on, or every lane stops
+    if (!__all_sync(0xffffffffu, ok)) return false;
     __syncwarp();
     if (lane == 0) mbar_arrive(&sh.slot_empty[cs]);
     if (++cs == nchunk) {
