@@ -554,7 +554,7 @@ int launch_small(const Plan& p) {
 // ---------------------------------------------------------------------------
 // Precision form, d = 4096, bfloat16 representation: the three 16-point
 // stages of W_4096 = W_16 (x) W_16 (x) W_16 on the tensor cores
-// (mma.sync m16n8k16, bfloat16 operands, float32 accumulation).  Write
+// (mma.sync m16n8k16, float16 operands, float32 accumulation).  Write
 // p = 256 p2 + 16 p1 + p0 and w = 256 w2 + 16 w1 + w0.  For one row and one
 // p2, stage 1 multiplies W_16 by the 16 x 16 block [p0][p1] (two n-tiles of
 // 8 p1) and gives [w0][p1]; its accumulator fragments are exactly the B
@@ -563,11 +563,15 @@ int launch_small(const Plan& p) {
 // stage 3 reads 16 p2 x 16 w0 per (row, w1) back with ldmatrix.trans, multiplies
 // by W_16 and gives [w2][w0]; eight rows of one w1 are packed as row pairs
 // into F[w2][w0][row] (32-byte rows, 32-byte swizzle) and written with one
-// 4-D TMA store (16 rows x 16 w0 x 16 w2).  The CTA's 16-row tile of A, rounded to bfloat16 once, sits in
-// tensor memory (128 KiB), laid out so that each thread's words for one
-// (row, p2) are four consecutive columns of its own lane.  Each stage's input
-// is rounded to bfloat16 (three roundings beside the final one); the identity
-// basis uses 4 I in all three stages (x 64 = sqrt(d)).
+// 4-D TMA store (16 rows x 16 w0 x 16 w2).  The CTA's 16-row tile of A sits
+// in tensor memory (128 KiB) as float16, each row scaled by a power of two
+// 2^e_r that brings its largest entry into [1/2, 1), laid out so that each
+// thread's words for one (row, p2) are four consecutive columns of its own
+// lane; stage 3's A operand is W_16 2^-e_r (exact in float16), so the output
+// comes back at A's scale.  Float16 keeps 11 significant bits: the input and
+// the two intermediate stages each add ~2^-12 ||a_i|| (rms over w) beside the
+// final bfloat16 rounding; the identity basis uses 4 I in all three stages
+// (x 64 = sqrt(d)).
 // ---------------------------------------------------------------------------
 namespace tc {
 
@@ -577,17 +581,30 @@ constexpr int E_ROW = 16 * E_W1;             // bytes per row
 constexpr int E_BYTES = TI * E_ROW;          // 135168
 constexpr int F_WARP = 16 * 16 * TI * 2;     // [w2][w0][row] bfloat16 per warp: 8 KiB
 constexpr int MASK_WORDS = 16 * 32 * 4;      // [p2][lane][4]
-constexpr size_t SMEM = size_t(E_BYTES) + size_t(WARPS) * F_WARP + MASK_WORDS * 4 + 16;
+constexpr size_t OFF_MASK = size_t(E_BYTES) + size_t(WARPS) * F_WARP;
+constexpr size_t OFF_SLOT = OFF_MASK + MASK_WORDS * 4;
+constexpr size_t OFF_RFRAG = OFF_SLOT + 16;                 // [2][TI rows][32 lanes] uint4
+constexpr size_t OFF_RMAX = OFF_RFRAG + 2 * size_t(TI) * 32 * 16;
+constexpr size_t OFF_REM = OFF_RMAX + TI * 4;
+constexpr size_t SMEM = OFF_REM + TI * 4;
 constexpr uint32_t TMEM_COLS = 256;          // 4 rows x 16 p2 x 4 words per lane
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// float16 bits of 2^k, exact for k in [-24, 15]
+__device__ __forceinline__ uint32_t f16_pow2(int k) {
+  return k >= -14 ? uint32_t(k + 15) << 10 : 1u << (k + 24);
+}
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
                                          uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%10,%10,%10,%10};"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
@@ -642,8 +659,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* E = smem;
   unsigned char* Fw = smem + E_BYTES + (threadIdx.x >> 5) * F_WARP;  // this warp's F
-  uint32_t* maskt = reinterpret_cast<uint32_t*>(smem + E_BYTES + WARPS * F_WARP);
-  uint32_t* tmem_slot = maskt + MASK_WORDS;
+  uint32_t* maskt = reinterpret_cast<uint32_t*>(smem + OFF_MASK);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_SLOT);
+  uint4* rfrag = reinterpret_cast<uint4*>(smem + OFF_RFRAG);     // [W16 | 4 I][row][lane]
+  uint32_t* rmax = reinterpret_cast<uint32_t*>(smem + OFF_RMAX);  // row maxima (float bits)
+  int* rrem = reinterpret_cast<int*>(smem + OFF_REM);             // exponent left for float32
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, q = lane & 3;
   const int quarter = warp & 3, phalf = warp >> 2;  // lane quarter of tensor memory; p2 half
@@ -672,8 +692,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int e = 0; e < 4; ++e) {
       const float w0 = (__popc(rr[e] & cc[e]) & 1) ? -1.f : 1.f;
       const float w1 = (__popc(rr[e] & (cc[e] + 1)) & 1) ? -1.f : 1.f;
-      aw[e] = pack_bf16x2(w0, w1);
-      ai[e] = pack_bf16x2(rr[e] == cc[e] ? 4.f : 0.f, rr[e] == cc[e] + 1 ? 4.f : 0.f);
+      aw[e] = pack_f16x2(w0, w1);
+      ai[e] = pack_f16x2(rr[e] == cc[e] ? 4.f : 0.f, rr[e] == cc[e] + 1 ? 4.f : 0.f);
     }
   }
 
@@ -705,22 +725,64 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool ident = b == D / 2;
 
     if (t != cur_tile) {  // this warp's share of the tile into its lanes of tensor memory
+      // Rows are scaled by powers of two 2^e_r (largest entry in [1/2, 1)), so
+      // that the float16 stage inputs keep 11 significant bits whatever the
+      // magnitude of A; stage 3 multiplies by 2^-e_r again.  Row r is loaded
+      // by the two warps of lane quarter r mod 4, each for half of p.
+      __syncthreads();  // every warp is done with the previous tile's row data
+      if (tid < TI) rmax[tid] = 0u;
+      __syncthreads();
 #pragma unroll 1
       for (int rl = 0; rl < 4; ++rl) {
         const int64_t row = i0 + quarter + 4 * rl;
+        float mx = 0.f;
+        if (row < a.m) {
+          const float* arow = a.A + row * a.lda;
+          for (int64_t p = 2048 * phalf + lane; p < 2048 * phalf + 2048 && p < a.n; p += 32)
+            mx = fmaxf(mx, fabsf(arow[p]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(&rmax[quarter + 4 * rl], __float_as_uint(mx));
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int rl = 0; rl < 4; ++rl) {
+        const int r = quarter + 4 * rl;
+        const int64_t row = i0 + r;
         const bool rv = row < a.m;
         const float* arow = a.A + (rv ? row : 0) * a.lda;
+        int ex = 0;
+        const float mx = __uint_as_float(rmax[r]);
+        if (mx > 0.f) frexpf(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
+        const int e = -ex;
+        const float sc = ldexpf(1.f, e);
 #pragma unroll 1
         for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
           uint32_t v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int p = p2 * 256 + (g + 8 * (j >> 1)) * 16 + 2 * q + 8 * (j & 1);
-            const float x0 = (rv && p < a.n) ? arow[p] : 0.f;
-            const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] : 0.f;
-            v[j] = pack_bf16x2(x0, x1);
+            const float x0 = (rv && p < a.n) ? arow[p] * sc : 0.f;
+            const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] * sc : 0.f;
+            v[j] = pack_f16x2(x0, x1);
           }
           tmem_st4(tlane + tcol(rl, p2), v);
+        }
+        if (phalf == 0) {
+          // stage-3 A operands W_16 2^-e and 4 I 2^-e, exact in float16 for
+          // e in [-13, 24]; the rest of the exponent is undone in float32
+          const int ef = e < -13 ? -13 : (e > 24 ? 24 : e);
+          const uint32_t mw = f16_pow2(-ef), mi = f16_pow2(2 - ef);
+          uint32_t fw[4], fi[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            fw[k] = (aw[k] & 0x80008000u) | mw | (mw << 16);
+            fi[k] = ((ai[k] & 0x7fffu) ? mi : 0u) | ((ai[k] & 0x7fff0000u) ? (mi << 16) : 0u);
+          }
+          rfrag[r * 32 + lane] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
+          rfrag[(TI + r) * 32 + lane] = make_uint4(fi[0], fi[1], fi[2], fi[3]);
+          if (lane == 0) rrem[r] = e - ef;
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -776,14 +838,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         float d1a[4], d1b[4], d2a[4], d2b[4];
         mma16816(d1a, A16, x[h][0], x[h][1]);  // [w0][p1 0..7]
         mma16816(d1b, A16, x[h][2], x[h][3]);  // [w0][p1 8..15]
-        mma16816(d2a, A16, pack_bf16x2(d1a[0], d1a[1]), pack_bf16x2(d1b[0], d1b[1]));  // w0 0..7
-        mma16816(d2b, A16, pack_bf16x2(d1a[2], d1a[3]), pack_bf16x2(d1b[2], d1b[3]));  // w0 8..15
+        mma16816(d2a, A16, pack_f16x2(d1a[0], d1a[1]), pack_f16x2(d1b[0], d1b[1]));  // w0 0..7
+        mma16816(d2b, A16, pack_f16x2(d1a[2], d1a[3]), pack_f16x2(d1b[2], d1b[3]));  // w0 8..15
         // [w1][w0] -> E[r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
         const int mi = lane >> 3, mj = lane & 7;
         const int w1 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
         const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
-        stmatrix_x4(addr, pack_bf16x2(d2a[0], d2a[1]), pack_bf16x2(d2a[2], d2a[3]),
-                    pack_bf16x2(d2b[0], d2b[1]), pack_bf16x2(d2b[2], d2b[3]));
+        stmatrix_x4(addr, pack_f16x2(d2a[0], d2a[1]), pack_f16x2(d2a[2], d2a[3]),
+                    pack_f16x2(d2b[0], d2b[1]), pack_f16x2(d2b[2], d2b[3]));
       }
       tmem_wait_ld(xa, xb);
     }
@@ -808,13 +870,21 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int p2 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
             uint32_t m[4];
             ldmatrix_x4_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
+            const uint4 f4 = rfrag[((ident ? TI : 0) + r) * 32 + lane];
+            const uint32_t A3[4] = {f4.x, f4.y, f4.z, f4.w};  // this row's 2^-e_r
             float d3a[4], d3b[4];
-            mma16816(d3a, A16, m[0], m[1]);  // [w2][w0 0..7]
-            mma16816(d3b, A16, m[2], m[3]);  // [w2][w0 8..15]
+            mma16816(d3a, A3, m[0], m[1]);  // [w2][w0 0..7]
+            mma16816(d3b, A3, m[2], m[3]);  // [w2][w0 8..15]
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               v[h][e] = d3a[e];
               v[h][4 + e] = d3b[e];
+            }
+            const int er = rrem[r];
+            if (er != 0) {  // rows beyond float16's exponent range (rare)
+              const float s3 = ldexpf(1.f, -er);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[h][e] *= s3;
             }
           }
 #pragma unroll
@@ -1327,28 +1397,36 @@ __global__ void __launch_bounds__(THREADS, 1)
           mk[4 * c + 3] = u.w;
         }
       }
+      // four rows per tensor-memory round trip: their loads are in flight together
 #pragma unroll 1
-      for (int r = 0; r < RPW; ++r) {
-        uint32_t v[16];
-        k10::tmem_ld16(tx + uint32_t(16 * r), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        asm volatile(""
-                     : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
-                       "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
-                       "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]));
-        uint32_t y[16];
+      for (int r0 = 0; r0 < RPW; r0 += 4) {
+        uint32_t v[4][16];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {  // register c of each p2 unit: (nt, j)
-          const uint32_t a0 = v[c] ^ mk[c], a1 = v[4 + c] ^ mk[4 + c];
-          const uint32_t a2 = v[8 + c] ^ mk[8 + c], a3 = v[12 + c] ^ mk[12 + c];
-          const uint32_t s01 = hadd2(a0, a1), d01 = hsub2(a0, a1);
-          const uint32_t s23 = hadd2(a2, a3), d23 = hsub2(a2, a3);
-          y[c] = hadd2(s01, s23);       // w2 = 0
-          y[4 + c] = hadd2(d01, d23);   // w2 = 1
-          y[8 + c] = hsub2(s01, s23);   // w2 = 2
-          y[12 + c] = hsub2(d01, d23);  // w2 = 3
+        for (int rr = 0; rr < 4; ++rr) k10::tmem_ld16(tx + uint32_t(16 * (r0 + rr)), v[rr]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+          asm volatile(""
+                       : "+r"(v[rr][0]), "+r"(v[rr][1]), "+r"(v[rr][2]), "+r"(v[rr][3]),
+                         "+r"(v[rr][4]), "+r"(v[rr][5]), "+r"(v[rr][6]), "+r"(v[rr][7]),
+                         "+r"(v[rr][8]), "+r"(v[rr][9]), "+r"(v[rr][10]), "+r"(v[rr][11]),
+                         "+r"(v[rr][12]), "+r"(v[rr][13]), "+r"(v[rr][14]), "+r"(v[rr][15]));
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          uint32_t y[16];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {  // register c of each p2 unit: (nt, j)
+            const uint32_t a0 = v[rr][c] ^ mk[c], a1 = v[rr][4 + c] ^ mk[4 + c];
+            const uint32_t a2 = v[rr][8 + c] ^ mk[8 + c], a3 = v[rr][12 + c] ^ mk[12 + c];
+            const uint32_t s01 = hadd2(a0, a1), d01 = hsub2(a0, a1);
+            const uint32_t s23 = hadd2(a2, a3), d23 = hsub2(a2, a3);
+            y[c] = hadd2(s01, s23);       // w2 = 0
+            y[4 + c] = hadd2(d01, d23);   // w2 = 1
+            y[8 + c] = hsub2(s01, s23);   // w2 = 2
+            y[12 + c] = hsub2(d01, d23);  // w2 = 3
+          }
+          k10::tmem_st16(ty + uint32_t(16 * (r0 + rr)), y);
         }
-        k10::tmem_st16(ty + uint32_t(16 * r), y);
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }

@@ -40,18 +40,14 @@ def representation_slice(plan, b):
     return R[b, :, :m].float().cpu().numpy().astype(np.float64)
 
 
-# Tensor-core preprocessing of a bfloat16 representation.  Besides the final
-# rounding of each entry (2^-8 |R|), the rounding of the stage inputs perturbs
-# every entry of R[b][:, i] by a small multiple of its rms over w, which is
-# ||a_i|| (W / sqrt(d) is orthogonal):
-#   d = 4096: three 16-point stages with bfloat16 inputs (A and two
-#             intermediates, 8 significant bits); measured worst case 0.016
-#             over 8 bases x 4096 w x 256 rows;
-#   d = 1024: float16 stage inputs (11 significant bits, rows scaled by a power
-#             of two): the input, the 4-point stage's two additions and the
-#             first 16-point stage's output are rounded, each ~2^-12 ||a_i||
-#             in rms over w.
-TC_ABS = {12: 2.0 ** -5, 10: 2.0 ** -8}
+# Tensor-core preprocessing of a bfloat16 representation (d = 1024 and 4096).
+# Besides the final rounding of each entry (2^-8 |R|), the rounding of the
+# float16 stage inputs (11 significant bits, rows scaled by powers of two)
+# perturbs every entry of R[b][:, i] by a small multiple of its rms over w,
+# which is ||a_i|| (W / sqrt(d) is orthogonal): the input, and at d = 1024 the
+# 4-point stage's two additions and the first 16-point stage's output, at
+# d = 4096 the two intermediate stages, each ~2^-12 ||a_i|| in rms.
+TC_ABS = {12: 2.0 ** -8, 10: 2.0 ** -8}
 
 
 def repr_bound_bf16(R_ref, row_norms=None, k=12):
