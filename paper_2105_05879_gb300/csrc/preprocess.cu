@@ -586,7 +586,8 @@ constexpr size_t OFF_SLOT = OFF_MASK + MASK_WORDS * 4;
 constexpr size_t OFF_RFRAG = OFF_SLOT + 16;                 // [2][TI rows][32 lanes] uint4
 constexpr size_t OFF_RMAX = OFF_RFRAG + 2 * size_t(TI) * 32 * 16;
 constexpr size_t OFF_REM = OFF_RMAX + TI * 4;
-constexpr size_t SMEM = OFF_REM + TI * 4;
+constexpr size_t OFF_REXP = OFF_REM + TI * 4;
+constexpr size_t SMEM = OFF_REXP + TI * 4;
 constexpr uint32_t TMEM_COLS = 256;          // 4 rows x 16 p2 x 4 words per lane
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -664,6 +665,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint4* rfrag = reinterpret_cast<uint4*>(smem + OFF_RFRAG);     // [W16 | 4 I][row][lane]
   uint32_t* rmax = reinterpret_cast<uint32_t*>(smem + OFF_RMAX);  // row maxima (float bits)
   int* rrem = reinterpret_cast<int*>(smem + OFF_REM);             // exponent left for float32
+  int* rexp = reinterpret_cast<int*>(smem + OFF_REXP);            // row scale exponents e_r
+  uint32_t smask = 0u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, q = lane & 3;
   const int quarter = warp & 3, phalf = warp >> 2;  // lane quarter of tensor memory; p2 half
@@ -725,10 +728,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool ident = b == D / 2;
 
     if (t != cur_tile) {  // this warp's share of the tile into its lanes of tensor memory
-      // Rows are scaled by powers of two 2^e_r (largest entry in [1/2, 1)), so
-      // that the float16 stage inputs keep 11 significant bits whatever the
-      // magnitude of A; stage 3 multiplies by 2^-e_r again.  Row r is loaded
-      // by the two warps of lane quarter r mod 4, each for half of p.
+      // A row whose largest entry lies in [2^-8, 2^6) is used as it is: its
+      // stage values stay below 2^14 and, relative to ||a_i||, keep float16's
+      // 11 significant bits (entries below 2^-14 are subnormal but then below
+      // 2^-6 of the row's largest, with absolute error <= 2^-25).  Any other
+      // row is scaled by 2^e_r (largest entry into [1/2, 1)) and stage 3
+      // multiplies by 2^-e_r again.  Row r is loaded by the two warps of lane
+      // quarter r mod 4, each for half of p.
       __syncthreads();  // every warp is done with the previous tile's row data
       if (tid < TI) rmax[tid] = 0u;
       __syncthreads();
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int ex = 0;
         const float mx = __uint_as_float(rmax[r]);
         if (mx > 0.f) frexpf(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
-        const int e = -ex;
+        const int e = (mx > 0.f && (ex < -7 || ex > 6)) ? -ex : 0;
         const float sc = ldexpf(1.f, e);
 #pragma unroll 1
         for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
@@ -782,10 +788,17 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           rfrag[r * 32 + lane] = make_uint4(fw[0], fw[1], fw[2], fw[3]);
           rfrag[(TI + r) * 32 + lane] = make_uint4(fi[0], fi[1], fi[2], fi[3]);
-          if (lane == 0) rrem[r] = e - ef;
+          if (lane == 0) {
+            rrem[r] = e - ef;
+            rexp[r] = e;
+          }
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      __syncthreads();
+      smask = 0u;  // rows of this tile that stage 3 must scale back
+#pragma unroll
+      for (int r = 0; r < TI; ++r) smask |= rexp[r] != 0 ? (1u << r) : 0u;
       cur_tile = t;
     }
 
@@ -870,8 +883,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int p2 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
             uint32_t m[4];
             ldmatrix_x4_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
-            const uint4 f4 = rfrag[((ident ? TI : 0) + r) * 32 + lane];
-            const uint32_t A3[4] = {f4.x, f4.y, f4.z, f4.w};  // this row's 2^-e_r
+            uint32_t A3[4] = {A16[0], A16[1], A16[2], A16[3]};
+            const bool scaled = (smask >> r) & 1u;
+            if (scaled) {  // this row's W_16 2^-e_r (or 4 I 2^-e_r)
+              const uint4 f4 = rfrag[((ident ? TI : 0) + r) * 32 + lane];
+              A3[0] = f4.x;
+              A3[1] = f4.y;
+              A3[2] = f4.z;
+              A3[3] = f4.w;
+            }
             float d3a[4], d3b[4];
             mma16816(d3a, A3, m[0], m[1]);  // [w2][w0 0..7]
             mma16816(d3b, A3, m[2], m[3]);  // [w2][w0 8..15]
@@ -880,9 +900,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               v[h][e] = d3a[e];
               v[h][4 + e] = d3b[e];
             }
-            const int er = rrem[r];
-            if (er != 0) {  // rows beyond float16's exponent range (rare)
-              const float s3 = ldexpf(1.f, -er);
+            if (scaled && rrem[r] != 0) {  // beyond float16's exponent range
+              const float s3 = ldexpf(1.f, -rrem[r]);
 #pragma unroll
               for (int e = 0; e < 8; ++e) v[h][e] *= s3;
             }
@@ -1225,6 +1244,7 @@ namespace k10tc {
 
 constexpr int D = 1024, TI = 64, WARPS = 8, THREADS = WARPS * 32, RPW = TI / WARPS;
 constexpr int QW = 256;                         // outputs w per quarter
+static_assert(THREADS == QW, "the identity basis gives each thread one w of a quarter");
 constexpr int FBUF = QW * TI * 2;               // 32 KiB staging buffer
 constexpr int NBUF = 4;                         // staging ring
 constexpr int MASKW = 512;                      // float16 sign masks per basis (16 per lane)
@@ -1334,7 +1354,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (ir.beg < ir.end) build_masks(int(ir.beg % B), 0);
   __syncthreads();
   int mb = 0;
-  uint32_t kq = 0;  // quarters stored so far (staging ring position)
+  uint32_t kq = 0;      // quarters stored so far (staging ring position)
+  uint32_t wmask = 0u;  // this warp's rows that carry a power-of-two scale
   int64_t cur_tile = -1;
   for (int64_t item = ir.beg; item < ir.end; ++item) {
     const int64_t tg = item / B;
@@ -1344,6 +1365,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool ident = b == D / 2;
 
     if (t != cur_tile) {  // this warp's 8 rows into tensor memory, scaled, as B fragments
+      wmask = 0u;
 #pragma unroll 1
       for (int r = 0; r < RPW; ++r) {
         const int64_t row = i0 + warp * RPW + r;
@@ -1354,10 +1376,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int64_t p = lane; p < a.n; p += 32) mx = fmaxf(mx, fabsf(arow[p]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        // rows whose largest entry lies in [2^-8, 2^6) are used as they are
+        // (stage values below 2^14, 11 significant bits relative to ||a_i||);
+        // others are scaled by 2^e (largest entry into [1/2, 1))
         int ex = 0;
         if (mx > 0.f) frexpf(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
-        const int e = -ex;              // mx 2^e in [1/2, 1)
+        const int e = (mx > 0.f && (ex < -7 || ex > 6)) ? -ex : 0;
         const float sc = ldexpf(1.f, e);
+        if (e != 0) wmask |= 1u << r;
         uint32_t v[16];
 #pragma unroll
         for (int idx = 0; idx < 16; ++idx) {
@@ -1431,13 +1457,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
 
-#pragma unroll 1
+    // each quarter's tensor-memory loads are issued during the previous
+    // quarter (ping-pong registers), so their latency hides behind its stores
+    uint32_t yq[2][RPW][4];
+    if (!ident) {
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) tmem_ld4(ty + uint32_t(16 * r), yq[0][r]);
+    }
+#pragma unroll
     for (int q2 = 0; q2 < 4; ++q2) {
       unsigned char* Fb = smem + size_t(kq % NBUF) * FBUF;
       if (!ident) {
-        uint32_t yv[RPW][4];
-#pragma unroll
-        for (int r = 0; r < RPW; ++r) tmem_ld4(ty + uint32_t(16 * r + 4 * q2), yv[r]);
+        uint32_t (&yv)[RPW][4] = yq[q2 & 1];
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int r = 0; r < RPW; ++r)
@@ -1449,12 +1480,18 @@ __global__ void __launch_bounds__(THREADS, 1)
           float d1[2][4];
           mma_f16(d1[0], w16, yv[r][0], yv[r][1]);  // [w0][p1 0..7]
           mma_f16(d1[1], w16, yv[r][2], yv[r][3]);  // [w0][p1 8..15]
-          const uint4 f4 = frag[(warp * RPW + r) * 32 + lane];
-          const uint32_t fr[4] = {f4.x, f4.y, f4.z, f4.w};
+          uint32_t fr[4] = {w16[0], w16[1], w16[2], w16[3]};
+          if ((wmask >> r) & 1u) {  // this row's W_16 2^-e
+            const uint4 f4 = frag[(warp * RPW + r) * 32 + lane];
+            fr[0] = f4.x;
+            fr[1] = f4.y;
+            fr[2] = f4.z;
+            fr[3] = f4.w;
+          }
           float d2[2][4];
           mma_f16(d2[0], fr, pack_h2(d1[0][0], d1[0][1]), pack_h2(d1[1][0], d1[1][1]));  // w0 0..7
           mma_f16(d2[1], fr, pack_h2(d1[0][2], d1[0][3]), pack_h2(d1[1][2], d1[1][3]));  // w0 8..15
-          const int er = erem[warp * RPW + r];
+          const int er = ((wmask >> r) & 1u) ? erem[warp * RPW + r] : 0;
           if (er != 0) {
             const float s2 = ldexpf(1.f, -er);
 #pragma unroll
@@ -1471,6 +1508,11 @@ __global__ void __launch_bounds__(THREADS, 1)
               lo[pos] = val;
           }
         }
+        if (q2 < 3) {
+#pragma unroll
+          for (int r = 0; r < RPW; ++r)
+            tmem_ld4(ty + uint32_t(16 * r + 4 * (q2 + 1)), yq[(q2 + 1) & 1][r]);
+        }
         // position pos: w1 = g + 8 ((pos & 3) >> 1), w0 = 2q + 8 (pos >> 2) + (pos & 1);
         // the warp's 8 rows are 16-byte chunk `warp` of the 128-byte row w
 #pragma unroll
@@ -1482,11 +1524,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                        : "memory");
         }
       } else {
-        // identity basis: R[d/2][w][i] = sqrt(d) A[i][w] straight from A
+        // identity basis: R[d/2][w][i] = sqrt(d) A[i][w] straight from A; thread
+        // w of the quarter reads column w of the tile's rows (a warp reads 128
+        // contiguous bytes of a row per load) and packs 8 rows per store
+        const int w = tid;  // THREADS == QW
+        const int64_t col = int64_t(QW) * q2 + w;
 #pragma unroll 1
-        for (int c = tid; c < QW * 8; c += THREADS) {
-          const int w = c >> 3, ch = c & 7;
-          const int64_t col = int64_t(QW) * q2 + w;
+        for (int ch = 0; ch < TI / 8; ++ch) {
           float v[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
