@@ -1252,7 +1252,8 @@ constexpr size_t OFF_MASK = size_t(NBUF) * FBUF;
 constexpr size_t OFF_FRAG = OFF_MASK + 2 * MASKW * 4;                    // [warp][row][lane] uint4
 constexpr size_t OFF_ER = OFF_FRAG + size_t(WARPS) * RPW * 32 * 16;     // [warp][row] int
 constexpr size_t OFF_SLOT = OFF_ER + size_t(WARPS) * RPW * 4;
-constexpr size_t SMEM = OFF_SLOT + 16 + 1024;  // + slack for 1024-byte alignment
+constexpr size_t OFF_SCR = OFF_SLOT + 16;                               // [warp][512] half2 words
+constexpr size_t SMEM = OFF_SCR + size_t(WARPS) * 512 * 4 + 1024;  // + slack for 1024-byte alignment
 constexpr uint32_t TMEM_COLS = 512;             // per warp: 128 columns of x, 128 of y
 
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
@@ -1366,14 +1367,37 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (t != cur_tile) {  // this warp's 8 rows into tensor memory, scaled, as B fragments
       wmask = 0u;
+      uint32_t* scr = reinterpret_cast<uint32_t*>(smem + OFF_SCR) + warp * 512;
 #pragma unroll 1
       for (int r = 0; r < RPW; ++r) {
         const int64_t row = i0 + warp * RPW + r;
         const bool rv = row < a.m;
         const float* arow = a.A + (rv ? row : 0) * a.lda;
+        // lane holds p = 4 (lane + 32 c) + e, c < 8, e < 4: coalesced loads, all
+        // in flight together; 16-byte loads when the row is a whole aligned d
+        float x[32];
+        const bool vec = rv && a.n == D && (reinterpret_cast<uintptr_t>(arow) & 15u) == 0;
+        if (vec) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(arow) + lane + 32 * c);
+            x[4 * c] = f.x;
+            x[4 * c + 1] = f.y;
+            x[4 * c + 2] = f.z;
+            x[4 * c + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int p = 4 * (lane + 32 * c) + e;
+              x[4 * c + e] = (rv && p < a.n) ? arow[p] : 0.f;
+            }
+        }
         float mx = 0.f;
-        if (rv)
-          for (int64_t p = lane; p < a.n; p += 32) mx = fmaxf(mx, fabsf(arow[p]));
+#pragma unroll
+        for (int k = 0; k < 32; ++k) mx = fmaxf(mx, fabsf(x[k]));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         // rows whose largest entry lies in [2^-8, 2^6) are used as they are
@@ -1384,14 +1408,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int e = (mx > 0.f && (ex < -7 || ex > 6)) ? -ex : 0;
         const float sc = ldexpf(1.f, e);
         if (e != 0) wmask |= 1u << r;
+        // the row as float16 pairs in p order, then each lane's fragment words
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          scr[2 * (lane + 32 * c)] = pack_h2(x[4 * c] * sc, x[4 * c + 1] * sc);
+          scr[2 * (lane + 32 * c) + 1] = pack_h2(x[4 * c + 2] * sc, x[4 * c + 3] * sc);
+        }
+        __syncwarp();
         uint32_t v[16];
 #pragma unroll
-        for (int idx = 0; idx < 16; ++idx) {
-          const int p = 256 * (idx >> 2) + 16 * (g + 8 * ((idx >> 1) & 1)) + 2 * q + 8 * (idx & 1);
-          const float x0 = (rv && p < a.n) ? arow[p] * sc : 0.f;
-          const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] * sc : 0.f;
-          v[idx] = pack_h2(x0, x1);
-        }
+        for (int idx = 0; idx < 16; ++idx)  // p = 256 p2 + 16 (g + 8 nt) + 2 q + 8 j
+          v[idx] = scr[128 * (idx >> 2) + 8 * (g + 8 * ((idx >> 1) & 1)) + q + 4 * (idx & 1)];
+        __syncwarp();  // the next row reuses the scratch
         k10::tmem_st16(tx + uint32_t(16 * r), v);
         // second-stage A operand: W_16 times 2^-e, exact in float16 for e in
         // [-15, 24]; any remainder is undone in float32 on the outputs
@@ -1530,18 +1558,24 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int w = tid;  // THREADS == QW
         const int64_t col = int64_t(QW) * q2 + w;
 #pragma unroll 1
-        for (int ch = 0; ch < TI / 8; ++ch) {
-          float v[8];
+        for (int half = 0; half < 2; ++half) {  // 32 loads in flight before the stores
+          float v[TI / 2];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int64_t row = i0 + 8 * ch + k;
+          for (int k = 0; k < TI / 2; ++k) {
+            const int64_t row = i0 + (TI / 2) * half + k;
             v[k] = (row < a.m && col < a.n) ? 32.f * a.A[row * a.lda + col] : 0.f;
           }
-          const uint32_t addr = smem_addr(Fb + w * (TI * 2) + ((ch ^ (w & 7)) << 4));
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
-                       "r"(pack_b2(v[0], v[1])), "r"(pack_b2(v[2], v[3])),
-                       "r"(pack_b2(v[4], v[5])), "r"(pack_b2(v[6], v[7]))
-                       : "memory");
+#pragma unroll
+          for (int c4 = 0; c4 < TI / 16; ++c4) {
+            const int ch = (TI / 16) * half + c4;
+            const uint32_t addr = smem_addr(Fb + w * (TI * 2) + ((ch ^ (w & 7)) << 4));
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                         "r"(pack_b2(v[8 * c4], v[8 * c4 + 1])),
+                         "r"(pack_b2(v[8 * c4 + 2], v[8 * c4 + 3])),
+                         "r"(pack_b2(v[8 * c4 + 4], v[8 * c4 + 5])),
+                         "r"(pack_b2(v[8 * c4 + 6], v[8 * c4 + 7]))
+                         : "memory");
+          }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
