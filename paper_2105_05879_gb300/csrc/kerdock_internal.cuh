@@ -16,7 +16,11 @@ constexpr int kMaxK = 32;             // number of median-of-means batches
 constexpr int kRegK = 16;             // batches whose means a finalizer thread holds in registers
 constexpr uint32_t kDefaultPollLimit = 1u << 22;  // mbarrier polls before a wait gives up
 constexpr int64_t kMaxN = 1 << 24;    // samples per query
-constexpr size_t kStatusBytes = 256;  // status word area at the start of the table buffer
+// The table buffer starts with a status area: the device status word at byte
+// 0 and, from byte kWorkOffset, counters of dynamically scheduled kernels.
+constexpr size_t kStatusBytes = 1024;
+constexpr size_t kWorkOffset = 256;
+constexpr int kWorkCounters = int((kStatusBytes - kWorkOffset) / 4);
 
 // Device status word codes (first error wins).
 enum : uint32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadIndex = 2 };
@@ -50,6 +54,9 @@ struct Plan {
   uint32_t poll_limit = kDefaultPollLimit;  // query-kernel waits (lowered only by a test hook)
 
   uint32_t* status() const { return reinterpret_cast<uint32_t*>(table); }
+  int* work_counters() const {
+    return reinterpret_cast<int*>(static_cast<char*>(table) + kWorkOffset);
+  }
   uint32_t* signs() const {
     return reinterpret_cast<uint32_t*>(static_cast<char*>(table) + kStatusBytes);
   }

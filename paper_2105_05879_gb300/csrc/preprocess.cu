@@ -32,6 +32,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "kerdock_internal.cuh"
 
 namespace kd {
@@ -141,6 +143,7 @@ struct PreArgs {
   int64_t num_tiles;
   int64_t group;  // G: consecutive CTAs (or clusters) that sweep the bases in step
   uint32_t* status;  // the plan's device status word
+  int* work;         // per-tile counters of the dynamic schedule (zeroed before the launch)
 };
 
 // Work split.  Tiles are taken in groups of G adjacent tiles; the G CTAs (or
@@ -864,7 +867,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();  // E holds stages 1-2 of all 16 rows
 
-    // Stage 3: warp handles w1 = warp and warp + 8, 16 rows each.
+    // Stage 3: warp handles w1 = warp and warp + 8, 16 rows each.  A tile
+    // without scaled rows (the usual case) runs the plain W_16 code.
+    auto stage3 = [&](auto scaled_tag) {
+    constexpr bool SC = decltype(scaled_tag)::value;
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
       const int w1 = warp + 8 * s;
@@ -884,13 +890,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t m[4];
             ldmatrix_x4_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
             uint32_t A3[4] = {A16[0], A16[1], A16[2], A16[3]};
-            const bool scaled = (smask >> r) & 1u;
-            if (scaled) {  // this row's W_16 2^-e_r (or 4 I 2^-e_r)
-              const uint4 f4 = rfrag[((ident ? TI : 0) + r) * 32 + lane];
-              A3[0] = f4.x;
-              A3[1] = f4.y;
-              A3[2] = f4.z;
-              A3[3] = f4.w;
+            bool scaled = false;
+            if constexpr (SC) {
+              scaled = (smask >> r) & 1u;
+              if (scaled) {  // this row's W_16 2^-e_r (or 4 I 2^-e_r)
+                const uint4 f4 = rfrag[((ident ? TI : 0) + r) * 32 + lane];
+                A3[0] = f4.x;
+                A3[1] = f4.y;
+                A3[2] = f4.z;
+                A3[3] = f4.w;
+              }
             }
             float d3a[4], d3b[4];
             mma16816(d3a, A3, m[0], m[1]);  // [w2][w0 0..7]
@@ -900,7 +909,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               v[h][e] = d3a[e];
               v[h][4 + e] = d3b[e];
             }
-            if (scaled && rrem[r] != 0) {  // beyond float16's exponent range
+            if (SC && scaled && rrem[r] != 0) {  // beyond float16's exponent range
               const float s3 = ldexpf(1.f, -rrem[r]);
 #pragma unroll
               for (int e = 0; e < 8; ++e) v[h][e] *= s3;
@@ -928,6 +937,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
+    };
+    if (smask == 0u)
+      stage3(std::integral_constant<bool, false>{});
+    else
+      stage3(std::integral_constant<bool, true>{});
   }
   if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1351,19 +1365,50 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   };
 
-  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
-  if (ir.beg < ir.end) build_masks(int(ir.beg % B), 0);
-  __syncthreads();
+  // Dynamic schedule: CTA c starts on tile c mod T and takes CH bases at a
+  // time from that tile's counter; when its tile has none left it moves to
+  // the next tile that has (a tile reload), so SMs that write more slowly
+  // than others do not set the kernel's time.
+  __shared__ int s_grab[2];
+  constexpr int CH = 8;
+  const int T = int(a.num_tiles);
+  int t = int(blockIdx.x % T);
+  int b_next = 0, b_end = 0;
+  bool masks_ready = false;
   int mb = 0;
   uint32_t kq = 0;      // quarters stored so far (staging ring position)
   uint32_t wmask = 0u;  // this warp's rows that carry a power-of-two scale
   int64_t cur_tile = -1;
-  for (int64_t item = ir.beg; item < ir.end; ++item) {
-    const int64_t tg = item / B;
-    const int b = int(item - tg * B);
-    const int64_t t = tg * a.group + ir.slot;
-    const int64_t i0 = t * TI;
+  for (;;) {
+    if (b_next >= b_end) {
+      if (tid == 0) {
+        int gt = -1, gb = -1;
+        for (int k = 0; k < T && gb < 0; ++k) {
+          const int tt = (t + k) % T;
+          if (*reinterpret_cast<volatile int*>(a.work + tt) >= int(B)) continue;
+          const int got = atomicAdd(a.work + tt, CH);
+          if (got < int(B)) {
+            gt = tt;
+            gb = got;
+          }
+        }
+        s_grab[0] = gt;
+        s_grab[1] = gb;
+      }
+      __syncthreads();
+      if (s_grab[1] < 0) break;  // every tile is done
+      t = s_grab[0];
+      b_next = s_grab[1];
+      b_end = b_next + CH < int(B) ? b_next + CH : int(B);
+      masks_ready = false;
+    }
+    const int b = b_next++;
+    const int64_t i0 = int64_t(t) * TI;
     const bool ident = b == D / 2;
+    if (!masks_ready) {
+      build_masks(b, mb);
+      __syncthreads();
+    }
 
     if (t != cur_tile) {  // this warp's 8 rows into tensor memory, scaled, as B fragments
       wmask = 0u;
@@ -1503,39 +1548,51 @@ __global__ void __launch_bounds__(THREADS, 1)
           asm volatile("" : "+r"(yv[r][0]), "+r"(yv[r][1]), "+r"(yv[r][2]), "+r"(yv[r][3]));
         uint32_t out[8][4];
         float lo[8];
+        // the warp's rows carry no scale in the usual case: plain W_16 then
+        auto rows = [&](auto scaled_tag) {
+          constexpr bool SC = decltype(scaled_tag)::value;
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) {
-          float d1[2][4];
-          mma_f16(d1[0], w16, yv[r][0], yv[r][1]);  // [w0][p1 0..7]
-          mma_f16(d1[1], w16, yv[r][2], yv[r][3]);  // [w0][p1 8..15]
-          uint32_t fr[4] = {w16[0], w16[1], w16[2], w16[3]};
-          if ((wmask >> r) & 1u) {  // this row's W_16 2^-e
-            const uint4 f4 = frag[(warp * RPW + r) * 32 + lane];
-            fr[0] = f4.x;
-            fr[1] = f4.y;
-            fr[2] = f4.z;
-            fr[3] = f4.w;
+          for (int r = 0; r < RPW; ++r) {
+            float d1[2][4];
+            mma_f16(d1[0], w16, yv[r][0], yv[r][1]);  // [w0][p1 0..7]
+            mma_f16(d1[1], w16, yv[r][2], yv[r][3]);  // [w0][p1 8..15]
+            uint32_t fr[4] = {w16[0], w16[1], w16[2], w16[3]};
+            if constexpr (SC) {
+              if ((wmask >> r) & 1u) {  // this row's W_16 2^-e
+                const uint4 f4 = frag[(warp * RPW + r) * 32 + lane];
+                fr[0] = f4.x;
+                fr[1] = f4.y;
+                fr[2] = f4.z;
+                fr[3] = f4.w;
+              }
+            }
+            float d2[2][4];
+            mma_f16(d2[0], fr, pack_h2(d1[0][0], d1[0][1]), pack_h2(d1[1][0], d1[1][1]));
+            mma_f16(d2[1], fr, pack_h2(d1[0][2], d1[0][3]), pack_h2(d1[1][2], d1[1][3]));
+            if constexpr (SC) {
+              const int er = ((wmask >> r) & 1u) ? erem[warp * RPW + r] : 0;
+              if (er != 0) {
+                const float s2 = ldexpf(1.f, -er);
+#pragma unroll
+                for (int m = 0; m < 2; ++m)
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) d2[m][e] *= s2;
+              }
+            }
+#pragma unroll
+            for (int pos = 0; pos < 8; ++pos) {
+              const float val = d2[pos >> 2][pos & 3];
+              if (r & 1)
+                out[pos][r >> 1] = pack_b2(lo[pos], val);
+              else
+                lo[pos] = val;
+            }
           }
-          float d2[2][4];
-          mma_f16(d2[0], fr, pack_h2(d1[0][0], d1[0][1]), pack_h2(d1[1][0], d1[1][1]));  // w0 0..7
-          mma_f16(d2[1], fr, pack_h2(d1[0][2], d1[0][3]), pack_h2(d1[1][2], d1[1][3]));  // w0 8..15
-          const int er = ((wmask >> r) & 1u) ? erem[warp * RPW + r] : 0;
-          if (er != 0) {
-            const float s2 = ldexpf(1.f, -er);
-#pragma unroll
-            for (int m = 0; m < 2; ++m)
-#pragma unroll
-              for (int e = 0; e < 4; ++e) d2[m][e] *= s2;
-          }
-#pragma unroll
-          for (int pos = 0; pos < 8; ++pos) {
-            const float val = d2[pos >> 2][pos & 3];
-            if (r & 1)
-              out[pos][r >> 1] = pack_b2(lo[pos], val);
-            else
-              lo[pos] = val;
-          }
-        }
+        };
+        if (wmask == 0u)
+          rows(std::integral_constant<bool, false>{});
+        else
+          rows(std::integral_constant<bool, true>{});
         if (q2 < 3) {
 #pragma unroll
           for (int r = 0; r < RPW; ++r)
@@ -1582,7 +1639,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       // the staging buffer of the next quarter was last stored NBUF - 1 quarters
       // ago: at most NBUF - 2 later stores may still be reading
       if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
-      if (q2 == 3 && item + 1 < ir.end) build_masks(b + 1 == int(B) ? 0 : b + 1, mb ^ 1);
+      // the next basis of this grab gets its masks now, into the other buffer
+      if (q2 == 3 && b_next < b_end) build_masks(b_next, mb ^ 1);
       __syncthreads();
       if (tid == 0) {
         tma_store_2d(&tmap, smem_addr(Fb), int(i0), b * D + QW * q2);
@@ -1590,7 +1648,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       ++kq;
     }
-    mb ^= 1;
+    if (b_next < b_end) {
+      mb ^= 1;
+      masks_ready = true;
+    } else {
+      masks_ready = false;  // built into the current buffer after the next grab
+    }
   }
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1631,14 +1694,15 @@ int launch_d1024_tc(const Plan& p) {
   a.ldr = p.ldr;
   a.status = p.status();
   a.num_tiles = (p.ldr + k10tc::TI - 1) / k10tc::TI;
-  // one CTA per SM (its shared memory and all 512 tensor-memory columns);
-  // groups of up to 8 CTAs on adjacent tiles walk the bases in step
-  a.group = pick_group(a.num_tiles, 8);
-  int64_t ngrp = int64_t(p.num_sms) / a.group;
-  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
-  if (ngrp > items) ngrp = items;
-  if (ngrp < 1) ngrp = 1;
-  kern<<<unsigned(ngrp * a.group), k10tc::THREADS, k10tc::SMEM, p.stream>>>(a, map);
+  a.group = 1;
+  if (a.num_tiles > int64_t(kWorkCounters)) return KERDOCK_ERR_UNSUPPORTED;
+  a.work = p.work_counters();
+  KD_CUDA_TRY(cudaMemsetAsync(a.work, 0, size_t(a.num_tiles) * sizeof(int), p.stream));
+  // one CTA per SM (its shared memory and all 512 tensor-memory columns)
+  int64_t grid = p.num_sms;
+  const int64_t grabs = a.num_tiles * ((p.B + 7) / 8);
+  if (grid > grabs) grid = grabs;
+  kern<<<unsigned(grid), k10tc::THREADS, k10tc::SMEM, p.stream>>>(a, map);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
 }

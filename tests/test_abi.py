@@ -40,7 +40,9 @@ def test_plan_info_sizes(lib):
     assert info["d"] == 1024 and info["k"] == 10 and info["num_bases"] == 513
     assert info["L"] == 1024 * 513 and info["ldr"] == 1024
     assert info["repr_bytes"] == 513 * 1024 * 1024 * 4
-    assert info["table_bytes"] == 256 + 512 * (32 + 32) * 4
+    # a 1 KiB status area (status word, scheduling counters), then the sign
+    # table twice: p order and lane-transposed, 32 words per basis each
+    assert info["table_bytes"] == 1024 + 512 * (32 + 32) * 4
     K.kerdock_plan_destroy(h)
     # padding: n = 2048 -> d = 4096 (power of four), m ragged -> ldr multiple of 8
     h = K.kerdock_plan_create(1001, 2048, K.KERDOCK_BF16, 10, 3, 5000)
