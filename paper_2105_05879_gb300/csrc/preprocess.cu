@@ -1350,65 +1350,79 @@ __global__ void __launch_bounds__(THREADS, 1)
   // Float16 sign masks of basis b in the lanes' fragment order: mask word
   // (lane, reg) flips the elements p and p + 1 of B-fragment register reg =
   // 4 p2 + 2 nt + j, p = 256 p2 + 16 (g + 8 nt) + 2 q + 8 j.
-  auto build_masks = [&](int b, int mb) {
-    uint32_t* mk = masks + mb * MASKW;
-    for (int idx = tid; idx < MASKW; idx += THREADS) {
-      const int l = idx >> 4, reg = idx & 15;
-      const int p = 256 * (reg >> 2) + 16 * ((l >> 2) + 8 * ((reg >> 1) & 1)) + 2 * (l & 3) +
-                    8 * (reg & 1);
-      uint32_t m = 0;
-      if (b != D / 2) {
-        const uint32_t wd = __ldg(a.signs + int64_t(b) * a.sign_words + (p >> 5)) >> (p & 31);
-        m = ((wd & 1u) << 15) | ((wd & 2u) << 30);
-      }
-      mk[((reg >> 2) * 32 + l) * 4 + (reg & 3)] = m;
+  // Thread tid builds the masks idx = tid and tid + THREADS; the sign words
+  // are requested early (sign_words) and turned into masks later (put_masks).
+  static_assert(MASKW == 2 * THREADS, "two mask words per thread");
+  auto mask_p = [](int idx) {
+    const int l = idx >> 4, reg = idx & 15;
+    return 256 * (reg >> 2) + 16 * ((l >> 2) + 8 * ((reg >> 1) & 1)) + 2 * (l & 3) +
+           8 * (reg & 1);
+  };
+  auto sign_words = [&](int b, uint32_t (&wd)[2]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int p = mask_p(tid + h * THREADS);
+      wd[h] = b != D / 2 ? __ldg(a.signs + int64_t(b) * a.sign_words + (p >> 5)) : 0u;
     }
   };
+  auto put_masks = [&](const uint32_t (&wd)[2], int mb) {
+    uint32_t* mk = masks + mb * MASKW;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int idx = tid + h * THREADS, l = idx >> 4, reg = idx & 15;
+      const uint32_t bits = wd[h] >> (mask_p(idx) & 31);
+      mk[((reg >> 2) * 32 + l) * 4 + (reg & 3)] = ((bits & 1u) << 15) | ((bits & 2u) << 30);
+    }
+  };
+  auto build_masks = [&](int b, int mb) {
+    uint32_t wd[2];
+    sign_words(b, wd);
+    put_masks(wd, mb);
+  };
+  uint32_t wd_next[2] = {0u, 0u};  // sign words of the grab's next basis, requested early
 
   // Dynamic schedule: CTA c starts on tile c mod T and takes CH bases at a
   // time from that tile's counter; when its tile has none left it moves to
   // the next tile that has (a tile reload), so SMs that write more slowly
   // than others do not set the kernel's time.
-  __shared__ int s_grab[2];
+  // The last item of a grab already takes the next one (thread 0, during its
+  // first phase, into the other slot of s_grab), so the next grab's first
+  // masks are prepared like any other basis's.
+  __shared__ int s_grab[2][2];  // [slot][tile, first basis (-1: none left)]
   constexpr int CH = 8;
   const int T = int(a.num_tiles);
-  int t = int(blockIdx.x % T);
-  int b_next = 0, b_end = 0;
-  bool masks_ready = false;
+  auto grab = [&](int from, int slot) {  // thread 0 only
+    int gt = -1, gb = -1;
+    for (int k = 0; k < T && gb < 0; ++k) {
+      const int tt = (from + k) % T;
+      if (*reinterpret_cast<volatile int*>(a.work + tt) >= int(B)) continue;
+      const int got = atomicAdd(a.work + tt, CH);
+      if (got < int(B)) {
+        gt = tt;
+        gb = got;
+      }
+    }
+    s_grab[slot][0] = gt;
+    s_grab[slot][1] = gb;
+  };
+  int gs = 0;  // slot of the current grab
+  if (tid == 0) grab(int(blockIdx.x % T), 0);
+  __syncthreads();
+  int t = s_grab[0][0];
+  int b_next = s_grab[0][1];
+  int b_end = b_next + CH < int(B) ? b_next + CH : int(B);
+  if (b_next >= 0) build_masks(b_next, 0);
+  __syncthreads();
   int mb = 0;
   uint32_t kq = 0;      // quarters stored so far (staging ring position)
   uint32_t wmask = 0u;  // this warp's rows that carry a power-of-two scale
   int64_t cur_tile = -1;
-  for (;;) {
-    if (b_next >= b_end) {
-      if (tid == 0) {
-        int gt = -1, gb = -1;
-        for (int k = 0; k < T && gb < 0; ++k) {
-          const int tt = (t + k) % T;
-          if (*reinterpret_cast<volatile int*>(a.work + tt) >= int(B)) continue;
-          const int got = atomicAdd(a.work + tt, CH);
-          if (got < int(B)) {
-            gt = tt;
-            gb = got;
-          }
-        }
-        s_grab[0] = gt;
-        s_grab[1] = gb;
-      }
-      __syncthreads();
-      if (s_grab[1] < 0) break;  // every tile is done
-      t = s_grab[0];
-      b_next = s_grab[1];
-      b_end = b_next + CH < int(B) ? b_next + CH : int(B);
-      masks_ready = false;
-    }
+  while (b_next >= 0) {
     const int b = b_next++;
+    const bool last = b_next >= b_end;  // last item of this grab
+    if (last && tid == 0) grab(t, gs ^ 1);
     const int64_t i0 = int64_t(t) * TI;
     const bool ident = b == D / 2;
-    if (!masks_ready) {
-      build_masks(b, mb);
-      __syncthreads();
-    }
 
     if (t != cur_tile) {  // this warp's 8 rows into tensor memory, scaled, as B fragments
       wmask = 0u;
@@ -1639,8 +1653,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       // the staging buffer of the next quarter was last stored NBUF - 1 quarters
       // ago: at most NBUF - 2 later stores may still be reading
       if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
-      // the next basis of this grab gets its masks now, into the other buffer
-      if (q2 == 3 && b_next < b_end) build_masks(b_next, mb ^ 1);
+      // the next basis (of this grab, or the first of the next one, known
+      // after quarter 0's barrier): its sign words are requested at quarter 1
+      // and become masks, in the other buffer, at quarter 3
+      if (q2 == 1 || q2 == 3) {
+        const int nb = last ? s_grab[gs ^ 1][1] : b_next;
+        if (nb >= 0) {
+          if (q2 == 1)
+            sign_words(nb, wd_next);
+          else
+            put_masks(wd_next, mb ^ 1);
+        }
+      }
       __syncthreads();
       if (tid == 0) {
         tma_store_2d(&tmap, smem_addr(Fb), int(i0), b * D + QW * q2);
@@ -1648,11 +1672,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       ++kq;
     }
-    if (b_next < b_end) {
-      mb ^= 1;
-      masks_ready = true;
-    } else {
-      masks_ready = false;  // built into the current buffer after the next grab
+    mb ^= 1;
+    if (last) {  // move to the grab taken during this item (-1: all tiles are done)
+      gs ^= 1;
+      t = s_grab[gs][0];
+      b_next = s_grab[gs][1];
+      b_end = b_next + CH < int(B) ? b_next + CH : int(B);
     }
   }
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
