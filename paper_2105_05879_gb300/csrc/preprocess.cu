@@ -1259,8 +1259,8 @@ namespace k10tc {
 constexpr int D = 1024, TI = 64, WARPS = 8, THREADS = WARPS * 32, RPW = TI / WARPS;
 constexpr int QW = 256;                         // outputs w per quarter
 static_assert(THREADS == QW, "the identity basis gives each thread one w of a quarter");
-constexpr int FBUF = QW * TI * 2;               // 32 KiB staging buffer
-constexpr int NBUF = 4;                         // staging ring
+constexpr int FBUF = QW * TI * 2;               // 32 KiB: one quarter's staging
+constexpr int NBUF = 4;                         // two rounds of two quarters
 constexpr int MASKW = 512;                      // float16 sign masks per basis (16 per lane)
 constexpr size_t OFF_MASK = size_t(NBUF) * FBUF;
 constexpr size_t OFF_FRAG = OFF_MASK + 2 * MASKW * 4;                    // [warp][row][lane] uint4
@@ -1551,9 +1551,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int r = 0; r < RPW; ++r) tmem_ld4(ty + uint32_t(16 * r), yq[0][r]);
     }
+    // Quarters are staged in rounds of two (64 KiB): one proxy fence and one
+    // barrier per round; the round's buffer was stored two rounds ago.
 #pragma unroll
     for (int q2 = 0; q2 < 4; ++q2) {
-      unsigned char* Fb = smem + size_t(kq % NBUF) * FBUF;
+      unsigned char* Fb = smem + size_t((kq & 1) * 2 + (q2 & 1)) * FBUF;
       if (!ident) {
         uint32_t (&yv)[RPW][4] = yq[q2 & 1];
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -1613,13 +1615,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             tmem_ld4(ty + uint32_t(16 * r + 4 * (q2 + 1)), yq[(q2 + 1) & 1][r]);
         }
         // position pos: w1 = g + 8 ((pos & 3) >> 1), w0 = 2q + 8 (pos >> 2) + (pos & 1);
-        // the warp's 8 rows are 16-byte chunk `warp` of the 128-byte row w
+        // the warp's 8 rows are 16-byte chunk `warp` ^ (w & 7) of the 128-byte
+        // row w.  Lanes with odd g store their positions in pairwise swapped
+        // order, so that in each quarter-warp the lanes g = 2k and 2k + 1 hit
+        // different 16-byte chunks (their w differ by 16, not in w & 7).
+        const bool oddg = g & 1;
 #pragma unroll
-        for (int pos = 0; pos < 8; ++pos) {
+        for (int i = 0; i < 8; ++i) {
+          const int pos = i ^ int(oddg);
           const int w = 16 * (g + 8 * ((pos & 3) >> 1)) + 2 * q + 8 * (pos >> 2) + (pos & 1);
           const uint32_t addr = smem_addr(Fb + w * (TI * 2) + ((warp ^ (w & 7)) << 4));
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(out[pos][0]),
-                       "r"(out[pos][1]), "r"(out[pos][2]), "r"(out[pos][3])
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr),
+                       "r"(oddg ? out[i ^ 1][0] : out[i][0]), "r"(oddg ? out[i ^ 1][1] : out[i][1]),
+                       "r"(oddg ? out[i ^ 1][2] : out[i][2]), "r"(oddg ? out[i ^ 1][3] : out[i][3])
                        : "memory");
         }
       } else {
@@ -1649,10 +1657,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
+      if ((q2 & 1) == 0) continue;  // the round's second quarter ends it
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      // the staging buffer of the next quarter was last stored NBUF - 1 quarters
-      // ago: at most NBUF - 2 later stores may still be reading
-      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory");
+      // the next round's buffers were stored by the previous round, whose
+      // stores must be done reading them
+      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       // the next basis (of this grab, or the first of the next one, known
       // after quarter 0's barrier): its sign words are requested at quarter 1
       // and become masks, in the other buffer, at quarter 3
@@ -1667,6 +1676,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       __syncthreads();
       if (tid == 0) {
+        tma_store_2d(&tmap, smem_addr(Fb - FBUF), int(i0), b * D + QW * (q2 - 1));
         tma_store_2d(&tmap, smem_addr(Fb), int(i0), b * D + QW * q2);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
