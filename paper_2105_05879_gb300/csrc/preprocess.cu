@@ -1657,23 +1657,24 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
-      if ((q2 & 1) == 0) continue;  // the round's second quarter ends it
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      // the next round's buffers were stored by the previous round, whose
-      // stores must be done reading them
-      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      // the next basis (of this grab, or the first of the next one, known
-      // after quarter 0's barrier): its sign words are requested at quarter 1
-      // and become masks, in the other buffer, at quarter 3
-      if (q2 == 1 || q2 == 3) {
+      // the next basis (of this grab, or the first of the next one, which
+      // thread 0 took at the start of this item and is visible after round
+      // 0's barrier): its sign words are requested at quarter 2 and become
+      // masks, in the other buffer, at quarter 3
+      if (q2 >= 2) {
         const int nb = last ? s_grab[gs ^ 1][1] : b_next;
         if (nb >= 0) {
-          if (q2 == 1)
+          if (q2 == 2)
             sign_words(nb, wd_next);
           else
             put_masks(wd_next, mb ^ 1);
         }
       }
+      if ((q2 & 1) == 0) continue;  // the round's second quarter ends it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the next round's buffers were stored by the previous round, whose
+      // stores must be done reading them
+      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         tma_store_2d(&tmap, smem_addr(Fb - FBUF), int(i0), b * D + QW * (q2 - 1));
