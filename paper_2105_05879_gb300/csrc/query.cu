@@ -577,9 +577,20 @@ __device__ void gather_role(const Seq& seq, const LaunchCfg& cfg, const Regions&
     float* means = rg.means_base + (qs % kMBufs) * cfg.mstride;
     bool ok;
     if (DYN) {
-      ok = qd.dtype == KERDOCK_BF16
-               ? gather_query<__nv_bfloat16, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
-               : gather_query<float, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+      // each query's own type and granules per gather thread (a batch mixes
+      // row sizes; the loop for the largest would idle on the smaller rows)
+      constexpr int kGT = Roles<CW>::kGatherThreads;
+      const int64_t gran = qd.ldr / (qd.dtype == KERDOCK_BF16 ? 8 : 4);
+      const int gpt = gran <= kGT ? 1 : (gran <= 2 * kGT ? 2 : 4);
+      if (qd.dtype == KERDOCK_BF16) {
+        ok = gpt == 1   ? gather_query<__nv_bfloat16, 1, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
+             : gpt == 2 ? gather_query<__nv_bfloat16, 2, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
+                        : gather_query<__nv_bfloat16, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+      } else {
+        ok = gpt == 1   ? gather_query<float, 1, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
+             : gpt == 2 ? gather_query<float, 2, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
+                        : gather_query<float, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+      }
     } else {
       ok = gather_query<RT, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
     }
