@@ -578,11 +578,11 @@ int launch_small(const Plan& p) {
 // ---------------------------------------------------------------------------
 namespace tc {
 
-constexpr int TI = 16, WARPS = 8, THREADS = WARPS * 32, D = 4096;
+constexpr int TI = 16, WARPS = 16, THREADS = WARPS * 32, D = 4096;
 constexpr int E_W1 = 16 * 32 + 16;           // bytes per (row, w1): 16 p2 x 32 B + pad
 constexpr int E_ROW = 16 * E_W1;             // bytes per row
 constexpr int E_BYTES = TI * E_ROW;          // 135168
-constexpr int F_WARP = 16 * 16 * TI * 2;     // [w2][w0][row] bfloat16 per warp: 8 KiB
+constexpr int F_WARP = 16 * 8 * TI * 2;      // [w2][w0 half][row] bfloat16 per warp: 4 KiB
 constexpr int MASK_WORDS = 16 * 32 * 4;      // [p2][lane][4]
 constexpr size_t OFF_MASK = size_t(E_BYTES) + size_t(WARPS) * F_WARP;
 constexpr size_t OFF_SLOT = OFF_MASK + MASK_WORDS * 4;
@@ -619,9 +619,9 @@ __device__ __forceinline__ void stmatrix_x4(uint32_t addr, uint32_t e0, uint32_t
                "r"(e0), "r"(e1), "r"(e2), "r"(e3)
                : "memory");
 }
-__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t addr, uint32_t (&m)[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-               : "=r"(m[0]), "=r"(m[1]), "=r"(m[2]), "=r"(m[3])
+__device__ __forceinline__ void ldmatrix_x2_trans(uint32_t addr, uint32_t (&m)[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
+               : "=r"(m[0]), "=r"(m[1])
                : "r"(addr)
                : "memory");
 }
@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t smask = 0u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, q = lane & 3;
-  const int quarter = warp & 3, phalf = warp >> 2;  // lane quarter of tensor memory; p2 half
+  const int quarter = warp & 3, pq = warp >> 2;  // lane quarter of tensor memory; p2 quarter
   const bool aligned = (smem_addr(smem) & 1023u) == 0;
 
   if (warp == 0) {
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 
   const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
-  // This thread's eight sign words of basis b (mask words k = 8 tid + u), as
+  // This thread's four sign words of basis b (mask words k = 4 tid + u), as
   // loaded from the p-order table; requested one basis ahead.
   constexpr int MW = MASK_WORDS / THREADS;
   auto mask_p = [&](int u) {
@@ -736,8 +736,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       // 11 significant bits (entries below 2^-14 are subnormal but then below
       // 2^-6 of the row's largest, with absolute error <= 2^-25).  Any other
       // row is scaled by 2^e_r (largest entry into [1/2, 1)) and stage 3
-      // multiplies by 2^-e_r again.  Row r is loaded by the two warps of lane
-      // quarter r mod 4, each for half of p.
+      // multiplies by 2^-e_r again.  Row r is loaded by the four warps of lane
+      // quarter r mod 4, each for a quarter of p.
       __syncthreads();  // every warp is done with the previous tile's row data
       if (tid < TI) rmax[tid] = 0u;
       __syncthreads();
@@ -747,7 +747,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         float mx = 0.f;
         if (row < a.m) {
           const float* arow = a.A + row * a.lda;
-          for (int64_t p = 2048 * phalf + lane; p < 2048 * phalf + 2048 && p < a.n; p += 32)
+          for (int64_t p = 1024 * pq + lane; p < 1024 * pq + 1024 && p < a.n; p += 32)
             mx = fmaxf(mx, fabsf(arow[p]));
         }
 #pragma unroll
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int e = (mx > 0.f && (ex < -7 || ex > 6)) ? -ex : 0;
         const float sc = ldexpf(1.f, e);
 #pragma unroll 1
-        for (int p2 = 8 * phalf; p2 < 8 * phalf + 8; ++p2) {
+        for (int p2 = 4 * pq; p2 < 4 * pq + 4; ++p2) {
           uint32_t v[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tmem_st4(tlane + tcol(rl, p2), v);
         }
-        if (phalf == 0) {
+        if (pq == 0) {
           // stage-3 A operands W_16 2^-e and 4 I 2^-e, exact in float16 for
           // e in [-13, 24]; the rest of the exponent is undone in float32
           const int ef = e < -13 ? -13 : (e > 24 ? 24 : e);
@@ -819,27 +819,27 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();  // masks ready; every warp is done reading E for the previous item
 
-    // Stages 1 and 2 for this warp's rows (quarter + 4 rl) and p2 half.
+    // Stages 1 and 2 for this warp's rows (quarter + 4 rl) and p2 quarter.
     uint32_t A16[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) A16[e] = ident ? ai[e] : aw[e];
-    // 32 units (row slot rl, p2) per warp, two at a time; the next pair's words
+    // 16 units (row slot rl, p2) per warp, two at a time; the next pair's words
     // are loaded from tensor memory while this pair is multiplied.
-    auto unit_rl = [](int u) { return u >> 3; };
-    auto unit_p2 = [phalf](int u) { return 8 * phalf + (u & 7); };
+    auto unit_rl = [](int u) { return u >> 2; };
+    auto unit_p2 = [pq](int u) { return 4 * pq + (u & 3); };
     uint32_t xa[4], xb[4];
     tmem_ld4(tlane + tcol(unit_rl(0), unit_p2(0)), xa);
     tmem_ld4(tlane + tcol(unit_rl(1), unit_p2(1)), xb);
     tmem_wait_ld(xa, xb);
 #pragma unroll 1
-    for (int u = 0; u < 32; u += 2) {
+    for (int u = 0; u < 16; u += 2) {
       uint32_t x[2][4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         x[0][e] = xa[e];
         x[1][e] = xb[e];
       }
-      if (u + 2 < 32) {
+      if (u + 2 < 16) {
         tmem_ld4(tlane + tcol(unit_rl(u + 2), unit_p2(u + 2)), xa);
         tmem_ld4(tlane + tcol(unit_rl(u + 3), unit_p2(u + 3)), xb);
       }
@@ -867,28 +867,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();  // E holds stages 1-2 of all 16 rows
 
-    // Stage 3: warp handles w1 = warp and warp + 8, 16 rows each.  A tile
-    // without scaled rows (the usual case) runs the plain W_16 code.
+    // Stage 3: warp handles w1 = warp, 16 rows, one half of w0 at a time.  A
+    // tile without scaled rows (the usual case) runs the plain W_16 code.
     auto stage3 = [&](auto scaled_tag) {
     constexpr bool SC = decltype(scaled_tag)::value;
+    const int w1 = warp;
 #pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
-      const int w1 = warp + 8 * s;
+    for (int hh = 0; hh < 2; ++hh) {
       if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       __syncwarp();  // the previous TMA store has read this warp's F
 #pragma unroll 1
       for (int g8 = 0; g8 < 2; ++g8) {
-        uint32_t packed[8][4];
+        uint32_t packed[4][4];
 #pragma unroll
         for (int rp = 0; rp < 4; ++rp) {
-          float v[2][8];
+          float v[2][4];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = 8 * g8 + 2 * rp + h;
-            const int mi = lane >> 3, mj = lane & 7;
-            const int p2 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
-            uint32_t m[4];
-            ldmatrix_x4_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
+            // lanes 0-15 address p2 = lane & 15 of the w0 half hh (the
+            // 16-byte half hh ^ swizzle); the other lanes' addresses are unused
+            const int p2 = lane & 15, wh = hh ^ ((p2 >> 2) & 1);
+            uint32_t m[2];
+            ldmatrix_x2_trans(smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16), m);
             uint32_t A3[4] = {A16[0], A16[1], A16[2], A16[3]};
             bool scaled = false;
             if constexpr (SC) {
@@ -901,39 +902,32 @@ __global__ void __launch_bounds__(THREADS, 1)
                 A3[3] = f4.w;
               }
             }
-            float d3a[4], d3b[4];
-            mma16816(d3a, A3, m[0], m[1]);  // [w2][w0 0..7]
-            mma16816(d3b, A3, m[2], m[3]);  // [w2][w0 8..15]
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              v[h][e] = d3a[e];
-              v[h][4 + e] = d3b[e];
-            }
+            mma16816(v[h], A3, m[0], m[1]);  // [w2][w0 8 hh .. 8 hh + 7]
             if (SC && scaled && rrem[r] != 0) {  // beyond float16's exponent range
               const float s3 = ldexpf(1.f, -rrem[r]);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) v[h][e] *= s3;
+              for (int e = 0; e < 4; ++e) v[h][e] *= s3;
             }
           }
 #pragma unroll
-          for (int pos = 0; pos < 8; ++pos) packed[pos][rp] = pack_bf16x2(v[0][pos], v[1][pos]);
+          for (int pos = 0; pos < 4; ++pos) packed[pos][rp] = pack_bf16x2(v[0][pos], v[1][pos]);
         }
-        // position pos: w2 = g + 8 ((pos >> 1) & 1), w0 = 2q + (pos & 1) + 8 (pos >> 2).
-        // F uses the tensor map's 32-byte swizzle: the 16-byte half g8 of the
-        // 32-byte row (w2, w0) sits at g8 ^ (bit 2 of w0), so the eight lanes of
-        // a quarter-warp cover four bank slots instead of two.
+        // position pos: w2 = g + 8 (pos >> 1), w0 = 8 hh + 2q + (pos & 1).
+        // F is [w2][w0 - 8 hh][row] under the tensor map's 32-byte swizzle:
+        // the 16-byte half g8 of the 32-byte row (w2, w0') sits at g8 ^ (bit 2
+        // of w0'), so the eight lanes of a quarter-warp cover four bank slots.
 #pragma unroll
-        for (int pos = 0; pos < 8; ++pos) {
-          const int w2 = g + 8 * ((pos >> 1) & 1), w0 = 2 * q + (pos & 1) + 8 * (pos >> 2);
+        for (int pos = 0; pos < 4; ++pos) {
+          const int w2 = g + 8 * (pos >> 1), w0 = 2 * q + (pos & 1);
           const int half = g8 ^ ((w0 >> 2) & 1);
-          *reinterpret_cast<uint4*>(Fw + (w2 * 16 + w0) * (TI * 2) + half * 16) =
+          *reinterpret_cast<uint4*>(Fw + (w2 * 8 + w0) * (TI * 2) + half * 16) =
               make_uint4(packed[pos][0], packed[pos][1], packed[pos][2], packed[pos][3]);
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0 && aligned) {
-        tma_store_4d(&tmap, smem_addr(Fw), int(i0), 0, w1, b * 16);
+        tma_store_4d(&tmap, smem_addr(Fw), int(i0), 8 * hh, w1, b * 16);
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
@@ -976,12 +970,12 @@ EncodeTiledFn encoder() {
 int launch_d4096_tc(const Plan& p) {
   tc::EncodeTiledFn enc = tc::encoder();
   if (enc == nullptr) return KERDOCK_ERR_UNSUPPORTED;
-  // R[b][w][i] (bfloat16) as [(b, w2)][w1][w0][i]: box 16 rows x 16 w0 x 1 w1 x 16 w2
+  // R[b][w][i] (bfloat16) as [(b, w2)][w1][w0][i]: box 16 rows x 8 w0 x 1 w1 x 16 w2
   CUtensorMap map;
   const cuuint64_t dims[4] = {cuuint64_t(p.ldr), 16, 16, cuuint64_t(p.B) * 16};
   const cuuint64_t strides[3] = {cuuint64_t(p.ldr) * 2, cuuint64_t(p.ldr) * 32,
                                  cuuint64_t(p.ldr) * 512};
-  const cuuint32_t box[4] = {tc::TI, 16, 1, 16};
+  const cuuint32_t box[4] = {tc::TI, 8, 1, 16};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, p.repr, dims, strides, box, es,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
