@@ -583,9 +583,7 @@ constexpr int E_W1 = 16 * 32 + 16;           // bytes per (row, w1): 16 p2 x 32 
 constexpr int E_ROW = 16 * E_W1;             // bytes per row
 constexpr int E_BYTES = TI * E_ROW;          // 135168
 constexpr int F_WARP = 16 * 8 * TI * 2;      // [w2][w0 half][row] bfloat16 per warp: 4 KiB
-constexpr int MASK_WORDS = 16 * 32 * 4;      // [p2][lane][4]
-constexpr size_t OFF_MASK = size_t(E_BYTES) + size_t(WARPS) * F_WARP;
-constexpr size_t OFF_SLOT = OFF_MASK + MASK_WORDS * 4;
+constexpr size_t OFF_SLOT = size_t(E_BYTES) + size_t(WARPS) * F_WARP;
 constexpr size_t OFF_RFRAG = OFF_SLOT + 16;                 // [2][TI rows][32 lanes] uint4
 constexpr size_t OFF_RMAX = OFF_RFRAG + 2 * size_t(TI) * 32 * 16;
 constexpr size_t OFF_REM = OFF_RMAX + TI * 4;
@@ -663,7 +661,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* E = smem;
   unsigned char* Fw = smem + E_BYTES + (threadIdx.x >> 5) * F_WARP;  // this warp's F
-  uint32_t* maskt = reinterpret_cast<uint32_t*>(smem + OFF_MASK);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_SLOT);
   uint4* rfrag = reinterpret_cast<uint4*>(smem + OFF_RFRAG);     // [W16 | 4 I][row][lane]
   uint32_t* rmax = reinterpret_cast<uint32_t*>(smem + OFF_RMAX);  // row maxima (float bits)
@@ -704,24 +701,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 
   const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
-  // This thread's four sign words of basis b (mask words k = 4 tid + u), as
-  // loaded from the p-order table; requested one basis ahead.
-  constexpr int MW = MASK_WORDS / THREADS;
-  auto mask_p = [&](int u) {
-    const int k = tid * MW + u;
-    const int p2 = k >> 7, l = (k >> 2) & 31, j = k & 3;
-    return p2 * 256 + ((l >> 2) + 8 * (j >> 1)) * 16 + 2 * (l & 3) + 8 * (j & 1);
-  };
-  auto load_words = [&](int b, uint32_t (&wd)[MW]) {
-    const uint32_t* srow = a.signs + int64_t(b == D / 2 ? 0 : b) * a.sign_words;
+  // Step (i) of Lemma 6 in registers.  The B fragment word j of (p2, lane)
+  // holds p = 256 p2 + 16 (g + 8 (j >> 1)) + 2q + 8 (j & 1) and p + 1, so the
+  // warp's p2 quarter needs two sign words per p2 (j >> 1 = 0, 1), both at bit
+  // offset 16 (g & 1) + 2q, plus 8 for j & 1.  They are requested for the next
+  // basis while stage 3 of this one runs.
+  const int wsh = 16 * (g & 1) + 2 * q;
+  auto load_words = [&](int b, uint32_t (&wd)[8]) {
+    const uint32_t* srow =
+        a.signs + int64_t(b == D / 2 ? 0 : b) * a.sign_words + 32 * pq + (g >> 1);
 #pragma unroll
-    for (int u = 0; u < MW; ++u) {
-      const int p = mask_p(u);
-      wd[u] = b == D / 2 ? 0u : __ldg(srow + (p >> 5)) >> (p & 31);
-    }
+    for (int k = 0; k < 8; ++k)
+      wd[k] = b == D / 2 ? 0u : __ldg(srow + 8 * (k >> 1) + 4 * (k & 1)) >> wsh;
   };
-  uint32_t wnext[MW];
-  if (ir.beg < ir.end) load_words(int(ir.beg % B), wnext);
+  uint32_t wd[8];
+  if (ir.beg < ir.end) load_words(int(ir.beg % B), wd);
   int64_t cur_tile = -1;
   for (int64_t item = ir.beg; item < ir.end; ++item) {
     const int64_t tg = item / B;
@@ -805,66 +799,67 @@ __global__ void __launch_bounds__(THREADS, 1)
       cur_tile = t;
     }
 
-    // Step (i) of Lemma 6 as bfloat16 sign masks in the threads' word order,
-    // from the words requested during the previous basis; then request the
-    // next basis's words.
-    {
-      uint32_t wcur[MW];
-#pragma unroll
-      for (int u = 0; u < MW; ++u) wcur[u] = wnext[u];
-      if (item + 1 < ir.end) load_words(b + 1 == int(B) ? 0 : b + 1, wnext);
-#pragma unroll
-      for (int u = 0; u < MW; ++u)
-        maskt[tid * MW + u] = ((wcur[u] & 1u) << 15) | ((wcur[u] & 2u) << 30);
-    }
-    __syncthreads();  // masks ready; every warp is done reading E for the previous item
+    __syncthreads();  // every warp is done reading E for the previous item
 
     // Stages 1 and 2 for this warp's rows (quarter + 4 rl) and p2 quarter.
     uint32_t A16[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) A16[e] = ident ? ai[e] : aw[e];
-    // 16 units (row slot rl, p2) per warp, two at a time; the next pair's words
-    // are loaded from tensor memory while this pair is multiplied.
-    auto unit_rl = [](int u) { return u >> 2; };
-    auto unit_p2 = [pq](int u) { return 4 * pq + (u & 3); };
+    // 16 units (row slot rl, p2) per warp in p2-major order, two at a time
+    // (pair pi: p2 = 4 pq + (pi >> 1), rl = 2 (pi & 1) + h); the next pair's
+    // words are loaded from tensor memory while this pair is multiplied.
+    auto pair_col = [&](int pi, int h) {
+      return tlane + tcol(2 * (pi & 1) + h, 4 * pq + (pi >> 1));
+    };
     uint32_t xa[4], xb[4];
-    tmem_ld4(tlane + tcol(unit_rl(0), unit_p2(0)), xa);
-    tmem_ld4(tlane + tcol(unit_rl(1), unit_p2(1)), xb);
+    tmem_ld4(pair_col(0, 0), xa);
+    tmem_ld4(pair_col(0, 1), xb);
     tmem_wait_ld(xa, xb);
 #pragma unroll 1
-    for (int u = 0; u < 16; u += 2) {
-      uint32_t x[2][4];
+    for (int pl = 0; pl < 4; ++pl) {
+      const int p2 = 4 * pq + pl;
+      // float16x2 sign masks of this p2 from its two words (now wd[0], wd[1])
+      uint32_t mk[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        x[0][e] = xa[e];
-        x[1][e] = xb[e];
-      }
-      if (u + 2 < 16) {
-        tmem_ld4(tlane + tcol(unit_rl(u + 2), unit_p2(u + 2)), xa);
-        tmem_ld4(tlane + tcol(unit_rl(u + 3), unit_p2(u + 3)), xb);
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t t = wd[j >> 1] >> (8 * (j & 1));
+        mk[j] = ((t & 1u) << 15) | ((t & 2u) << 30);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = quarter + 4 * unit_rl(u + h), p2 = unit_p2(u + h);
-        const uint4 mk = *reinterpret_cast<const uint4*>(&maskt[(p2 * 32 + lane) * 4]);
-        x[h][0] ^= mk.x;
-        x[h][1] ^= mk.y;
-        x[h][2] ^= mk.z;
-        x[h][3] ^= mk.w;
-        float d1a[4], d1b[4], d2a[4], d2b[4];
-        mma16816(d1a, A16, x[h][0], x[h][1]);  // [w0][p1 0..7]
-        mma16816(d1b, A16, x[h][2], x[h][3]);  // [w0][p1 8..15]
-        mma16816(d2a, A16, pack_f16x2(d1a[0], d1a[1]), pack_f16x2(d1b[0], d1b[1]));  // w0 0..7
-        mma16816(d2b, A16, pack_f16x2(d1a[2], d1a[3]), pack_f16x2(d1b[2], d1b[3]));  // w0 8..15
-        // [w1][w0] -> E[r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
-        const int mi = lane >> 3, mj = lane & 7;
-        const int w1 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
-        const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
-        stmatrix_x4(addr, pack_f16x2(d2a[0], d2a[1]), pack_f16x2(d2a[2], d2a[3]),
-                    pack_f16x2(d2b[0], d2b[1]), pack_f16x2(d2b[2], d2b[3]));
+      for (int hp = 0; hp < 2; ++hp) {
+        const int pi = 2 * pl + hp;
+        uint32_t x[2][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x[0][e] = xa[e] ^ mk[e];
+          x[1][e] = xb[e] ^ mk[e];
+        }
+        if (pi + 1 < 8) {
+          tmem_ld4(pair_col(pi + 1, 0), xa);
+          tmem_ld4(pair_col(pi + 1, 1), xb);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = quarter + 4 * (2 * hp + h);
+          float d1a[4], d1b[4], d2a[4], d2b[4];
+          mma16816(d1a, A16, x[h][0], x[h][1]);  // [w0][p1 0..7]
+          mma16816(d1b, A16, x[h][2], x[h][3]);  // [w0][p1 8..15]
+          mma16816(d2a, A16, pack_f16x2(d1a[0], d1a[1]), pack_f16x2(d1b[0], d1b[1]));  // w0 0..7
+          mma16816(d2b, A16, pack_f16x2(d1a[2], d1a[3]), pack_f16x2(d1b[2], d1b[3]));  // w0 8..15
+          // [w1][w0] -> E[r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
+          const int mi = lane >> 3, mj = lane & 7;
+          const int w1 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
+          const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
+          stmatrix_x4(addr, pack_f16x2(d2a[0], d2a[1]), pack_f16x2(d2a[2], d2a[3]),
+                      pack_f16x2(d2b[0], d2b[1]), pack_f16x2(d2b[2], d2b[3]));
+        }
+        tmem_wait_ld(xa, xb);
       }
-      tmem_wait_ld(xa, xb);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wd[k] = wd[k + 2];
     }
+    // the words of the next basis, used by its stages 1-2
+    if (item + 1 < ir.end) load_words(b + 1 == int(B) ? 0 : b + 1, wd);
     __syncthreads();  // E holds stages 1-2 of all 16 rows
 
     // Stage 3: warp handles w1 = warp, 16 rows, one half of w0 at a time.  A
@@ -915,13 +910,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         // position pos: w2 = g + 8 (pos >> 1), w0 = 8 hh + 2q + (pos & 1).
         // F is [w2][w0 - 8 hh][row] under the tensor map's 32-byte swizzle:
         // the 16-byte half g8 of the 32-byte row (w2, w0') sits at g8 ^ (bit 2
-        // of w0'), so the eight lanes of a quarter-warp cover four bank slots.
+        // of w0').  Lanes of odd g store the positions of a pair in the other
+        // order, so the eight lanes of a quarter-warp cover all eight bank
+        // slots: (bit 0 of w0') ^ (g & 1), bit 1 of w0', half.
+        const bool swp = g & 1;
 #pragma unroll
         for (int pos = 0; pos < 4; ++pos) {
-          const int w2 = g + 8 * (pos >> 1), w0 = 2 * q + (pos & 1);
+          const int ps = swp ? pos ^ 1 : pos;
+          const int w2 = g + 8 * (pos >> 1), w0 = 2 * q + (ps & 1);
           const int half = g8 ^ ((w0 >> 2) & 1);
-          *reinterpret_cast<uint4*>(Fw + (w2 * 8 + w0) * (TI * 2) + half * 16) =
-              make_uint4(packed[pos][0], packed[pos][1], packed[pos][2], packed[pos][3]);
+          uint4 val;
+          val.x = swp ? packed[pos ^ 1][0] : packed[pos][0];
+          val.y = swp ? packed[pos ^ 1][1] : packed[pos][1];
+          val.z = swp ? packed[pos ^ 1][2] : packed[pos][2];
+          val.w = swp ? packed[pos ^ 1][3] : packed[pos][3];
+          *reinterpret_cast<uint4*>(Fw + (w2 * 8 + w0) * (TI * 2) + half * 16) = val;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
