@@ -1010,6 +1010,376 @@ int launch_d4096_tc(const Plan& p) {
 }
 
 // ---------------------------------------------------------------------------
+// d = 4096, float32 representation, on the tensor cores
+// (preprocess_d4096_tc32_kernel).  The three stages of
+// preprocess_d4096_tc_kernel with float32 accuracy: every float16 data operand
+// is a pair hi + lo (hi = float16(v), lo = float16(v - hi): 22 significant
+// bits together), and W_16, exact in float16, multiplies both into one
+// float32 accumulator (two MMAs per product).  Every row is scaled by 2^e_r
+// (largest entry into [1/2, 1)) before the split, so the pair keeps 22 bits of
+// each entry down to 2^-3 of the row's largest and an absolute 2^-25 below
+// that (lo becomes subnormal); stage 3 multiplies by 2^-e_r in float32.  A
+// CTA's tile is 8 rows (32-byte float32 runs, as 16 rows of bfloat16), E
+// holds the hi and lo planes of stages 1-2 and tensor memory the hi and lo
+// words of the tile, so both take the bfloat16 kernel's space and each item
+// the same number of MMAs for the same 128 KiB of output.
+// ---------------------------------------------------------------------------
+namespace tc32 {
+
+using tc::ldmatrix_x2_trans;
+using tc::mma16816;
+using tc::pack_f16x2;
+using tc::stmatrix_x4;
+using tc::tma_store_4d;
+
+constexpr int TI = 8, WARPS = 16, THREADS = WARPS * 32, D = 4096;
+constexpr int E_W1 = 16 * 32 + 16;      // bytes per (row, w1) of one plane: 16 p2 x 32 B + pad
+constexpr int E_ROW = 16 * E_W1;        // bytes per row of one plane
+constexpr int E_PLANE = TI * E_ROW;     // 67584: hi plane, then lo plane
+constexpr int E_BYTES = 2 * E_PLANE;
+constexpr int F_WARP = 16 * 8 * TI * 4;  // [w2][w0 half][row] float32 per warp: 4 KiB
+constexpr size_t OFF_SLOT = size_t(E_BYTES) + size_t(WARPS) * F_WARP;
+constexpr size_t OFF_RMAX = OFF_SLOT + 16;
+constexpr size_t OFF_RSC = OFF_RMAX + TI * 4;
+constexpr size_t SMEM = OFF_RSC + TI * 4;
+constexpr uint32_t TMEM_COLS = 256;  // 2 rows x 16 p2 x (4 hi + 4 lo) words per lane
+
+// Column of tensor memory holding a thread's eight words (hi 0-3, lo 4-7) for (row slot rl, p2).
+__device__ __forceinline__ uint32_t tcol(int rl, int p2) { return uint32_t((rl * 16 + p2) * 8); }
+
+// d += A B (float32 accumulator in and out)
+__device__ __forceinline__ void mma16816_acc(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                             uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// (v0, v1) as float16x2 pairs hi + lo
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(v0, v1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(v0 - hf.x, v1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                 "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+// Loads are asynchronous: the registers are valid after this wait, which
+// names them so that the compiler does not read them earlier.
+__device__ __forceinline__ void tmem_wait_ld8(uint32_t (&u)[8], uint32_t (&v)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]),
+                 "+r"(u[6]), "+r"(u[7]), "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]),
+                 "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+                   taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+               "r"(v[7])
+               : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    preprocess_d4096_tc32_kernel(const PreArgs a, const __grid_constant__ CUtensorMap tmap) {
+  constexpr int64_t B = D / 2 + 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* E = smem;
+  unsigned char* Fw = smem + E_BYTES + (threadIdx.x >> 5) * F_WARP;  // this warp's F
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + OFF_SLOT);
+  uint32_t* rmax = reinterpret_cast<uint32_t*>(smem + OFF_RMAX);  // row maxima (float bits)
+  float* rsc = reinterpret_cast<float*>(smem + OFF_RSC);          // 2^-e_r
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int quarter = warp & 3, pq = warp >> 2;  // lane quarter of tensor memory; p2 quarter
+  const bool aligned = (smem_addr(smem) & 1023u) == 0;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  const uint32_t tlane = tmem + (uint32_t(quarter * 32) << 16);
+  if (tid == 0 && !aligned) set_status(a.status, kStatusBadIndex);
+
+  // A fragments (rows g, g+8; columns 2q, 2q+1, 2q+8, 2q+9) of W_16 and of 4 I.
+  uint32_t aw[4], ai[4];
+  {
+    const int rr[4] = {g, g + 8, g, g + 8};
+    const int cc[4] = {2 * q, 2 * q, 2 * q + 8, 2 * q + 8};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float w0 = (__popc(rr[e] & cc[e]) & 1) ? -1.f : 1.f;
+      const float w1 = (__popc(rr[e] & (cc[e] + 1)) & 1) ? -1.f : 1.f;
+      aw[e] = pack_f16x2(w0, w1);
+      ai[e] = pack_f16x2(rr[e] == cc[e] ? 4.f : 0.f, rr[e] == cc[e] + 1 ? 4.f : 0.f);
+    }
+  }
+
+  const ItemRange ir = item_range(blockIdx.x, gridDim.x, a.group, a.num_tiles, B);
+  // Step (i) of Lemma 6 in registers, as in preprocess_d4096_tc_kernel: the
+  // warp's p2 quarter needs two sign words per p2, requested for the next
+  // basis while stage 3 of this one runs.
+  const int wsh = 16 * (g & 1) + 2 * q;
+  auto load_words = [&](int b, uint32_t (&wd)[8]) {
+    const uint32_t* srow =
+        a.signs + int64_t(b == D / 2 ? 0 : b) * a.sign_words + 32 * pq + (g >> 1);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      wd[k] = b == D / 2 ? 0u : __ldg(srow + 8 * (k >> 1) + 4 * (k & 1)) >> wsh;
+  };
+  uint32_t wd[8];
+  if (ir.beg < ir.end) load_words(int(ir.beg % B), wd);
+  int64_t cur_tile = -1;
+  for (int64_t item = ir.beg; item < ir.end; ++item) {
+    const int64_t tg = item / B;
+    const int b = int(item - tg * B);
+    const int64_t t = tg * a.group + ir.slot;
+    const int64_t i0 = t * TI;
+    const bool ident = b == D / 2;
+
+    if (t != cur_tile) {  // this warp's share of the tile into its lanes of tensor memory
+      // Row r is loaded by the four warps of lane quarter r mod 4, each for a
+      // quarter of p, scaled by 2^e_r (|e_r| <= 126) and split into hi + lo.
+      __syncthreads();  // every warp is done with the previous tile's row data
+      if (tid < TI) rmax[tid] = 0u;
+      __syncthreads();
+#pragma unroll 1
+      for (int rl = 0; rl < 2; ++rl) {
+        const int64_t row = i0 + quarter + 4 * rl;
+        float mx = 0.f;
+        if (row < a.m) {
+          const float* arow = a.A + row * a.lda;
+          for (int64_t p = 1024 * pq + lane; p < 1024 * pq + 1024 && p < a.n; p += 32)
+            mx = fmaxf(mx, fabsf(arow[p]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(&rmax[quarter + 4 * rl], __float_as_uint(mx));
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int rl = 0; rl < 2; ++rl) {
+        const int r = quarter + 4 * rl;
+        const int64_t row = i0 + r;
+        const bool rv = row < a.m;
+        const float* arow = a.A + (rv ? row : 0) * a.lda;
+        int ex = 0;
+        const float mx = __uint_as_float(rmax[r]);
+        if (mx > 0.f) frexpf(mx, &ex);  // mx = f 2^ex, f in [1/2, 1)
+        int e = mx > 0.f ? -ex : 0;
+        e = e > 126 ? 126 : (e < -126 ? -126 : e);
+        const float sc = ldexpf(1.f, e);
+        if (pq == 0 && lane == 0) rsc[r] = ldexpf(1.f, -e);
+#pragma unroll 1
+        for (int p2 = 4 * pq; p2 < 4 * pq + 4; ++p2) {
+          uint32_t v[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int p = p2 * 256 + (g + 8 * (j >> 1)) * 16 + 2 * q + 8 * (j & 1);
+            const float x0 = (rv && p < a.n) ? arow[p] * sc : 0.f;
+            const float x1 = (rv && p + 1 < a.n) ? arow[p + 1] * sc : 0.f;
+            split2(x0, x1, v[j], v[4 + j]);
+          }
+          tmem_st8(tlane + tcol(rl, p2), v);
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      cur_tile = t;
+    }
+
+    __syncthreads();  // every warp is done reading E for the previous item
+
+    // Stages 1 and 2 for this warp's rows (quarter, quarter + 4) and p2
+    // quarter: for each p2 the two rows, with the next p2's words loaded from
+    // tensor memory while these are multiplied.
+    uint32_t A16[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) A16[e] = ident ? ai[e] : aw[e];
+    uint32_t xa[8], xb[8];
+    tmem_ld8(tlane + tcol(0, 4 * pq), xa);
+    tmem_ld8(tlane + tcol(1, 4 * pq), xb);
+    tmem_wait_ld8(xa, xb);
+#pragma unroll 1
+    for (int pl = 0; pl < 4; ++pl) {
+      const int p2 = 4 * pq + pl;
+      // float16x2 sign masks of this p2 from its two words (now wd[0], wd[1]);
+      // they flip hi and lo alike
+      uint32_t mk[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t u = wd[j >> 1] >> (8 * (j & 1));
+        mk[j] = ((u & 1u) << 15) | ((u & 2u) << 30);
+      }
+      uint32_t x[2][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        x[0][e] = xa[e] ^ mk[e & 3];
+        x[1][e] = xb[e] ^ mk[e & 3];
+      }
+      if (pl < 3) {
+        tmem_ld8(tlane + tcol(0, p2 + 1), xa);
+        tmem_ld8(tlane + tcol(1, p2 + 1), xb);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = quarter + 4 * h;
+        float d1a[4], d1b[4];
+        mma16816(d1a, A16, x[h][0], x[h][1]);  // [w0][p1 0..7]
+        mma16816_acc(d1a, A16, x[h][4], x[h][5]);
+        mma16816(d1b, A16, x[h][2], x[h][3]);  // [w0][p1 8..15]
+        mma16816_acc(d1b, A16, x[h][6], x[h][7]);
+        uint32_t bh[4], bl[4];
+        split2(d1a[0], d1a[1], bh[0], bl[0]);
+        split2(d1b[0], d1b[1], bh[1], bl[1]);
+        split2(d1a[2], d1a[3], bh[2], bl[2]);
+        split2(d1b[2], d1b[3], bh[3], bl[3]);
+        float d2a[4], d2b[4];
+        mma16816(d2a, A16, bh[0], bh[1]);  // w0 0..7
+        mma16816_acc(d2a, A16, bl[0], bl[1]);
+        mma16816(d2b, A16, bh[2], bh[3]);  // w0 8..15
+        mma16816_acc(d2b, A16, bl[2], bl[3]);
+        uint32_t eh[4], el[4];
+        split2(d2a[0], d2a[1], eh[0], el[0]);
+        split2(d2a[2], d2a[3], eh[1], el[1]);
+        split2(d2b[0], d2b[1], eh[2], el[2]);
+        split2(d2b[2], d2b[3], eh[3], el[3]);
+        // [w1][w0] -> E[plane][r][w1][p2][w0 half ^ swizzle]; matrix i = (w1 half i&1, w0 half i>>1)
+        const int mi = lane >> 3, mj = lane & 7;
+        const int w1 = mj + 8 * (mi & 1), wh = (mi >> 1) ^ ((p2 >> 2) & 1);
+        const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
+        stmatrix_x4(addr, eh[0], eh[1], eh[2], eh[3]);
+        stmatrix_x4(addr + E_PLANE, el[0], el[1], el[2], el[3]);
+      }
+      if (pl < 3) tmem_wait_ld8(xa, xb);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wd[k] = wd[k + 2];
+    }
+    // the words of the next basis, used by its stages 1-2
+    if (item + 1 < ir.end) load_words(b + 1 == int(B) ? 0 : b + 1, wd);
+    __syncthreads();  // E holds stages 1-2 of all 8 rows
+
+    // Stage 3: warp handles w1 = warp, 8 rows, one half of w0 at a time.
+    const int w1 = warp;
+    const bool swp = g & 1;
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[TI][4];
+#pragma unroll
+      for (int r = 0; r < TI; ++r) {
+        // lanes 0-15 address p2 = lane & 15 of the w0 half hh (the 16-byte
+        // half hh ^ swizzle); the other lanes' addresses are unused
+        const int p2 = lane & 15, wh = hh ^ ((p2 >> 2) & 1);
+        const uint32_t addr = smem_addr(E + r * E_ROW + w1 * E_W1 + p2 * 32 + wh * 16);
+        uint32_t mh[2], ml[2];
+        ldmatrix_x2_trans(addr, mh);
+        ldmatrix_x2_trans(addr + E_PLANE, ml);
+        mma16816(v[r], A16, mh[0], mh[1]);  // [w2][w0 8 hh .. 8 hh + 7]
+        mma16816_acc(v[r], A16, ml[0], ml[1]);
+        const float s = rsc[r];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[r][e] *= s;
+      }
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      __syncwarp();  // the previous TMA store has read this warp's F
+      // position pos: w2 = g + 8 (pos >> 1), w0 = 8 hh + 2q + (pos & 1).  F is
+      // [w2][w0 - 8 hh][row] (32-byte rows) under the tensor map's 32-byte
+      // swizzle: rows 4 r4 .. 4 r4 + 3 of (w2, w0') sit in the 16-byte half
+      // r4 ^ (bit 2 of w0').  Odd-g lanes store the positions of a pair in the
+      // other order, so a quarter-warp covers all eight bank slots.
+#pragma unroll
+      for (int r4 = 0; r4 < 2; ++r4) {
+#pragma unroll
+        for (int pos = 0; pos < 4; ++pos) {
+          const int ps = swp ? pos ^ 1 : pos;
+          const int w2 = g + 8 * (pos >> 1), w0 = 2 * q + (ps & 1);
+          const int half = r4 ^ ((w0 >> 2) & 1);
+          uint4 val;
+          val.x = __float_as_uint(swp ? v[4 * r4][pos ^ 1] : v[4 * r4][pos]);
+          val.y = __float_as_uint(swp ? v[4 * r4 + 1][pos ^ 1] : v[4 * r4 + 1][pos]);
+          val.z = __float_as_uint(swp ? v[4 * r4 + 2][pos ^ 1] : v[4 * r4 + 2][pos]);
+          val.w = __float_as_uint(swp ? v[4 * r4 + 3][pos ^ 1] : v[4 * r4 + 3][pos]);
+          *reinterpret_cast<uint4*>(Fw + (w2 * 8 + w0) * (TI * 4) + half * 16) = val;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && aligned) {
+        tma_store_4d(&tmap, smem_addr(Fw), int(i0), 8 * hh, w1, b * 16);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+}  // namespace tc32
+
+int launch_d4096_tc32(const Plan& p) {
+  tc::EncodeTiledFn enc = tc::encoder();
+  if (enc == nullptr) return KERDOCK_ERR_UNSUPPORTED;
+  // R[b][w][i] (float32) as [(b, w2)][w1][w0][i]: box 8 rows x 8 w0 x 1 w1 x 16 w2
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {cuuint64_t(p.ldr), 16, 16, cuuint64_t(p.B) * 16};
+  const cuuint64_t strides[3] = {cuuint64_t(p.ldr) * 4, cuuint64_t(p.ldr) * 64,
+                                 cuuint64_t(p.ldr) * 1024};
+  const cuuint32_t box[4] = {tc32::TI, 8, 1, 16};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p.repr, dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return KERDOCK_ERR_UNSUPPORTED;
+  auto kern = tc32::preprocess_d4096_tc32_kernel;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(tc32::SMEM)));
+  PreArgs a;
+  a.A = p.A;
+  a.lda = p.lda;
+  a.m = p.m;
+  a.n = p.n;
+  a.signs = p.signs();
+  a.sign_words = p.sign_words;
+  a.R = p.repr;
+  a.ldr = p.ldr;
+  a.status = p.status();
+  a.num_tiles = (p.ldr + tc32::TI - 1) / tc32::TI;
+  // groups of up to 16 CTAs (one per SM) on adjacent 8-row tiles
+  a.group = pick_group(a.num_tiles, 16);
+  int64_t ngrp = int64_t(p.num_sms) / a.group;
+  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
+  if (ngrp > items) ngrp = items;
+  if (ngrp < 1) ngrp = 1;
+  kern<<<unsigned(ngrp * a.group), tc32::THREADS, tc32::SMEM, p.stream>>>(a, map);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
 // d = 1024, float32 or bfloat16 representation.  Write p = 32 s + k and
 // w = 32 w_hi + w_lo, so W_1024 = W_32 (over s) (x) W_32 (over k).  The CTA's
 // 16-row tile of A lives in tensor memory: thread (row pair rp, source s)
@@ -1752,7 +2122,7 @@ int launch_typed(const Plan& p) {
       return launch_d1024<OutT>(p);
     case 12:
       if (sizeof(OutT) == 2) return launch_d4096_tc(p);
-      return launch_d4096<OutT>(p);
+      return launch_d4096_tc32(p);
     default: return KERDOCK_ERR_UNSUPPORTED;
   }
 }

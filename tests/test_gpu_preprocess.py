@@ -96,12 +96,12 @@ def test_preprocess_n1024_sampled_bases(K):
     plan.close()
 
 
-@pytest.mark.parametrize("m,n,dtype", [(40, 4096, "f32"), (33, 3000, "f32"), (70, 2048, "bf16"),
-                                     (37, 4096, "bf16")])
+@pytest.mark.parametrize("m,n,dtype", [(40, 4096, "f32"), (33, 3000, "f32"), (37, 4096, "f32"),
+                                     (70, 2048, "bf16"), (37, 4096, "bf16")])
 def test_preprocess_d4096_parity(K, m, n, dtype):
-    # d = 4096 (k = 12): the four-CTA cluster kernel (float32) or the
-    # tensor-core kernel (bfloat16); the oracle checks a spread of bases,
-    # including the identity basis d/2 = 2048.
+    # d = 4096 (k = 12): the tensor-core kernels (float32 as float16 hi + lo
+    # pairs, bfloat16 from float16 stages); the oracle checks a spread of
+    # bases, including the identity basis d/2 = 2048.
     torch = torch_cuda()
     rng = np.random.default_rng(m * 31 + n)
     A = rng.standard_normal((m, n)).astype(np.float32)
@@ -125,7 +125,13 @@ def test_preprocess_d4096_parity(K, m, n, dtype):
         Rg = Rg[:, :m]
         scale = np.abs(Rref[t_]).max()
         if dtype == "f32":
-            assert np.abs(Rg - Rref[t_]).max() <= 1e-4 * scale, b
+            # per entry within 1e-5 of its row's norm, the scale of the
+            # float32 transform's own error (hi + lo keeps 22 bits per stage)
+            norms = np.linalg.norm(f32(A), axis=1)
+            err = np.abs(Rg - Rref[t_])
+            worst = max(worst, float((err / np.maximum(norms, 1e-300)[None, :]).max()))
+            assert (err <= 1e-5 * norms[None, :] + 1e-30).all(), b
+            assert err.max() <= 1e-4 * scale, b
         else:
             norms = np.linalg.norm(f32(A), axis=1)
             err = np.abs(Rg - Rref[t_])
@@ -134,6 +140,8 @@ def test_preprocess_d4096_parity(K, m, n, dtype):
             assert (err <= repr_bound_bf16(Rref[t_], norms, 12) + 1e-6 * scale).all(), b
     if dtype == "bf16":
         print(f"d=4096 bf16 tensor cores m={m} n={n}: worst (err - 2^-8|R|)/||a_i|| = {worst:.3e}")
+    else:
+        print(f"d=4096 f32 tensor cores m={m} n={n}: worst err/||a_i|| = {worst:.3e}")
     plan.close()
 
 
