@@ -864,6 +864,7 @@ def run_profile_case(args):
     launches first), so a profiler can skip the warm-up launches and capture
     one or two launches that end by themselves.
       profile_pre4096  kerdock_preprocess, m = 256, n = 4096, bfloat16 (4.3 GB)
+      profile_pre4096_f32  kerdock_preprocess, m = 128, n = 4096, float32 (4.3 GB)
       profile_q4096    kerdock_apply, m = 256, n = 4096, bfloat16, 512 queries,
                        J = 1000, K = 2
       profile_pre1024  kerdock_preprocess, m = n = 1024, float32 (2.15 GB)
@@ -879,11 +880,13 @@ def run_profile_case(args):
     if case in ("profile_pre1024", "profile_pre1024_bf16"):
         m = n = 1024
         dtype = "bf16" if case.endswith("bf16") else "f32"
+    elif case == "profile_pre4096_f32":
+        m, n, dtype = 128, 4096, "f32"
     else:
         m, n, dtype = 256, 4096, "bf16"
     A = (torch.randn(m, n, device="cuda") / n ** 0.5).contiguous()
     plan = K.KerdockPlan(m, n, J=1000, K=2, S=32, dtype=dtype)
-    if case in ("profile_pre4096", "profile_pre1024", "profile_pre1024_bf16"):
+    if case in ("profile_pre4096", "profile_pre4096_f32", "profile_pre1024", "profile_pre1024_bf16"):
         for _ in range(args.steps + 2):
             plan.preprocess(A)
     else:
@@ -1080,7 +1083,8 @@ def main():
                     help="skip the precision / batching / learned sub-objects of the main line")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "n4096_bf16", "mixed_batch", "n2048_learned", "fig1",
-                             "n1024_shared", "profile_pre4096", "profile_q4096",
+                             "n1024_shared", "profile_pre4096", "profile_pre4096_f32",
+                             "profile_q4096",
                              "profile_pre1024", "profile_pre1024_bf16"])
     ap.add_argument("--_oracle_sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--_oracle_steps", type=int, default=None, help=argparse.SUPPRESS)

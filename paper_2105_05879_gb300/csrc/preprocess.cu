@@ -22,12 +22,12 @@
 //    and stores 8-byte row pairs (streaming stores).  Groups of 16 CTAs own
 //    adjacent tiles and walk the bases in step, so every 128-byte line of an
 //    output row R[b][w][.] is completed by two CTAs at about the same time.
-//  * d = 4096, float32 (preprocess_d4096_kernel): a 4-CTA cluster per 32-row
-//    tile, each CTA holding a quarter of p; the second half of the stages
-//    combines sources pushed over distributed shared memory.
-//  * d = 4096, bfloat16 (preprocess_d4096_tc_kernel, precision form): the
-//    three 16-point stages on the tensor cores.
-#include <cooperative_groups.h>
+//  * d = 1024, bfloat16 (preprocess_d1024_tc_kernel): W_16 (x) W_16 (x) W_4 on
+//    the tensor cores, 64-row tiles.
+//  * d = 4096, bfloat16 (preprocess_d4096_tc_kernel, precision form) and
+//    float32 (preprocess_d4096_tc32_kernel): the three 16-point stages of
+//    W_16 (x) W_16 (x) W_16 on the tensor cores, float32 as float16 hi + lo
+//    operand pairs.
 #include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime)
 
 #include <cuda_fp16.h>
@@ -293,233 +293,11 @@ __global__ void __launch_bounds__(PreCfg<LOG_D>::THREADS, 2)
   }
 }
 
-// ---------------------------------------------------------------------------
-// d = 4096: a cluster of four CTAs shares one tile of TI rows (TI = 32: the
-// representation's rows then get 64-byte (bfloat16) or 128-byte (float32)
-// runs per output row).  Write p = 1024 q + 64 s + j: CTA q keeps the quarter
-// p in [1024 q, 1024 (q+1)) of the tile in shared memory; its thread (r, s)
-// holds row r's 64 values of source s in registers and runs the six butterfly
-// stages over j there (phase 1).  Output w = 64 w_hi + w_lo: the w_lo of the
-// phase-1 results are spread over the cluster, CTA c taking w_lo in
-// [16 c, 16 c + 16), and each CTA's thread (r, w_lo) combines the 64 sources
-// (q, s) of its column in two rounds of 32 (s < 8, s >= 8), five stages per
-// round plus one combining stage (phase 2).  Each round, every thread of the
-// sending half writes its values straight into the owners' exchange buffers
-// over distributed shared memory; split cluster barriers separate writing from
-// reading, and the "buffer free" half of each barrier pair overlaps with the
-// next round's arithmetic.
-// ---------------------------------------------------------------------------
-namespace cg = cooperative_groups;
-
-template <int TI>
-struct Big {
-  static constexpr int D = 4096, Q = 1024, CL = 4;  // CTAs per cluster, p per CTA
-  static constexpr int NS = 16, RG = 64;             // sources per CTA, values per source
-  static constexpr int THREADS = TI * NS;            // thread (r, s) = (tid % TI, tid / TI)
-  static constexpr int WLC = RG / CL;                // w_lo per CTA: 16
-  static constexpr int HS = NS / 2;                  // sources per CTA per round: 8
-  static constexpr int RSRC = HS * CL;               // sources per round: 32
-  static constexpr int AST = Q + 4;                  // A-tile row stride (floats)
-  static constexpr int XSRC = WLC * TI + (TI == 32 ? 0 : 16);  // floats per source: [w_lo][row]
-  static constexpr size_t SMEM = size_t(TI) * AST * 4 + size_t(RSRC) * XSRC * 4;
-  static constexpr int MINB = THREADS >= 512 ? 1 : 2;
-  static_assert(THREADS <= 1024 && TI % 8 == 0, "tile");
-};
-
-__device__ __forceinline__ void cluster_arrive() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait() {
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ void store_one(T* dst, float v);
-template <>
-__device__ __forceinline__ void store_one<float>(float* dst, float v) {
-  asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(dst), "f"(v) : "memory");
-}
-template <>
-__device__ __forceinline__ void store_one<__nv_bfloat16>(__nv_bfloat16* dst, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  asm volatile("st.global.cs.b16 [%0], %1;" ::"l"(dst),
-               "h"(*reinterpret_cast<const unsigned short*>(&h))
-               : "memory");
-}
-
-template <typename OutT, int TI>
-__global__ void __launch_bounds__(Big<TI>::THREADS, Big<TI>::MINB)
-    preprocess_d4096_kernel(const PreArgs a) {
-  using C = Big<TI>;
-  constexpr int64_t B = C::D / 2 + 1;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int q = int(cluster.block_rank());
-  extern __shared__ __align__(16) float smem[];
-  float* At = smem;                            // [TI][AST]: this CTA's quarter of the tile
-  float* X = smem + size_t(TI) * C::AST;       // [32 sources][16 w_lo][TI rows]
-  float* Xc[C::CL];
-#pragma unroll
-  for (int c = 0; c < C::CL; ++c) Xc[c] = cluster.map_shared_rank(X, c);
-  OutT* R = static_cast<OutT*>(a.R);
-  const int tid = threadIdx.x;
-  const int r = tid % TI, s = tid / TI;  // phase 1: (row, source); phase 2: (row, w_lo in CTA)
-  const float sqrt_d = 64.f;
-
-  const ItemRange ir =
-      item_range(blockIdx.x / C::CL, gridDim.x / C::CL, a.group, a.num_tiles, B);
-  int64_t cur_tile = -1;
-  cluster_arrive();  // pairs with the first "exchange buffers free" wait
-
-  for (int64_t item = ir.beg; item < ir.end; ++item) {
-    const int64_t tg = item / B;
-    const int b = int(item - tg * B);
-    const int64_t t = tg * a.group + ir.slot;
-    const int64_t i0 = t * TI;
-    const bool ident = b == C::D / 2;
-    if (t != cur_tile) {
-      __syncthreads();  // the previous tile's phase 1 is done everywhere in this CTA
-      for (int idx = tid; idx < TI * C::Q; idx += C::THREADS) {
-        const int i = idx / C::Q, pq = idx % C::Q;
-        const int64_t gp = int64_t(q) * C::Q + pq;
-        float v = 0.f;
-        if (i0 + i < a.m && gp < a.n) v = a.A[(i0 + i) * a.lda + gp];
-        At[i * C::AST + pq] = v;
-      }
-      cur_tile = t;
-      __syncthreads();
-    }
-
-    // Phase 1: step (i) of Lemma 6 from the source's two sign words, then the
-    // six stages over j in registers.
-    uint32_t wd[2] = {0u, 0u};
-    if (!ident) {
-      const uint32_t* srow = a.signs + int64_t(b) * a.sign_words + q * (C::Q / 32) + s * 2;
-      wd[0] = __ldg(srow);
-      wd[1] = __ldg(srow + 1);
-    }
-    float2 v[C::RG / 2];
-#pragma unroll
-    for (int j = 0; j < C::RG; j += 4) {
-      float4 x4 = *reinterpret_cast<const float4*>(&At[r * C::AST + s * C::RG + j]);
-      if (!ident) {
-        uint32_t f[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          f[e] = (wd[(j + e) >> 5] << (31 - ((j + e) & 31))) & 0x80000000u;
-        x4.x = __uint_as_float(__float_as_uint(x4.x) ^ f[0]);
-        x4.y = __uint_as_float(__float_as_uint(x4.y) ^ f[1]);
-        x4.z = __uint_as_float(__float_as_uint(x4.z) ^ f[2]);
-        x4.w = __uint_as_float(__float_as_uint(x4.w) ^ f[3]);
-      }
-      v[j / 2] = make_float2(x4.x, x4.y);
-      v[j / 2 + 1] = make_float2(x4.z, x4.w);
-    }
-    if (!ident) fwht_pairs<C::RG / 2>(v);
-
-    // Phase 2 in two rounds of 32 sources (q', s') with s' / 8 == round.
-    float2 z[2][C::RSRC / 2];  // per round: pairs (source k, source k + 16)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      cluster_wait();  // every CTA is done reading the exchange buffers
-      if ((s >> 3) == e) {
-        const int src = q * C::HS + (s & 7);
-#pragma unroll
-        for (int j = 0; j < C::RG; ++j) {
-          const float val = (j & 1) ? v[j / 2].y : v[j / 2].x;
-          Xc[j / C::WLC][src * C::XSRC + (j % C::WLC) * TI + r] = val;
-        }
-      }
-      cluster_arrive();  // this round's values are written
-      cluster_wait();    // ... by every CTA of the cluster
-#pragma unroll
-      for (int k = 0; k < C::RSRC / 2; ++k)
-        z[e][k] = make_float2(X[k * C::XSRC + s * TI + r],
-                              X[(k + C::RSRC / 2) * C::XSRC + s * TI + r]);
-      cluster_arrive();  // done reading; the buffers may be refilled
-      if (!ident) {
-#pragma unroll
-        for (int k = 0; k < C::RSRC / 2; ++k)
-          z[e][k] = make_float2(z[e][k].x + z[e][k].y, z[e][k].x - z[e][k].y);
-        fwht_across<C::RSRC / 2>(z[e]);
-      }
-    }
-
-    // Combine the rounds (source bit s / 8) and store.  Round-local source
-    // k = 8 q' + (s' mod 8) and the round e give w_hi = 16 q' + 8 e + (s' mod 8).
-    const int64_t row = i0 + r;
-    if (row < a.ldr) {
-      OutT* rb = R + (int64_t(b) * C::D + q * C::WLC + s) * a.ldr + row;
-      const int64_t wstride = int64_t(C::RG) * a.ldr;  // one step of w_hi
-#pragma unroll
-      for (int k = 0; k < C::RSRC; ++k) {
-        const float z0 = (k < C::RSRC / 2) ? z[0][k].x : z[0][k - C::RSRC / 2].y;
-        const float z1 = (k < C::RSRC / 2) ? z[1][k].x : z[1][k - C::RSRC / 2].y;
-        float y0, y1;
-        if (ident) {
-          y0 = z0 * sqrt_d;
-          y1 = z1 * sqrt_d;
-        } else {
-          y0 = z0 + z1;
-          y1 = z0 - z1;
-        }
-        const int whi = (k >> 3) * 16 + (k & 7);
-        store_one<OutT>(rb + int64_t(whi) * wstride, y0);
-        store_one<OutT>(rb + int64_t(whi + 8) * wstride, y1);
-      }
-    }
-  }
-  cluster_wait();  // pairs with the last arrive: no CTA leaves while others read its buffers
-}
-
 // Largest power of two <= limit and <= num_tiles (the tile group size G).
 int64_t pick_group(int64_t num_tiles, int64_t limit) {
   int64_t g = 1;
   while (g * 2 <= limit && g * 2 <= num_tiles) g *= 2;
   return g;
-}
-
-template <typename OutT>
-int launch_d4096(const Plan& p) {
-  constexpr int TI = 32;
-  using C = Big<TI>;
-  auto kern = preprocess_d4096_kernel<OutT, TI>;
-  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(C::SMEM)));
-  PreArgs a;
-  a.A = p.A;
-  a.lda = p.lda;
-  a.m = p.m;
-  a.n = p.n;
-  a.signs = p.signs();
-  a.sign_words = p.sign_words;
-  a.R = p.repr;
-  a.ldr = p.ldr;
-  a.status = p.status();
-  a.num_tiles = (p.ldr + TI - 1) / TI;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C::CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(C::THREADS);
-  cfg.dynamicSmemBytes = C::SMEM;
-  cfg.stream = p.stream;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3(C::CL);
-  int clusters = 0;
-  KD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
-  if (clusters < 1) return KERDOCK_ERR_UNSUPPORTED;
-  // groups of up to 4 clusters on adjacent 32-row tiles: 4 x 64 B = two whole
-  // 128-byte lines per output row for bfloat16
-  a.group = pick_group(a.num_tiles, clusters < 4 ? clusters : 4);
-  int64_t ngrp = clusters / a.group;
-  const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
-  if (ngrp > items) ngrp = items;
-  cfg.gridDim = dim3(unsigned(ngrp * a.group * C::CL));
-  KD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
-  return KERDOCK_OK;
 }
 
 template <int LOG_D, typename OutT>
