@@ -776,8 +776,10 @@ int launch_d4096_tc(const Plan& p) {
   a.ldr = p.ldr;
   a.status = p.status();
   a.num_tiles = (p.ldr + tc::TI - 1) / tc::TI;
-  // groups of up to 16 CTAs (one per SM) on adjacent 16-row tiles
-  a.group = pick_group(a.num_tiles, 16);
+  // groups of up to 8 CTAs (one per SM) on adjacent 16-row tiles: 152 SMs
+  // are 19 such groups (groups of 16 would leave 8 SMs idle; a store-only
+  // probe of the pattern runs as fast with groups of 4 as of 16)
+  a.group = pick_group(a.num_tiles, 8);
   int64_t ngrp = int64_t(p.num_sms) / a.group;
   const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
   if (ngrp > items) ngrp = items;
@@ -1146,8 +1148,9 @@ int launch_d4096_tc32(const Plan& p) {
   a.ldr = p.ldr;
   a.status = p.status();
   a.num_tiles = (p.ldr + tc32::TI - 1) / tc32::TI;
-  // groups of up to 16 CTAs (one per SM) on adjacent 8-row tiles
-  a.group = pick_group(a.num_tiles, 16);
+  // groups of up to 8 CTAs (one per SM) on adjacent 8-row tiles, as for the
+  // bfloat16 kernel
+  a.group = pick_group(a.num_tiles, 8);
   int64_t ngrp = int64_t(p.num_sms) / a.group;
   const int64_t items = ((a.num_tiles + a.group - 1) / a.group) * p.B;
   if (ngrp > items) ngrp = items;
