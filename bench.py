@@ -520,7 +520,7 @@ def run_batch(args, K, torch, peak):
                               seed=77 + pi, index=r))
             truth.append(np.nonzero(np.abs(z) >= eps)[0])
     batch = K.KerdockBatch(specs, graph=True)
-    rk, cr, tune_ms = tuning.autotune_batch(batch, reps=2, use_cache=False)
+    rk, cr, tune_ms = tuning.autotune_batch(batch, reps=5, use_cache=False)
     for _ in range(args.warmup):
         batch.launch()
     batch.sync()

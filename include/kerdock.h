@@ -225,12 +225,14 @@ int kerdock_batch_create(kerdock_batch_t* batch, const kerdock_query_t* queries,
 int kerdock_batch_launch(kerdock_batch_t batch);
 
 /* Set the query kernel's ring geometry for this batch: ring_kb KiB of shared
- * memory for representation rows and crows rows per ring chunk (1, 2 or 4;
- * 0 = default for either); re-captures the graph. */
+ * memory for representation rows and crows rows per ring chunk (1, 2, 4 or
+ * 8; 0 = default for either); re-captures the graph.  A geometry whose ring
+ * holds too few chunks for the kernel's coefficient warps is refused with
+ * KERDOCK_ERR_UNSUPPORTED. */
 int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t crows);
 
 /* Autotuner: time reps launches of every candidate geometry (ring 64/96/128/
- * 160 KiB x 1/2/4 rows per chunk), keep the fastest and report it. */
+ * 160 KiB x 1/2/4/8 rows per chunk), keep the fastest and report it. */
 int kerdock_batch_tune(kerdock_batch_t batch, int32_t reps, int32_t* ring_kb, int32_t* crows,
                        float* best_ms);
 

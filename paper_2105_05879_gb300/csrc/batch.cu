@@ -20,7 +20,7 @@ namespace {
 
 // Candidate ring geometries tried by the autotuners.
 const int kTuneRingKb[] = {64, 96, 128, 160};
-const int kTuneCrows[] = {1, 2, 4};
+const int kTuneCrows[] = {1, 2, 4, 8};
 
 struct Timer {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -343,8 +343,8 @@ int kerdock_batch_destroy(kerdock_batch_t batch) {
 }
 
 int kerdock_plan_set_tuning(kerdock_plan_t plan, int32_t ring_kb, int32_t crows) {
-  if (plan == nullptr || ring_kb < 0 || crows < 0 || (crows != 0 && crows != 1 && crows != 2 &&
-                                                      crows != 4))
+  if (plan == nullptr || ring_kb < 0 || crows < 0 ||
+      (crows != 0 && crows != 1 && crows != 2 && crows != 4 && crows != 8))
     return KERDOCK_ERR_INVALID_ARG;
   kd::Plan& p = plan->p;
   kd::Tuning tu;

@@ -28,7 +28,7 @@ enum : uint32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadIndex = 2 };
 // Tunable geometry of the query kernel's row ring (0 = library default).
 struct Tuning {
   int ring_kb = 0;  // KiB of shared memory for the row ring
-  int crows = 0;    // rows per ring chunk (1, 2 or 4)
+  int crows = 0;    // rows per ring chunk (1, 2, 4 or 8)
 };
 
 struct Plan {
@@ -70,7 +70,7 @@ struct Plan {
 // byte offsets of the dynamic shared-memory regions.
 struct LaunchCfg {
   int nchunk;            // ring chunks; a chunk holds crows consecutive samples of one query
-  int crows;             // rows per chunk (1, 2 or 4)
+  int crows;             // rows per chunk (1, 2, 4 or 8)
   int pgroup;            // chunks the producer fills per warp instruction (pgroup * crows <= 32)
   uint32_t slot_bytes;   // ring slot stride: the largest row of the launch
   int64_t xpad;          // floats per x buffer
