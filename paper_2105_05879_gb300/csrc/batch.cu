@@ -108,7 +108,7 @@ void destroy_graph(kerdock_batch_s* b) {
 // Set the ring geometry and (re)capture the launch into a graph when asked.
 int configure(kerdock_batch_s* b, const kd::Tuning& tu) {
   kd::LaunchCfg cfg{};
-  if (!kd::make_cfg(b->dims, tu, b->means_in_smem, cfg)) return KERDOCK_ERR_UNSUPPORTED;
+  if (!kd::make_cfg(b->dims, tu, b->means_in_smem, cfg, true)) return KERDOCK_ERR_UNSUPPORTED;
   cfg.means_gmem = b->means_in_smem ? nullptr : b->d_means;
   cfg.status = b->status;
   b->cfg = cfg;

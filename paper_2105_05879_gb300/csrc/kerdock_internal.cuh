@@ -114,7 +114,9 @@ size_t align_up(size_t v, size_t al);
 void dims_add(Dims& dm, const Plan& p, int64_t K, int64_t S);
 Dims plan_dims(const Plan& p);  // one plan's dims with its single-plan kernel's split
 bool means_fit_smem(const Dims& dm);
-bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c);
+// packed: the batch kernel, whose chunks may pack several small rows per slot
+bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c,
+              bool packed = false);
 QueryDesc plan_desc(const Plan& p);
 void set_query_params(QueryDesc& d, int64_t J, int64_t K, int64_t S, float eps, uint64_t seed,
                       int flags);
@@ -200,6 +202,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Raise the phase's expected transaction bytes without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
                "r"(bytes)
                : "memory");
 }

@@ -29,6 +29,7 @@
 // All hand-offs are mbarrier phases; every wait is bounded and a timeout sets
 // the plan's status word and ends the CTA.
 #include <mutex>
+#include <type_traits>
 
 #include "kerdock_internal.cuh"
 
@@ -70,7 +71,8 @@ struct Roles {
   static constexpr int kGatherWarps = kFirstFinalWarp - kFirstGatherWarp;
   static constexpr int kGatherThreads = kGatherWarps * 32;
 };
-constexpr int kMaxSlots = 128;  // ring rows
+constexpr int kMaxSlots = 128;  // ring slots
+constexpr int kMaxChunkRows = 32;  // rows of one packed chunk: one producer lane each
 constexpr int kMaxChunks = 64;
 // > every CW: each coefficient warp steps CW chunks and starts at chunk cw < CW
 // The ring must hold more chunks than the kernel's coefficient warps: each
@@ -345,17 +347,30 @@ __device__ __forceinline__ void init_barriers(Shared& sh, const LaunchCfg& c) {
   __syncthreads();
 }
 
+// Rows of a query per ring slot in a batch launch.  A batch's slot is as large
+// as its largest row; a query whose rows are at most half of it packs 2, 4,
+// ... rows into each slot (a chunk then carries crows * rows_per_slot
+// consecutive samples, at most kMaxChunkRows), so the small rows of a mixed
+// batch keep more bytes in flight and pay a chunk's barriers once per several
+// rows.  Single-plan launches keep one row per slot (the slot is the row),
+// and their code is compiled without the packed paths.
+__device__ __forceinline__ int rows_per_slot(const QueryDesc& qd, const LaunchCfg& cfg) {
+  int rps = 1;
+  while (2u * uint32_t(rps) * qd.row_bytes <= cfg.slot_bytes &&
+         2 * rps * cfg.crows <= kMaxChunkRows)
+    rps *= 2;
+  return rps;
+}
+
 // ---------------------------------------------------------------- producer
 template <class Seq>
 __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Regions& rg, Shared& sh) {
+  constexpr bool kPack = std::is_same<Seq, BatchSeq>::value;
   const int lane = threadIdx.x & 31;
   const int CR = cfg.crows;
   const uint32_t nchunk = uint32_t(cfg.nchunk);
   uint32_t cslot = 0, cphase = 0;  // ring chunk of the next chunk to fill and its phase
   uint64_t filled = 0;             // chunks filled so far
-  const int ci = lane / CR, r = lane % CR;
-  // the CR lanes that fill one chunk
-  const uint32_t chunk_mask = ((CR == 32 ? 0u : (1u << CR)) - 1u) << (ci * CR);
   const int64_t nq = seq.size();
   for (int64_t qs = 0; qs < nq; ++qs) {
     const QueryDesc qd = seq.get(qs);
@@ -366,10 +381,16 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
     for (int64_t p = lane; p < cfg.xpad; p += 32) xq[p] = p < qd.n ? qd.x[p] : 0.f;
     __syncwarp();
     if (lane == 0) mbar_arrive(&sh.x_full[xb]);
-    const int64_t qchunks = (qd.N + CR - 1) / CR;
+    // RPC rows per chunk (a power of two), one lane each; pg chunks per step
+    const int rps = kPack ? rows_per_slot(qd, cfg) : 1, RPC = CR * rps;
+    const int pg = cfg.pgroup < 32 / RPC ? cfg.pgroup : 32 / RPC;
+    const int ci = lane / RPC, r = lane % RPC;
+    // the RPC lanes that fill one chunk
+    const uint32_t chunk_mask = RPC == 32 ? 0xffffffffu : ((1u << RPC) - 1u) << (ci * RPC);
+    const int64_t qchunks = (qd.N + RPC - 1) / RPC;
     const unsigned char* R = static_cast<const unsigned char*>(qd.R);
-    for (int64_t c0 = 0; c0 < qchunks; c0 += cfg.pgroup) {
-      const int cnt = int(qchunks - c0 < cfg.pgroup ? qchunks - c0 : cfg.pgroup);
+    for (int64_t c0 = 0; c0 < qchunks; c0 += pg) {
+      const int cnt = int(qchunks - c0 < pg ? qchunks - c0 : pg);
       bool ok = true;
       uint32_t cs = cslot + uint32_t(ci), ph = cphase;
       if (cs >= nchunk) {
@@ -381,19 +402,32 @@ __device__ void producer_role(const Seq& seq, const LaunchCfg& cfg, const Region
       // the lanes of one chunk arm it together or not at all, so an abort
       // leaves no chunk partly armed; each armed chunk records its fill number
       ok = __all_sync(chunk_mask, ok);
+      // Row r of a chunk goes to byte r * row_bytes of the chunk's CR slots.
+      // With one row per slot each lane arrives with its own bytes; with
+      // packed slots every copy's bytes are expected before any arrival and
+      // the first lane of each slot arrives once (a slot past the end of the
+      // query arrives empty), so the CR arrivals close the phase only when
+      // every row has landed.
       if (ci < cnt && ok) {
         if (r == 0) sh.armed[cs] = uint32_t(filled + uint64_t(ci) + 1);
-        const int64_t j = (c0 + ci) * CR + r;
+        const int64_t j = (c0 + ci) * RPC + r;
         if (j < qd.N) {
           const uint64_t ell =
               sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j), uint64_t(qd.L));
           if (qd.ells_out) qd.ells_out[j] = int64_t(ell);
-          mbar_arrive_expect_tx(&sh.row_full[cs], qd.row_bytes);
-          bulk_g2s(rg.ring + (size_t(cs) * CR + r) * cfg.slot_bytes,
+          if (rps == 1)
+            mbar_arrive_expect_tx(&sh.row_full[cs], qd.row_bytes);
+          else
+            mbar_expect_tx(&sh.row_full[cs], qd.row_bytes);
+          bulk_g2s(rg.ring + size_t(cs) * CR * cfg.slot_bytes + size_t(r) * qd.row_bytes,
                    R + int64_t(ell) * qd.row_bytes, qd.row_bytes, &sh.row_full[cs]);
-        } else {
+        } else if (rps == 1) {
           mbar_arrive(&sh.row_full[cs]);  // past the end of the query: empty row
         }
+      }
+      if (kPack && rps > 1) {
+        __syncwarp();
+        if (ci < cnt && ok && r % rps == 0) mbar_arrive(&sh.row_full[cs]);
       }
       if (__any_sync(0xffffffffu, !ok)) return;
       filled += uint64_t(cnt);
@@ -413,7 +447,11 @@ struct CoefState {
   uint64_t cbase;   // global chunk counter of the current query's first chunk
 };
 
-template <bool XREG, int CW>
+// PACK (the batch kernel): a chunk holds crows * rows_per_slot samples, up to
+// kMaxChunkRows, computed four at a time with each lane keeping its own
+// sample's coefficient; the coefficient area has kMaxChunkRows entries per
+// chunk.
+template <bool XREG, int CW, bool PACK>
 __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const LaunchCfg& cfg,
                            const Regions& rg, Shared& sh, const float* xq) {
   const int lane = threadIdx.x & 31;
@@ -425,6 +463,56 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
   float xr[32];
 #pragma unroll
   for (int t = 0; t < 32; ++t) xr[t] = (XREG && t * 32 < cfg.xpad) ? xq[t * 32 + lane] : 0.f;
+  if constexpr (PACK) {
+    const int RPC = CR * rows_per_slot(qd, cfg);
+    const uint64_t cend = st.cbase + uint64_t((qd.N + RPC - 1) / RPC);
+    for (; st.cc < cend; st.cc += CW) {
+      const int64_t j0 = int64_t(st.cc - st.cbase) * RPC;
+      const int cnt = int(qd.N - j0 < RPC ? qd.N - j0 : RPC);
+      // lane s draws sample j0 + s of the chunk and keeps its coefficient
+      uint32_t my_ell = 0;
+      if (lane < cnt)
+        my_ell = uint32_t(
+            sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j0 + lane), uint64_t(qd.L)));
+      float my_c = 0.f;
+      for (int h = 0; h < cnt; h += 4) {
+        uint32_t ell[4];
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2)
+          ell[s2] = __shfl_sync(0xffffffffu, my_ell, h + s2 < cnt ? h + s2 : h);
+        float c[4];
+        if (RPC >= 4)
+          kerdock_coefficients<XREG, 4>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr,
+                                        xq, c);
+        else if (RPC == 2)
+          kerdock_coefficients<XREG, 2>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr,
+                                        xq, c);
+        else
+          kerdock_coefficients<XREG, 1>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, xr,
+                                        xq, c);
+#pragma unroll
+        for (int s2 = 0; s2 < 4; ++s2)
+          if (lane == h + s2) my_c = c[s2];
+      }
+      // the gather warps must be done with this chunk's previous samples
+      if (st.cc >= nchunk && !warp_wait(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg)) return false;
+      if (lane < cnt) {
+        const uint32_t w = my_ell & dmask;
+        if (int64_t(my_ell >> qd.k) == half) my_c = w < qd.n ? qd.sqrt_d * xq[w] : 0.f;
+        rg.coef_s[st.cs * kMaxChunkRows + lane] = my_c;
+        if (qd.coef_out) qd.coef_out[j0 + lane] = my_c;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.coef_full[st.cs]);
+      st.cs += CW;
+      if (st.cs >= nchunk) {
+        st.cs -= nchunk;
+        st.ph ^= 1u;
+      }
+    }
+    st.cbase = cend;
+    return true;
+  }
   const uint64_t cend = st.cbase + uint64_t((qd.N + CR - 1) / CR);
   for (; st.cc < cend; st.cc += CW) {
     const int64_t j0 = int64_t(st.cc - st.cbase) * CR;
@@ -502,13 +590,13 @@ __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& r
     if (!warp_wait(&sh.x_full[xb], uint32_t(qs / kXBufs) & 1u, sh, cfg)) return;
     const float* xq = rg.xbuf + xb * cfg.xpad;
     bool ok;
-    if (XMODE == 0) {
-      ok = coef_query<true, CW>(qd, qs, st, cfg, rg, sh, xq);
-    } else if (XMODE == 1) {
-      ok = coef_query<false, CW>(qd, qs, st, cfg, rg, sh, xq);
-    } else {
-      ok = qd.n <= 1024 ? coef_query<true, CW>(qd, qs, st, cfg, rg, sh, xq)
-                        : coef_query<false, CW>(qd, qs, st, cfg, rg, sh, xq);
+    if constexpr (XMODE == 0) {
+      ok = coef_query<true, CW, false>(qd, qs, st, cfg, rg, sh, xq);
+    } else if constexpr (XMODE == 1) {
+      ok = coef_query<false, CW, false>(qd, qs, st, cfg, rg, sh, xq);
+    } else {  // the batch kernel
+      ok = qd.n <= 1024 ? coef_query<true, CW, true>(qd, qs, st, cfg, rg, sh, xq)
+                        : coef_query<false, CW, true>(qd, qs, st, cfg, rg, sh, xq);
     }
     if (!ok) return;
     __syncwarp();
@@ -517,7 +605,8 @@ __device__ void coef_role(const Seq& seq, const LaunchCfg& cfg, const Regions& r
 }
 
 // ---------------------------------------------------------------- gather
-template <typename RT, int GPT, int CW>
+// PACK (the batch kernel): a chunk holds crows * rows_per_slot rows.
+template <typename RT, int GPT, int CW, bool PACK>
 __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint32_t& ph,
                              const LaunchCfg& cfg, const Regions& rg, Shared& sh, float* means) {
   using G = Granule<RT>;
@@ -534,43 +623,85 @@ __device__ bool gather_query(const QueryDesc& qd, int64_t qs, uint32_t& cs, uint
 #pragma unroll
     for (int e = 0; e < GR / 2; ++e) acc[u][e] = make_float2(0.f, 0.f);
   int batch_left = qd.J, batch = 0;
-  for (int64_t j0 = 0; j0 < qd.N; j0 += CR) {
-    const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
+  const int RPC = PACK ? CR * rows_per_slot(qd, cfg) : CR;  // rows per chunk
+  for (int64_t j0 = 0; j0 < qd.N; j0 += RPC) {
+    const int cnt = int(qd.N - j0 < RPC ? qd.N - j0 : RPC);
     bool ok = wait_phase(&sh.row_full[cs], ph, sh, cfg);
     if (ok) ok = wait_phase(&sh.coef_full[cs], ph, sh, cfg);
-#pragma unroll
-    for (int s2 = 0; s2 < 8; ++s2) {
-      if (s2 >= cnt || !ok) break;
-      const float c = rg.coef_s[cs * CR + s2];
-      const unsigned char* row = rg.ring + (size_t(cs) * CR + s2) * cfg.slot_bytes;
-#pragma unroll
-      for (int u = 0; u < GPT; ++u) {
-        const int gi = gt + u * RL::kGatherThreads;
-        if (gi * GR < qd.ldr) {
-          G::fma(row + size_t(gi) * 16, make_float2(c, c), acc[u]);
-        }
-      }
-      if (--batch_left == 0) {
-        if (batch == 0 && qs >= kMBufs &&
-            !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg)) {
-          ok = false;
-          break;
-        }
-        float* mrow = means + int64_t(batch) * qd.ldr;
+    if constexpr (PACK) {
+      // row s2 of the chunk at byte s2 * row_bytes of its CR slots
+      const unsigned char* chunk = rg.ring + size_t(cs) * CR * cfg.slot_bytes;
+      const float* cf = rg.coef_s + cs * kMaxChunkRows;
+#pragma unroll 4
+      for (int s2 = 0; s2 < cnt; ++s2) {
+        if (!ok) break;
+        const float c = cf[s2];
+        const unsigned char* row = chunk + size_t(s2) * qd.row_bytes;
 #pragma unroll
         for (int u = 0; u < GPT; ++u) {
           const int gi = gt + u * RL::kGatherThreads;
           if (gi * GR < qd.ldr) {
-#pragma unroll
-            for (int e = 0; e < GR / 2; ++e) {
-              mrow[gi * GR + 2 * e] = acc[u][e].x * qd.inv_J;
-              mrow[gi * GR + 2 * e + 1] = acc[u][e].y * qd.inv_J;
-              acc[u][e] = make_float2(0.f, 0.f);
-            }
+            G::fma(row + size_t(gi) * 16, make_float2(c, c), acc[u]);
           }
         }
-        batch_left = qd.J;
-        ++batch;
+        if (--batch_left == 0) {
+          if (batch == 0 && qs >= kMBufs &&
+              !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg)) {
+            ok = false;
+            break;
+          }
+          float* mrow = means + int64_t(batch) * qd.ldr;
+#pragma unroll
+          for (int u = 0; u < GPT; ++u) {
+            const int gi = gt + u * RL::kGatherThreads;
+            if (gi * GR < qd.ldr) {
+#pragma unroll
+              for (int e = 0; e < GR / 2; ++e) {
+                mrow[gi * GR + 2 * e] = acc[u][e].x * qd.inv_J;
+                mrow[gi * GR + 2 * e + 1] = acc[u][e].y * qd.inv_J;
+                acc[u][e] = make_float2(0.f, 0.f);
+              }
+            }
+          }
+          batch_left = qd.J;
+          ++batch;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int s2 = 0; s2 < 8; ++s2) {
+        if (s2 >= cnt || !ok) break;
+        const float c = rg.coef_s[cs * CR + s2];
+        const unsigned char* row = rg.ring + (size_t(cs) * CR + s2) * cfg.slot_bytes;
+#pragma unroll
+        for (int u = 0; u < GPT; ++u) {
+          const int gi = gt + u * RL::kGatherThreads;
+          if (gi * GR < qd.ldr) {
+            G::fma(row + size_t(gi) * 16, make_float2(c, c), acc[u]);
+          }
+        }
+        if (--batch_left == 0) {
+          if (batch == 0 && qs >= kMBufs &&
+              !wait_phase(&sh.means_empty[mb], uint32_t(qs / kMBufs - 1) & 1u, sh, cfg)) {
+            ok = false;
+            break;
+          }
+          float* mrow = means + int64_t(batch) * qd.ldr;
+#pragma unroll
+          for (int u = 0; u < GPT; ++u) {
+            const int gi = gt + u * RL::kGatherThreads;
+            if (gi * GR < qd.ldr) {
+#pragma unroll
+              for (int e = 0; e < GR / 2; ++e) {
+                mrow[gi * GR + 2 * e] = acc[u][e].x * qd.inv_J;
+                mrow[gi * GR + 2 * e + 1] = acc[u][e].y * qd.inv_J;
+                acc[u][e] = make_float2(0.f, 0.f);
+              }
+            }
+          }
+          batch_left = qd.J;
+          ++batch;
+        }
       }
     }
     // the chunk's one warp-wide agreement (also where the warp reconverges
@@ -603,16 +734,16 @@ __device__ void gather_role(const Seq& seq, const LaunchCfg& cfg, const Regions&
       const int64_t gran = qd.ldr / (qd.dtype == KERDOCK_BF16 ? 8 : 4);
       const int gpt = gran <= kGT ? 1 : (gran <= 2 * kGT ? 2 : 4);
       if (qd.dtype == KERDOCK_BF16) {
-        ok = gpt == 1   ? gather_query<__nv_bfloat16, 1, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
-             : gpt == 2 ? gather_query<__nv_bfloat16, 2, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
-                        : gather_query<__nv_bfloat16, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+        ok = gpt == 1   ? gather_query<__nv_bfloat16, 1, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means)
+             : gpt == 2 ? gather_query<__nv_bfloat16, 2, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means)
+                        : gather_query<__nv_bfloat16, GPT, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means);
       } else {
-        ok = gpt == 1   ? gather_query<float, 1, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
-             : gpt == 2 ? gather_query<float, 2, CW>(qd, qs, cs, ph, cfg, rg, sh, means)
-                        : gather_query<float, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+        ok = gpt == 1   ? gather_query<float, 1, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means)
+             : gpt == 2 ? gather_query<float, 2, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means)
+                        : gather_query<float, GPT, CW, true>(qd, qs, cs, ph, cfg, rg, sh, means);
       }
     } else {
-      ok = gather_query<RT, GPT, CW>(qd, qs, cs, ph, cfg, rg, sh, means);
+      ok = gather_query<RT, GPT, CW, false>(qd, qs, cs, ph, cfg, rg, sh, means);
     }
     if (!ok) return;
     if (cfg.means_gmem != nullptr) __threadfence_block();
@@ -915,7 +1046,7 @@ bool means_fit_smem(const Dims& dm) {
 // with 2 KiB rows (n = 1024, bfloat16) chunks of eight took 0.63 ms for 1000
 // queries against 0.72 ms with four).  Returns false when the ring cannot hold
 // more chunks than the kernel has coefficient warps.
-bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c) {
+bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c, bool packed) {
   c = LaunchCfg{};
   c.poll_limit = kDefaultPollLimit;
   c.slot_bytes = dm.row_bytes;
@@ -940,25 +1071,32 @@ bool make_cfg(const Dims& dm, const Tuning& tu, bool means_in_smem, LaunchCfg& c
   c.nchunk = ns / cr;
   if (c.nchunk < min_chunks) return false;
   if (c.nchunk > kMaxChunks) c.nchunk = kMaxChunks;
-  ns = c.nchunk * cr;
+  // the layout; with packed chunks the coefficients take kMaxChunkRows floats
+  // per chunk, and a ring that leaves no room for them loses chunks
+  for (;; --c.nchunk) {
+    if (c.nchunk < min_chunks) return false;
+    ns = c.nchunk * cr;
+    size_t off = align_up(size_t(ns) * dm.row_bytes, 128);
+    c.off_coef = uint32_t(off);
+    off = align_up(off + (packed ? size_t(c.nchunk) * kMaxChunkRows : size_t(ns)) * 4, 16);
+    c.off_x = uint32_t(off);
+    off = align_up(off + size_t(kXBufs) * size_t(dm.xpad) * 4, 16);
+    c.off_means = uint32_t(off);
+    if (means_in_smem) off = align_up(off + means_bytes, 16);
+    c.off_mu = uint32_t(off);
+    off = align_up(off + size_t(dm.ldr) * 4, 16);
+    c.off_sel = uint32_t(off);
+    off = align_up(off + spad * 4, 16);
+    c.off_vals = uint32_t(off);
+    off = align_up(off + spad * 4, 16);
+    c.total = uint32_t(off);
+    if (off <= kSmemBudget) break;
+    if (!packed) return false;
+  }
   int g = 1;  // chunks per producer step: g * crows <= 32 lanes, g <= nchunk / 2
   while (2 * g * cr <= 32 && 4 * g <= c.nchunk) g *= 2;
   c.pgroup = g;
-  size_t off = align_up(size_t(ns) * dm.row_bytes, 128);
-  c.off_coef = uint32_t(off);
-  off = align_up(off + size_t(ns) * 4, 16);
-  c.off_x = uint32_t(off);
-  off = align_up(off + size_t(kXBufs) * size_t(dm.xpad) * 4, 16);
-  c.off_means = uint32_t(off);
-  if (means_in_smem) off = align_up(off + means_bytes, 16);
-  c.off_mu = uint32_t(off);
-  off = align_up(off + size_t(dm.ldr) * 4, 16);
-  c.off_sel = uint32_t(off);
-  off = align_up(off + spad * 4, 16);
-  c.off_vals = uint32_t(off);
-  off = align_up(off + spad * 4, 16);
-  c.total = uint32_t(off);
-  return off <= kSmemBudget;
+  return true;
 }
 
 // Descriptor fields that come from the plan alone.
