@@ -447,6 +447,135 @@ struct CoefState {
   uint64_t cbase;   // global chunk counter of the current query's first chunk
 };
 
+
+// kerdock_coefficients in two halves, so that a coefficient warp can request
+// the sign words of its next chunk (coef_issue) before it sums the current one
+// (coef_finish): the words' load latency then overlaps the sums.
+template <bool XREG, int NS>
+struct CoefWords {
+  static constexpr int kMaxGroups = XREG ? 1 : 4;
+  uint32_t F[kMaxGroups][NS];
+};
+template <bool XREG, int NS>
+__device__ __forceinline__ void coef_issue(const uint32_t* __restrict__ tsigns, int64_t tstride,
+                                           const uint32_t (&ell)[4], int kbits, uint32_t dmask,
+                                           int groups, int lane, CoefWords<XREG, NS>& W) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const uint32_t b = ell[s] >> kbits;
+    const uint32_t bmax = (dmask + 1u) / 2u - 1u;
+    const uint32_t* row = tsigns + int64_t(b < bmax ? b : bmax) * tstride;
+#pragma unroll
+    for (int g = 0; g < CoefWords<XREG, NS>::kMaxGroups; ++g)
+      W.F[g][s] = g < groups ? __ldg(row + (g << 5) + lane) : 0u;
+  }
+}
+template <bool XREG, int NS>
+__device__ __forceinline__ void coef_finish(CoefWords<XREG, NS>& W, const uint32_t (&ell)[4],
+                                            uint32_t dmask, int groups, int lane,
+                                            const float (&xr)[32], const float* xs, float (&c)[4]) {
+  constexpr int kMaxGroups = CoefWords<XREG, NS>::kMaxGroups;
+  float part[NS];
+  uint32_t whi[NS], pl[NS], wmask[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    part[s] = 0.f;
+    const uint32_t w = ell[s] & dmask;
+    whi[s] = w >> 5;
+    pl[s] = __popc(w & 31u & uint32_t(lane)) & 1u;
+    wmask[s] = __ballot_sync(0xffffffffu, __popc(whi[s] & 31u & uint32_t(lane)) & 1u);
+  }
+#pragma unroll
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (g >= groups) break;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      W.F[g][s] ^= wmask[s];
+      if ((__popc(whi[s] & uint32_t(g << 5)) & 1u) ^ pl[s]) W.F[g][s] = ~W.F[g][s];
+    }
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const float xv = XREG ? xr[t] : xs[((g << 5) + t) * 32 + lane];
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        part[s] += __uint_as_float(__float_as_uint(xv) ^ ((W.F[g][s] << (31 - t)) & 0x80000000u));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) c[s] = s < NS ? part[s] : 0.f;
+}
+
+// One query's chunks for this coefficient warp (every CW-th chunk, NS rows
+// each), with the next chunk's samples drawn and its sign words requested
+// before the current chunk is summed.  Used by the single-plan kernels with x
+// in registers (n <= 1024) and chunks of up to four rows: 3 % less time for
+// the n = 1024 float32 queries (0.644 against 0.662 ms for 1000); with x in
+// shared memory the second set of words spills registers.
+template <bool XREG, int NS, int CW>
+__device__ bool coef_chunks_pf(const QueryDesc& qd, CoefState& st, const LaunchCfg& cfg,
+                               const Regions& rg, Shared& sh, const float* xq,
+                               const float (&xr)[32], uint64_t cend) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nchunk = uint32_t(cfg.nchunk);
+  const int groups = int((qd.n + 1023) / 1024);
+  const uint32_t dmask = uint32_t(qd.d - 1);
+  const int64_t half = qd.d / 2;
+  auto draw = [&](uint64_t cc, uint32_t (&ell)[4]) {
+    const int64_t j0 = int64_t(cc - st.cbase) * NS;
+    const int cnt = int(qd.N - j0 < NS ? qd.N - j0 : NS);
+    uint32_t my_ell = 0;
+    if (lane < cnt)
+      my_ell = uint32_t(
+          sample_index(qd.seed, uint64_t(qd.ctr_base) + uint64_t(j0 + lane), uint64_t(qd.L)));
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) ell[s2] = __shfl_sync(0xffffffffu, my_ell, s2 < cnt ? s2 : 0);
+  };
+  uint32_t ell[4];
+  CoefWords<XREG, NS> W;
+  if (st.cc < cend) {
+    draw(st.cc, ell);
+    coef_issue<XREG, NS>(qd.tsigns, qd.tstride, ell, qd.k, dmask, groups, lane, W);
+  }
+  for (; st.cc < cend; st.cc += CW) {
+    const int64_t j0 = int64_t(st.cc - st.cbase) * NS;
+    const int cnt = int(qd.N - j0 < NS ? qd.N - j0 : NS);
+    uint32_t ell_next[4] = {0u, 0u, 0u, 0u};
+    CoefWords<XREG, NS> Wn;
+    if (st.cc + CW < cend) {
+      draw(st.cc + CW, ell_next);
+      coef_issue<XREG, NS>(qd.tsigns, qd.tstride, ell_next, qd.k, dmask, groups, lane, Wn);
+    }
+    float c[4];
+    coef_finish<XREG, NS>(W, ell, dmask, groups, lane, xr, xq, c);
+    if (st.cc >= nchunk && !warp_wait(&sh.slot_empty[st.cs], st.ph ^ 1u, sh, cfg)) return false;
+    if (lane == 0) {
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2) {
+        if (s2 >= cnt) break;
+        const uint32_t w = ell[s2] & dmask;
+        float cv = c[s2];
+        if (int64_t(ell[s2] >> qd.k) == half) cv = w < qd.n ? qd.sqrt_d * xq[w] : 0.f;
+        rg.coef_s[st.cs * NS + s2] = cv;
+        if (qd.coef_out) qd.coef_out[j0 + s2] = cv;
+      }
+      mbar_arrive(&sh.coef_full[st.cs]);
+    }
+    st.cs += CW;
+    if (st.cs >= nchunk) {
+      st.cs -= nchunk;
+      st.ph ^= 1u;
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) ell[s2] = ell_next[s2];
+    W = Wn;
+  }
+  return true;
+}
+
 // PACK (the batch kernel): a chunk holds crows * rows_per_slot samples, up to
 // kMaxChunkRows, computed four at a time with each lane keeping its own
 // sample's coefficient; the coefficient area has kMaxChunkRows entries per
@@ -514,6 +643,15 @@ __device__ bool coef_query(const QueryDesc& qd, int64_t qs, CoefState& st, const
     return true;
   }
   const uint64_t cend = st.cbase + uint64_t((qd.N + CR - 1) / CR);
+  if (XREG && CR <= 4) {  // the pipelined form (coef_chunks_pf)
+    bool ok;
+    if (CR == 4) ok = coef_chunks_pf<XREG, 4, CW>(qd, st, cfg, rg, sh, xq, xr, cend);
+    else if (CR == 2) ok = coef_chunks_pf<XREG, 2, CW>(qd, st, cfg, rg, sh, xq, xr, cend);
+    else ok = coef_chunks_pf<XREG, 1, CW>(qd, st, cfg, rg, sh, xq, xr, cend);
+    if (!ok) return false;
+    st.cbase = cend;
+    return true;
+  }
   for (; st.cc < cend; st.cc += CW) {
     const int64_t j0 = int64_t(st.cc - st.cbase) * CR;
     const int cnt = int(qd.N - j0 < CR ? qd.N - j0 : CR);
