@@ -126,3 +126,22 @@ def test_theory_parameters_errors(lib):
     with pytest.raises(K.KerdockError) as ei:
         K.kerdock_theory_parameters(1.0, 0.125, 0.0, 1e-9, 4096)
     assert ei.value.code == -2  # KERDOCK_ERR_UNSUPPORTED
+
+
+def test_ring_tuning_values(lib):
+    # rows per chunk 1, 2, 4 or 8 (0 = default); a geometry whose ring cannot
+    # hold more chunks than the query kernel has coefficient warps is refused
+    small = K.kerdock_plan_create(16, 16, 0, 4, 2, 4)        # 64-byte rows
+    for cr in (0, 1, 2, 4, 8):
+        K.kerdock_plan_set_tuning(small, 160, cr)
+    for cr in (3, 5, 6, 16):
+        with pytest.raises(K.KerdockError) as e:
+            K.kerdock_plan_set_tuning(small, 160, cr)
+        assert e.value.code == -1
+    large = K.kerdock_plan_create(4096, 4096, 0, 4, 2, 4)    # 16 KiB float32 rows
+    K.kerdock_plan_set_tuning(large, 160, 1)
+    with pytest.raises(K.KerdockError) as e:                 # 9 slots: one chunk of 8
+        K.kerdock_plan_set_tuning(large, 160, 8)
+    assert e.value.code == -2
+    K.kerdock_plan_destroy(small)
+    K.kerdock_plan_destroy(large)
