@@ -231,6 +231,30 @@ int kerdock_batch_launch(kerdock_batch_t batch);
  * KERDOCK_ERR_UNSUPPORTED. */
 int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t crows);
 
+/* Re-deal the queries to the CTAs by the caller's cost estimates: cost[i]
+ * (any unit, finite, >= 0) for the i-th query of the creation list, count
+ * the list's length.  The schedule is longest first onto the least-loaded
+ * CTA, as at creation, where the estimate is the query's gathered and
+ * refined bytes.  Results do not depend on the schedule (every query runs
+ * whole on one CTA, its samples in counter order).  Synchronises the stream
+ * once (the upload); INVALID_ARG on a wrong count or a negative, infinite or
+ * NaN cost. */
+int kerdock_batch_set_costs(kerdock_batch_t batch, const double* cost, int64_t count);
+
+/* CTAs of the batch's launch (one per SM, at most one per query); 0 for a
+ * null batch. */
+int32_t kerdock_batch_ctas(kerdock_batch_t batch);
+
+/* Set the schedule explicitly: CTA c (0 <= c < ctas) runs the queries
+ * order[cta_start[c] .. cta_start[c+1]-1] in that sequence (indices into the
+ * creation list).  order is a permutation of 0..count-1, cta_start has
+ * ctas + 1 non-decreasing entries from 0 to count, 1 <= ctas <=
+ * kerdock_batch_ctas(batch); CTAs from ctas on get no queries.  Both arrays
+ * are host memory, copied.  Results do not depend on the schedule.
+ * Synchronises the stream once; INVALID_ARG on any violation. */
+int kerdock_batch_set_schedule(kerdock_batch_t batch, const int32_t* order,
+                               const int64_t* cta_start, int32_t ctas);
+
 /* Autotuner: time reps launches of every candidate geometry (ring 64/96/128/
  * 160 KiB x 1/2/4/8 rows per chunk), keep the fastest and report it. */
 int kerdock_batch_tune(kerdock_batch_t batch, int32_t reps, int32_t* ring_kb, int32_t* crows,

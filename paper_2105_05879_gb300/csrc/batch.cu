@@ -105,6 +105,45 @@ void destroy_graph(kerdock_batch_s* b) {
   b->graph = nullptr;
 }
 
+// Deal the queries to the CTAs longest-first onto the least-loaded CTA by
+// cost (any unit); fills the host order and per-CTA start arrays.
+void deal(kerdock_batch_s* b, const std::vector<double>& cost) {
+  const size_t count = cost.size();
+  std::vector<int32_t> by_cost(count);
+  for (size_t i = 0; i < count; ++i) by_cost[i] = int32_t(i);
+  std::stable_sort(by_cost.begin(), by_cost.end(),
+                   [&](int32_t x, int32_t y) { return cost[size_t(x)] > cost[size_t(y)]; });
+  using Load = std::pair<double, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
+  std::vector<std::vector<int32_t>> per_cta(size_t(b->grid));
+  for (int32_t qi : by_cost) {
+    Load top = heap.top();
+    heap.pop();
+    per_cta[size_t(top.second)].push_back(qi);
+    top.first += cost[size_t(qi)];
+    heap.push(top);
+  }
+  b->order.clear();
+  b->cta_start.assign(size_t(b->grid) + 1, 0);
+  for (int c = 0; c < b->grid; ++c) {
+    b->cta_start[size_t(c) + 1] = b->cta_start[size_t(c)] + int64_t(per_cta[size_t(c)].size());
+    for (int32_t qi : per_cta[size_t(c)]) b->order.push_back(qi);
+  }
+}
+
+// Upload the schedule (order and per-CTA starts) on the batch's stream and
+// wait for it: the host arrays are the copies' sources.
+cudaError_t upload_schedule(kerdock_batch_s* b) {
+  cudaError_t e = cudaMemcpyAsync(b->d_order, b->order.data(), b->order.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_cta_start, b->cta_start.data(),
+                        b->cta_start.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return e;
+}
+
 // Set the ring geometry and (re)capture the launch into a graph when asked.
 int configure(kerdock_batch_s* b, const kd::Tuning& tu) {
   kd::LaunchCfg cfg{};
@@ -218,27 +257,7 @@ int kerdock_batch_create(kerdock_batch_t* batch, const kerdock_query_t* queries,
   }
   b->means_in_smem = kd::means_fit_smem(b->dims);
   b->grid = int(count < sms ? count : sms);
-  // Longest-first onto the least-loaded CTA.
-  std::vector<int32_t> by_cost(static_cast<size_t>(count));
-  for (int64_t i = 0; i < count; ++i) by_cost[size_t(i)] = int32_t(i);
-  std::stable_sort(by_cost.begin(), by_cost.end(),
-                   [&](int32_t x, int32_t y) { return cost[size_t(x)] > cost[size_t(y)]; });
-  using Load = std::pair<double, int>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
-  std::vector<std::vector<int32_t>> per_cta(size_t(b->grid));
-  for (int32_t qi : by_cost) {
-    Load top = heap.top();
-    heap.pop();
-    per_cta[size_t(top.second)].push_back(qi);
-    top.first += cost[size_t(qi)];
-    heap.push(top);
-  }
-  b->cta_start.assign(size_t(b->grid) + 1, 0);
-  for (int c = 0; c < b->grid; ++c) {
-    b->cta_start[size_t(c) + 1] = b->cta_start[size_t(c)] + int64_t(per_cta[size_t(c)].size());
-    for (int32_t qi : per_cta[size_t(c)]) b->order.push_back(qi);
-  }
+  deal(b, cost);
   const WsLayout w = ws_layout(count, b->grid, b->dims, b->means_in_smem);
   if (ws_bytes < w.total) {
     delete b;
@@ -251,13 +270,7 @@ int kerdock_batch_create(kerdock_batch_t* batch, const kerdock_query_t* queries,
   b->d_means = b->means_in_smem ? nullptr : reinterpret_cast<float*>(base + w.means);
   cudaError_t e = cudaMemcpyAsync(b->d_descs, b->descs.data(), b->descs.size() * sizeof(kd::QueryDesc),
                                   cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_order, b->order.data(), b->order.size() * sizeof(int32_t),
-                        cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_cta_start, b->cta_start.data(), b->cta_start.size() * sizeof(int64_t),
-                        cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host vectors stay alive anyway
+  if (e == cudaSuccess) e = upload_schedule(b);
   if (e != cudaSuccess) {
     delete b;
     return KERDOCK_ERR_CUDA;
@@ -284,6 +297,44 @@ int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t cro
   tu.ring_kb = ring_kb;
   tu.crows = crows;
   return configure(batch, tu);
+}
+
+int kerdock_batch_set_costs(kerdock_batch_t batch, const double* cost, int64_t count) {
+  if (batch == nullptr || cost == nullptr || count != int64_t(batch->descs.size()))
+    return KERDOCK_ERR_INVALID_ARG;
+  std::vector<double> c(static_cast<size_t>(count));
+  for (int64_t i = 0; i < count; ++i) {
+    if (!(cost[i] >= 0.0) || !(cost[i] <= 1e300)) return KERDOCK_ERR_INVALID_ARG;  // NaN, < 0, inf
+    c[size_t(i)] = cost[i];
+  }
+  deal(batch, c);
+  // the kernel (and a captured graph) reads the schedule through the same
+  // device arrays, so the new one takes effect from the next launch
+  if (upload_schedule(batch) != cudaSuccess) return KERDOCK_ERR_CUDA;
+  return KERDOCK_OK;
+}
+
+int32_t kerdock_batch_ctas(kerdock_batch_t batch) { return batch == nullptr ? 0 : batch->grid; }
+
+int kerdock_batch_set_schedule(kerdock_batch_t batch, const int32_t* order,
+                               const int64_t* cta_start, int32_t ctas) {
+  if (batch == nullptr || order == nullptr || cta_start == nullptr || ctas < 1 ||
+      ctas > batch->grid)
+    return KERDOCK_ERR_INVALID_ARG;
+  const int64_t count = int64_t(batch->descs.size());
+  if (cta_start[0] != 0 || cta_start[ctas] != count) return KERDOCK_ERR_INVALID_ARG;
+  for (int32_t c = 0; c < ctas; ++c)
+    if (cta_start[c + 1] < cta_start[c]) return KERDOCK_ERR_INVALID_ARG;
+  std::vector<char> seen(static_cast<size_t>(count), 0);  // order must be a permutation
+  for (int64_t i = 0; i < count; ++i) {
+    if (order[i] < 0 || order[i] >= count || seen[size_t(order[i])]) return KERDOCK_ERR_INVALID_ARG;
+    seen[size_t(order[i])] = 1;
+  }
+  batch->order.assign(order, order + count);
+  batch->cta_start.assign(size_t(batch->grid) + 1, count);  // CTAs past ctas get no queries
+  for (int32_t c = 0; c <= ctas; ++c) batch->cta_start[size_t(c)] = cta_start[c];
+  if (upload_schedule(batch) != cudaSuccess) return KERDOCK_ERR_CUDA;
+  return KERDOCK_OK;
 }
 
 int kerdock_batch_tune(kerdock_batch_t batch, int32_t reps, int32_t* ring_kb, int32_t* crows,

@@ -33,7 +33,9 @@ EXPORTED = [
     "kerdock_apply_debug", "kerdock_sync", "kerdock_debug_signs", "kerdock_plan_destroy",
     "kerdock_strerror", "kerdock_version", "kerdock_apply_noalloc",
     "kerdock_batch_workspace_bytes", "kerdock_batch_create", "kerdock_batch_launch",
-    "kerdock_batch_set_tuning", "kerdock_batch_tune", "kerdock_batch_sync",
+    "kerdock_batch_set_tuning", "kerdock_batch_set_costs", "kerdock_batch_ctas",
+    "kerdock_batch_set_schedule", "kerdock_batch_tune",
+    "kerdock_batch_sync",
     "kerdock_batch_destroy", "kerdock_plan_set_tuning", "kerdock_plan_tune",
     "kerdock_mlp_create", "kerdock_mlp_sizes", "kerdock_mlp_bind", "kerdock_mlp_pointers",
     "kerdock_mlp_sync_weights", "kerdock_mlp_init", "kerdock_mlp_forward", "kerdock_mlp_backward",
@@ -114,6 +116,10 @@ def load_library(path=None):
                                                 c_vp, c_sz, c_vp, c_i32]),
         "kerdock_batch_launch": (ctypes.c_int, [P]),
         "kerdock_batch_set_tuning": (ctypes.c_int, [P, c_i32, c_i32]),
+        "kerdock_batch_set_costs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), c_i64]),
+        "kerdock_batch_ctas": (c_i32, [P]),
+        "kerdock_batch_set_schedule": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32),
+                                                      ctypes.POINTER(c_i64), c_i32]),
         "kerdock_batch_tune": (ctypes.c_int, [P, c_i32, ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_int32),
                                               ctypes.POINTER(ctypes.c_float)]),
@@ -264,6 +270,28 @@ def kerdock_batch_launch(batch):
 def kerdock_batch_set_tuning(batch, ring_kb, crows):
     _check(load_library().kerdock_batch_set_tuning(batch, ring_kb, crows),
            "kerdock_batch_set_tuning")
+
+
+def kerdock_batch_set_costs(batch, costs):
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    _check(load_library().kerdock_batch_set_costs(
+        batch, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), c.size), "kerdock_batch_set_costs")
+
+
+def kerdock_batch_ctas(batch):
+    return int(load_library().kerdock_batch_ctas(batch))
+
+
+def kerdock_batch_set_schedule(batch, lists):
+    """lists[c] = the creation-list indices CTA c runs, in order."""
+    order = np.ascontiguousarray(np.concatenate([np.asarray(l, dtype=np.int32) for l in lists])
+                                 if lists else np.zeros(0, np.int32), dtype=np.int32)
+    start = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(l) for l in lists])]),
+                                 dtype=np.int64)
+    _check(load_library().kerdock_batch_set_schedule(
+        batch, order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        start.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(lists)),
+        "kerdock_batch_set_schedule")
 
 
 def kerdock_batch_tune(batch, reps):
@@ -650,6 +678,18 @@ class KerdockBatch:
 
     def set_tuning(self, ring_kb, crows):
         kerdock_batch_set_tuning(self.handle, ring_kb, crows)
+
+    def set_costs(self, costs):
+        """Re-deal the queries to the CTAs by these per-query cost estimates."""
+        kerdock_batch_set_costs(self.handle, costs)
+
+    @property
+    def ctas(self):
+        return kerdock_batch_ctas(self.handle)
+
+    def set_schedule(self, lists):
+        """Run lists[c] (indices into specs, in order) on CTA c."""
+        kerdock_batch_set_schedule(self.handle, lists)
 
     def sync(self):
         kerdock_batch_sync(self.handle)

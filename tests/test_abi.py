@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2105_05879_gb300 import build as kbuild
@@ -91,6 +92,17 @@ def test_calls_before_bind_fail_cleanly(lib):
     assert e.value.code == -8
     K.kerdock_plan_destroy(h)
     K.kerdock_plan_destroy(None)
+
+
+def test_batch_schedule_calls_null_handle(lib):
+    # a null batch is refused before any device work
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_batch_set_costs(None, np.ones(4))
+    assert e.value.code == -1
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_batch_set_schedule(None, [[0, 1], [2]])
+    assert e.value.code == -1
+    assert K.kerdock_batch_ctas(None) == 0
 
 
 def test_strerror_and_version(lib):

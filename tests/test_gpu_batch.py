@@ -97,6 +97,36 @@ def test_batch_mixed_plans_graph_replay():
     for a, b in zip(before, batch.results()):
         np.testing.assert_array_equal(a[0], b[0])
         np.testing.assert_allclose(a[1], b[1], atol=0)
+    # re-dealing the queries to other CTAs changes the schedule, never the results
+    nq = len(specs)
+    for costs in (np.arange(nq, dtype=np.float64), rng.random(nq), np.zeros(nq)):
+        batch.set_costs(costs)
+        batch.launch()
+        batch.sync()
+        for a, b in zip(before, batch.results()):
+            np.testing.assert_array_equal(a[0], b[0])
+            np.testing.assert_allclose(a[1], b[1], atol=0)
+    for bad in (np.ones(nq - 1), -np.ones(nq), np.full(nq, np.nan), np.full(nq, np.inf)):
+        with pytest.raises(K.KerdockError) as e:
+            batch.set_costs(bad)
+        assert e.value.code == -1
+    # explicit schedules: several queries per CTA, fewer CTAs than the launch
+    # (the rest run nothing), an empty list in the middle
+    assert batch.ctas == min(nq, torch.cuda.get_device_properties(0).multi_processor_count)
+    perm = rng.permutation(nq).tolist()
+    for lists in ([perm[i::4] for i in range(4)], [perm[:nq // 2], [], perm[nq // 2:]],
+                  [list(range(nq))]):
+        batch.set_schedule(lists)
+        batch.launch()
+        batch.sync()
+        for a, b in zip(before, batch.results()):
+            np.testing.assert_array_equal(a[0], b[0])
+            np.testing.assert_allclose(a[1], b[1], atol=0)
+    for bad in ([list(range(nq - 1))], [list(range(nq - 1)) + [0]],
+                [[i] for i in range(nq)] + [[]] * (batch.ctas + 1 - nq)):
+        with pytest.raises(K.KerdockError) as e:  # not a permutation; too many CTAs
+            batch.set_schedule(bad)
+        assert e.value.code == -1
     batch.close()
     for p in plans:
         p.close()
