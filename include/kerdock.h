@@ -211,8 +211,10 @@ typedef struct kerdock_batch_s* kerdock_batch_t;
  * invalid input). */
 size_t kerdock_batch_workspace_bytes(const kerdock_query_t* queries, int64_t count);
 
-/* Validate the queries, deal them to the CTAs by estimated cost (longest
- * first onto the least-loaded CTA), upload descriptors and schedule into
+/* Validate the queries, deal them to the CTAs plan by plan (plans in
+ * decreasing row size; each plan's queries longest first onto the
+ * least-loaded CTA by estimated cost, loads carried over), so that all CTAs
+ * work through one representation at a time; upload descriptors and schedule into
  * ws_dev (256-byte aligned, caller-owned, kept alive with the batch), and --
  * with KERDOCK_BATCH_GRAPH -- capture the launch into a CUDA graph.
  * Synchronises the stream once (the upload).  Every plan must stay bound and
@@ -233,9 +235,9 @@ int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t cro
 
 /* Re-deal the queries to the CTAs by the caller's cost estimates: cost[i]
  * (any unit, finite, >= 0) for the i-th query of the creation list, count
- * the list's length.  The schedule is longest first onto the least-loaded
- * CTA, as at creation, where the estimate is the query's gathered and
- * refined bytes.  Results do not depend on the schedule (every query runs
+ * the list's length.  The schedule is made as at creation (plan by plan,
+ * longest first onto the least-loaded CTA), where the estimate is the
+ * query's gathered and refined bytes.  Results do not depend on the schedule (every query runs
  * whole on one CTA, its samples in counter order).  Synchronises the stream
  * once (the upload); INVALID_ARG on a wrong count or a negative, infinite or
  * NaN cost. */

@@ -2,12 +2,13 @@
 // graph-captured launch, and the autotuner of the query kernel's ring.
 //
 // A batch is a fixed list of queries (plan, x, J, K, S, eps, seed, outputs).
-// At creation the host resolves every query into a device descriptor, orders
-// the queries by estimated cost (bytes gathered plus refined) and deals them
-// to the CTAs longest-first onto the least-loaded CTA, uploads descriptors and
-// schedule to the caller's workspace, and (optionally) captures the launch into
-// a CUDA graph that kerdock_batch_launch replays.  Inputs are read at replay
-// time, so a caller refills the same x buffers and replays.
+// At creation the host resolves every query into a device descriptor, deals
+// the queries to the CTAs plan by plan (largest rows first), each plan's
+// longest first onto the least-loaded CTA by estimated cost (bytes gathered
+// plus refined), uploads descriptors and schedule to the caller's workspace,
+// and (optionally) captures the launch into a CUDA graph that
+// kerdock_batch_launch replays.  Inputs are read at replay time, so a caller
+// refills the same x buffers and replays.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -105,14 +106,44 @@ void destroy_graph(kerdock_batch_s* b) {
   b->graph = nullptr;
 }
 
-// Deal the queries to the CTAs longest-first onto the least-loaded CTA by
-// cost (any unit); fills the host order and per-CTA start arrays.
+// Deal the queries to the CTAs by cost (any unit), plan by plan: the plans in
+// decreasing order of row size, each plan's queries longest first onto the
+// least-loaded CTA (loads carried from plan to plan), every CTA running its
+// share of one plan before the next.  So all CTAs sweep one representation at
+// a time, and the rows in flight share its address translations: on GB300 the
+// mixed batch of seven plans (n = 64 ... 4096, 2048 queries) took 5.20 ms this
+// way against 6.59 ms with one longest-first order over all queries, 7.1 ms
+// with each CTA's list rotated to a different starting point and 7.7 ms
+// shuffled.  Fills the host order and per-CTA start arrays.
 void deal(kerdock_batch_s* b, const std::vector<double>& cost) {
   const size_t count = cost.size();
+  // plan groups, identified by representation, in order of first appearance
+  std::vector<const void*> reprs;
+  std::vector<uint32_t> group_row_bytes;
+  std::vector<int> group(count);
+  for (size_t i = 0; i < count; ++i) {
+    const void* r = b->descs[i].R;
+    size_t g = 0;
+    while (g < reprs.size() && reprs[g] != r) ++g;
+    if (g == reprs.size()) {
+      reprs.push_back(r);
+      group_row_bytes.push_back(b->descs[i].row_bytes);
+    }
+    group[i] = int(g);
+  }
+  std::vector<int> gorder(reprs.size());
+  for (size_t g = 0; g < gorder.size(); ++g) gorder[g] = int(g);
+  std::stable_sort(gorder.begin(), gorder.end(), [&](int x, int y) {
+    return group_row_bytes[size_t(x)] > group_row_bytes[size_t(y)];
+  });
+  std::vector<int> grank(reprs.size());
+  for (size_t k = 0; k < gorder.size(); ++k) grank[size_t(gorder[k])] = int(k);
   std::vector<int32_t> by_cost(count);
   for (size_t i = 0; i < count; ++i) by_cost[i] = int32_t(i);
-  std::stable_sort(by_cost.begin(), by_cost.end(),
-                   [&](int32_t x, int32_t y) { return cost[size_t(x)] > cost[size_t(y)]; });
+  std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t x, int32_t y) {
+    const int gx = grank[size_t(group[size_t(x)])], gy = grank[size_t(group[size_t(y)])];
+    return gx != gy ? gx < gy : cost[size_t(x)] > cost[size_t(y)];
+  });
   using Load = std::pair<double, int>;
   std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
   for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});

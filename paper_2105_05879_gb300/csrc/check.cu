@@ -26,6 +26,11 @@ namespace {
 constexpr int kCheckThreads = 512;
 constexpr int kReconCols = 4;   // columns i per CTA: d = 4096 doubles x 4 = 128 KiB
 constexpr int kMaxProbes = 4;
+// Dynamic shared-memory caps, one per kernel for the whole process (captured
+// graphs included), so each is set to the largest size the kernel takes
+// (d, n <= 4096), never to one launch's size.
+constexpr int kReconSmemCap = 4096 * kReconCols * int(sizeof(double));
+constexpr int kRefSmemCap = 4096 * int(sizeof(double));
 
 template <typename T>
 __device__ __forceinline__ double load_rep(const T* p);
@@ -217,7 +222,11 @@ int check_range(const Plan& p, int64_t b0, int64_t nb) {
 template <typename T, int U>
 int launch_frame(const FrameArgs& fa, const Plan& p, size_t smem) {
   auto kern = frame_kernel<T, U>;
-  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  // the cap is per kernel and process-wide: the largest this instance takes
+  // (kMaxProbes vectors of m <= U * kCheckThreads doubles), not this launch's
+  constexpr int kCap = kMaxProbes * U * kCheckThreads * int(sizeof(double));
+  if (smem > size_t(kCap)) return KERDOCK_ERR_UNSUPPORTED;
+  KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kCap));
   kern<<<unsigned(p.num_sms), kCheckThreads, smem, p.stream>>>(fa);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
@@ -254,11 +263,11 @@ extern "C" int kerdock_check_reconstruction(kerdock_plan_t plan, int64_t b0, int
   const dim3 grid(unsigned((p.ldr + kd::kReconCols - 1) / kd::kReconCols), unsigned(nb));
   if (p.dtype == KERDOCK_BF16) {
     KD_CUDA_TRY(cudaFuncSetAttribute(kd::recon_kernel<__nv_bfloat16>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kd::kReconSmemCap));
     kd::recon_kernel<__nv_bfloat16><<<grid, kd::kCheckThreads, smem, p.stream>>>(a);
   } else {
     KD_CUDA_TRY(cudaFuncSetAttribute(kd::recon_kernel<float>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kd::kReconSmemCap));
     kd::recon_kernel<float><<<grid, kd::kCheckThreads, smem, p.stream>>>(a);
   }
   KD_CUDA_TRY(cudaGetLastError());
@@ -301,7 +310,7 @@ extern "C" int kerdock_check_tight_frame(kerdock_plan_t plan, const double* Y_de
   if (rc != KERDOCK_OK) return rc;
   const size_t zsmem = size_t(p.n) * sizeof(double);
   KD_CUDA_TRY(cudaFuncSetAttribute(kd::ref_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(zsmem)));
+                                   kd::kRefSmemCap));
   const double scale = double(nb) * double(p.d);
   kd::ref_kernel<<<unsigned(P), 1024, zsmem, p.stream>>>(p.A, p.lda, p.m, p.n, Y_dev, scale,
                                                          ref_dev);

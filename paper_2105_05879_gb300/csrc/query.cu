@@ -1276,8 +1276,12 @@ namespace {
 template <typename RT, int GPT, bool XREG>
 int launch_single(const QueryArgs& a, int64_t grid, cudaStream_t stream) {
   auto kern = query_kernel<RT, GPT, XREG>;
+  // The cap is one per kernel for the whole process, graphs captured by a
+  // caller included: set to the largest layout (make_cfg's budget), never to
+  // this launch's size, which would make a captured launch of a plan with a
+  // larger layout fail.
   KD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(a.cfg.total)));
+                                   int(kSmemBudget)));
   kern<<<unsigned(grid), kThreads, a.cfg.total, stream>>>(a);
   KD_CUDA_TRY(cudaGetLastError());
   return KERDOCK_OK;
@@ -1433,8 +1437,12 @@ int launch_apply_noalloc(const Plan& p, const float* X, int64_t q, int64_t ldx, 
 // Batches of queries over any mix of plans (one persistent launch).
 // ---------------------------------------------------------------------------
 int prepare_batch_kernel(const LaunchCfg& cfg) {
+  // One cap for every batch (each batch's graph keeps its own layout size):
+  // the largest layout, so that a batch configured later with a smaller one
+  // does not make the others' launches fail.
+  if (cfg.total > kSmemBudget) return KERDOCK_ERR_UNSUPPORTED;
   KD_CUDA_TRY(cudaFuncSetAttribute(query_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(cfg.total)));
+                                   int(kSmemBudget)));
   return KERDOCK_OK;
 }
 

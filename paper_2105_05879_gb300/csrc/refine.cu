@@ -265,8 +265,12 @@ extern "C" int kerdock_refine_scores(kerdock_plan_t plan, const float* X_dev, in
   a.out_count = out_count;
   a.xs_off = int64_t((size_t(p.m) * 4 + size_t(S) * 8 + 15) / 16 * 16);
   const size_t smem = size_t(a.xs_off) + size_t(p.n) * 4;
+  // the cap is per kernel and process-wide (captured graphs included): the
+  // largest layout, m = S = n = 4096, never this launch's size
+  constexpr int kCap = (4096 * 4 + 4096 * 8) + 4096 * 4;
+  if (smem > size_t(kCap)) return KERDOCK_ERR_UNSUPPORTED;
   KD_CUDA_TRY(cudaFuncSetAttribute(kd::score_refine_kernel,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kCap));
   int64_t grid = int64_t(p.num_sms) * 8;
   if (grid > q) grid = q;
   kd::score_refine_kernel<<<unsigned(grid), kd::kRThreads, smem, p.stream>>>(a);

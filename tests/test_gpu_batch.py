@@ -173,3 +173,29 @@ def test_batch_n4096_plan_and_large_sparsities():
     for p in plans:
         p.close()
     torch.cuda.empty_cache()
+
+
+def test_batches_with_different_layouts_coexist():
+    # Each batch's graph keeps its own shared-memory layout; the kernel's
+    # process-wide shared-memory cap must admit all of them.  The batch with
+    # the larger layout (n = 1024, float32 rows and x) is captured first, the
+    # smaller one (n = 64) after it, and both are replayed in turn.
+    torch = torch_cuda()
+    K = build_and_load()
+    rng = np.random.default_rng(23)
+    big_shapes, small_shapes = [(1024, "f32")], [(64, "f32")]
+    pb, mb, rb, sb, metab = _setup(K, torch, big_shapes, [6], rng)
+    ps, ms_, rs, ss, metas = _setup(K, torch, small_shapes, [5], rng)
+    big = K.KerdockBatch(sb, graph=True)
+    small = K.KerdockBatch(ss, graph=True)
+    for _ in range(2):
+        big.launch()
+        small.launch()
+        big.sync()
+        small.sync()
+        _check(big, sb, metab, mb, rb, big_shapes, oracle_limit=0)
+        _check(small, ss, metas, ms_, rs, small_shapes, oracle_limit=0)
+    big.close()
+    small.close()
+    for p in pb + ps:
+        p.close()
