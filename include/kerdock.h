@@ -352,6 +352,18 @@ int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q, int
                          float eps, uint64_t seed, int32_t flags, int32_t* out_idx,
                          float* out_val, int32_t* out_count, void* ws, size_t ws_bytes);
 
+/* The first half of kerdock_apply_shared: the scores it ranks, without the
+ * selection and refinement.  scores[r * m + i] = |mu_r[i]|, where mu_r is
+ * Theorem 3's estimate for query r with the shared sample set: the entrywise
+ * median over the K batch means (the mean of the two middle ones for even K)
+ * of c_j R[l_j] / J (Algorithm 1's streaming step).  scores: device, q * m
+ * float32, 16-byte aligned, caller-owned.  ws as kerdock_apply_shared.
+ * kerdock_refine_scores(plan, X, q, ldx, scores, S, eps, flags, ...) on these
+ * scores gives kerdock_apply_shared's outputs.  Errors as
+ * kerdock_apply_shared; ALIGNMENT for a misaligned scores. */
+int kerdock_apply_shared_scores(kerdock_plan_t plan, const float* X_dev, int64_t q, int64_t ldx,
+                                uint64_t seed, float* scores, void* ws, size_t ws_bytes);
+
 /* Parameters with a guarantee (Theorem 3 with gamma = (eps - delta)/2, as
  * the argument around Algorithm 1 asks of mu): J = ceil(4 e^2 a^2 / gamma^2)
  * and K = ceil(2 ln(m / eta)), where a = max_i ||a_i|| (||A||_{2->inf}).

@@ -255,6 +255,83 @@ extern "C" size_t kerdock_apply_shared_workspace_bytes(kerdock_plan_t plan, int6
   return kd::shared_layout(plan->p, q).total;
 }
 
+namespace kd {
+namespace {
+
+// Steps a3-a6 with the shared sample set: scores[r * m + i] = |mu_r[i]|, the
+// entrywise median over the K batch means of query r (q x m, row pitch m).
+// The intermediate products live in the workspace at base (layout lay).
+int shared_scores(Plan& p, const float* X_dev, int64_t q, int64_t ldx, uint64_t seed, char* base,
+                  const SharedLayout& lay, float* scores) {
+  int64_t* ells = reinterpret_cast<int64_t*>(base + lay.ells);
+  __nv_bfloat16* S2 = reinterpret_cast<__nv_bfloat16*>(base + lay.S2);
+  __nv_bfloat16* X2 = reinterpret_cast<__nv_bfloat16*>(base + lay.X2);
+  float* C = reinterpret_cast<float*>(base + lay.C);
+  __nv_bfloat16* A3 = reinterpret_cast<__nv_bfloat16*>(base + lay.A3);
+  __nv_bfloat16* G3 = reinterpret_cast<__nv_bfloat16*>(base + lay.G3);
+  float* Y = reinterpret_cast<float*>(base + lay.Y);
+  const int64_t N = p.N, J = p.J, K = p.K, n = p.n, m = p.m, ldr = p.ldr;
+  const int P = p.dtype == KERDOCK_BF16 ? 2 : 3;
+  cudaStream_t st = p.stream;
+
+  shared_samples_kernel<<<grid_for(N), kThreads, 0, st>>>(
+      seed, N, p.L, p.k, n, p.signs(), p.sign_words, float(int64_t(1) << (p.k / 2)), ells, S2);
+  KD_CUDA_TRY(cudaGetLastError());
+  split_queries_kernel<<<grid_for(q), kThreads, 0, st>>>(X_dev, q, ldx, n, X2);
+  KD_CUDA_TRY(cudaGetLastError());
+  const int64_t lda3 = a3_stride(P, J);
+  const dim3 ggrid(unsigned((m + 63) / 64), unsigned((J + 31) / 32), unsigned(K));
+  if (P == 3)
+    gather_rows_kernel<float><<<ggrid, kThreads, 0, st>>>(static_cast<const float*>(p.repr), ldr,
+                                                          ells, J, m, lda3, G3);
+  else
+    gather_rows_kernel<__nv_bfloat16><<<ggrid, kThreads, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(p.repr), ldr, ells, J, m, lda3, G3);
+  KD_CUDA_TRY(cudaGetLastError());
+  // C = X S^T over [x_hi | x_lo] and [s | s]
+  GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
+  g1.status = p.status();
+  int rc = gemm_bf16_f32_split(g1, lay.split_c, C, N, q * N, st);
+  if (rc != KERDOCK_OK) return rc;
+  split_coef_kernel<<<grid_for(q), kThreads, 0, st>>>(C, lay.split_c.slices, q, N, J, K, P, lda3,
+                                                      1.0f / float(J), A3);
+  KD_CUDA_TRY(cudaGetLastError());
+  for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
+    GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * lda3, lda3, 1, G3 + k * ldr * lda3, lda3,
+                1};
+    g2.status = p.status();
+    rc = gemm_bf16_f32_split(g2, lay.split_y, Y + k * lay.split_y.slices * q * ldr, ldr, q * ldr,
+                             st);
+    if (rc != KERDOCK_OK) return rc;
+  }
+  const unsigned mgrid = grid_for((q * ((m + 3) / 4) + kThreads - 1) / kThreads);
+  const int sl = lay.split_y.slices;
+  if (K <= 2)
+    median_abs_kernel<2><<<mgrid, kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+  else if (K <= 4)
+    median_abs_kernel<4><<<mgrid, kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+  else if (K <= 8)
+    median_abs_kernel<8><<<mgrid, kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+  else
+    median_abs_kernel<kMaxK><<<mgrid, kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
+  KD_CUDA_TRY(cudaGetLastError());
+  return KERDOCK_OK;
+}
+
+// The checks both entry points share; on success *lay is the workspace layout.
+int shared_validate(Plan& p, const float* X_dev, int64_t q, int64_t ldx, void* ws,
+                    size_t ws_bytes, SharedLayout* lay) {
+  if (X_dev == nullptr || ldx < p.n) return KERDOCK_ERR_INVALID_ARG;
+  if (q > 65535 * int64_t(64)) return KERDOCK_ERR_UNSUPPORTED;  // GEMM grid rows
+  *lay = shared_layout(p, q);
+  if (ws == nullptr || ws_bytes < lay->total) return KERDOCK_ERR_CAPACITY;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return KERDOCK_ERR_ALIGNMENT;
+  return KERDOCK_OK;
+}
+
+}  // namespace
+}  // namespace kd
+
 extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int64_t q,
                                     int64_t ldx, float eps, uint64_t seed, int32_t flags,
                                     int32_t* out_idx, float* out_val, int32_t* out_count,
@@ -264,71 +341,33 @@ extern "C" int kerdock_apply_shared(kerdock_plan_t plan, const float* X_dev, int
   if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
   if (!p.preprocessed) return KERDOCK_ERR_NOT_PREPROCESSED;
   if (q == 0) return KERDOCK_OK;
-  if (X_dev == nullptr || out_idx == nullptr || out_val == nullptr || out_count == nullptr ||
-      ldx < p.n || flags < 0 || flags > KERDOCK_FLAG_FULL_OUTPUT)
+  if (out_idx == nullptr || out_val == nullptr || out_count == nullptr || flags < 0 ||
+      flags > KERDOCK_FLAG_FULL_OUTPUT)
     return KERDOCK_ERR_INVALID_ARG;
   if (!(flags & KERDOCK_FLAG_FULL_OUTPUT) && !(eps > 0.0f)) return KERDOCK_ERR_INVALID_ARG;
-  if (q > 65535 * int64_t(64)) return KERDOCK_ERR_UNSUPPORTED;  // GEMM grid rows
-  const kd::SharedLayout lay = kd::shared_layout(p, q);
-  if (ws == nullptr || ws_bytes < lay.total) return KERDOCK_ERR_CAPACITY;
-  if (reinterpret_cast<uintptr_t>(ws) & 255) return KERDOCK_ERR_ALIGNMENT;
-  char* base = static_cast<char*>(ws);
-  int64_t* ells = reinterpret_cast<int64_t*>(base + lay.ells);
-  __nv_bfloat16* S2 = reinterpret_cast<__nv_bfloat16*>(base + lay.S2);
-  __nv_bfloat16* X2 = reinterpret_cast<__nv_bfloat16*>(base + lay.X2);
-  float* C = reinterpret_cast<float*>(base + lay.C);
-  __nv_bfloat16* A3 = reinterpret_cast<__nv_bfloat16*>(base + lay.A3);
-  __nv_bfloat16* G3 = reinterpret_cast<__nv_bfloat16*>(base + lay.G3);
-  float* Y = reinterpret_cast<float*>(base + lay.Y);
-  float* scores = reinterpret_cast<float*>(base + lay.scores);
-  const int64_t N = p.N, J = p.J, K = p.K, n = p.n, m = p.m, ldr = p.ldr;
-  const int P = p.dtype == KERDOCK_BF16 ? 2 : 3;
-  cudaStream_t st = p.stream;
-
-  kd::shared_samples_kernel<<<kd::grid_for(N), kd::kThreads, 0, st>>>(
-      seed, N, p.L, p.k, n, p.signs(), p.sign_words, float(int64_t(1) << (p.k / 2)), ells, S2);
-  KD_CUDA_TRY(cudaGetLastError());
-  kd::split_queries_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(X_dev, q, ldx, n, X2);
-  KD_CUDA_TRY(cudaGetLastError());
-  const int64_t lda3 = kd::a3_stride(P, J);
-  const dim3 ggrid(unsigned((m + 63) / 64), unsigned((J + 31) / 32), unsigned(K));
-  if (P == 3)
-    kd::gather_rows_kernel<float><<<ggrid, kd::kThreads, 0, st>>>(
-        static_cast<const float*>(p.repr), ldr, ells, J, m, lda3, G3);
-  else
-    kd::gather_rows_kernel<__nv_bfloat16><<<ggrid, kd::kThreads, 0, st>>>(
-        static_cast<const __nv_bfloat16*>(p.repr), ldr, ells, J, m, lda3, G3);
-  KD_CUDA_TRY(cudaGetLastError());
-  // C = X S^T over [x_hi | x_lo] and [s | s]
-  kd::GemmArgs g1{int(q), int(N), int(2 * n), X2, 2 * n, 1, S2, 2 * n, 1};
-  g1.status = p.status();
-  int rc = kd::gemm_bf16_f32_split(g1, lay.split_c, C, N, q * N, st);
+  kd::SharedLayout lay;
+  int rc = kd::shared_validate(p, X_dev, q, ldx, ws, ws_bytes, &lay);
   if (rc != KERDOCK_OK) return rc;
-  kd::split_coef_kernel<<<kd::grid_for(q), kd::kThreads, 0, st>>>(
-      C, lay.split_c.slices, q, N, J, K, P, lda3, 1.0f / float(J), A3);
-  KD_CUDA_TRY(cudaGetLastError());
-  for (int64_t k = 0; k < K; ++k) {  // Y_k = C_k R_k / J
-    kd::GemmArgs g2{int(q), int(m), int(P * J), A3 + k * q * lda3, lda3, 1,
-                    G3 + k * ldr * lda3, lda3, 1};
-    g2.status = p.status();
-    rc = kd::gemm_bf16_f32_split(g2, lay.split_y, Y + k * lay.split_y.slices * q * ldr, ldr,
-                                 q * ldr, st);
-    if (rc != KERDOCK_OK) return rc;
-  }
-  {
-    const unsigned mgrid = kd::grid_for((q * ((m + 3) / 4) + kd::kThreads - 1) / kd::kThreads);
-    const int sl = lay.split_y.slices;
-    if (K <= 2)
-      kd::median_abs_kernel<2><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
-    else if (K <= 4)
-      kd::median_abs_kernel<4><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
-    else if (K <= 8)
-      kd::median_abs_kernel<8><<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
-    else
-      kd::median_abs_kernel<kd::kMaxK>
-          <<<mgrid, kd::kThreads, 0, st>>>(Y, sl, q, m, ldr, int(K), scores);
-  }
-  KD_CUDA_TRY(cudaGetLastError());
+  char* base = static_cast<char*>(ws);
+  float* scores = reinterpret_cast<float*>(base + lay.scores);
+  rc = kd::shared_scores(p, X_dev, q, ldx, seed, base, lay, scores);
+  if (rc != KERDOCK_OK) return rc;
   return kerdock_refine_scores(plan, X_dev, q, ldx, scores, p.S, eps, flags, out_idx, out_val,
                                out_count);
+}
+
+extern "C" int kerdock_apply_shared_scores(kerdock_plan_t plan, const float* X_dev, int64_t q,
+                                           int64_t ldx, uint64_t seed, float* scores, void* ws,
+                                           size_t ws_bytes) {
+  if (plan == nullptr || q < 0) return KERDOCK_ERR_INVALID_ARG;
+  kd::Plan& p = plan->p;
+  if (!p.bound) return KERDOCK_ERR_NOT_BOUND;
+  if (!p.preprocessed) return KERDOCK_ERR_NOT_PREPROCESSED;
+  if (q == 0) return KERDOCK_OK;
+  if (scores == nullptr) return KERDOCK_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(scores) & 15) return KERDOCK_ERR_ALIGNMENT;
+  kd::SharedLayout lay;
+  int rc = kd::shared_validate(p, X_dev, q, ldx, ws, ws_bytes, &lay);
+  if (rc != KERDOCK_OK) return rc;
+  return kd::shared_scores(p, X_dev, q, ldx, seed, static_cast<char*>(ws), lay, scores);
 }

@@ -42,7 +42,8 @@ EXPORTED = [
     "kerdock_mlp_loss", "kerdock_mlp_adamw", "kerdock_mlp_destroy", "kerdock_refine_scores",
     "kerdock_plan_clone", "kerdock_mlp_set_input", "kerdock_debug_wait_timeout",
     "kerdock_mlp_set_skip", "kerdock_theory_parameters", "kerdock_apply_shared_workspace_bytes",
-    "kerdock_apply_shared", "kerdock_debug_gemm", "kerdock_debug_set_poll_limit",
+    "kerdock_apply_shared", "kerdock_apply_shared_scores", "kerdock_debug_gemm",
+    "kerdock_debug_set_poll_limit",
     "kerdock_check_reconstruction", "kerdock_check_tight_frame",
 ]
 
@@ -153,6 +154,8 @@ def load_library(path=None):
         "kerdock_apply_shared_workspace_bytes": (c_sz, [P, c_i64]),
         "kerdock_apply_shared": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_float, ctypes.c_uint64,
                                                 c_i32, c_vp, c_vp, c_vp, c_vp, c_sz]),
+        "kerdock_apply_shared_scores": (ctypes.c_int, [P, c_vp, c_i64, c_i64, ctypes.c_uint64,
+                                                       c_vp, c_vp, c_sz]),
         "kerdock_theory_parameters": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                      ctypes.c_double, c_i64, ctypes.POINTER(c_i32),
                                                      ctypes.POINTER(c_i32)]),
@@ -207,6 +210,12 @@ def kerdock_apply_shared(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr, val_ptr
     _check(load_library().kerdock_apply_shared(plan, X_ptr, q, ldx, eps, seed, flags, idx_ptr,
                                                val_ptr, cnt_ptr, ws_ptr, ws_bytes),
            "kerdock_apply_shared")
+
+
+def kerdock_apply_shared_scores(plan, X_ptr, q, ldx, seed, scores_ptr, ws_ptr, ws_bytes):
+    _check(load_library().kerdock_apply_shared_scores(plan, X_ptr, q, ldx, seed, scores_ptr,
+                                                      ws_ptr, ws_bytes),
+           "kerdock_apply_shared_scores")
 
 
 def kerdock_theory_parameters(a_row_norm_max, eps, delta, eta, m):
@@ -559,6 +568,20 @@ class KerdockPlan:
 
     def sync(self):
         kerdock_sync(self.handle)
+
+    def shared_scores(self, X, seed, out=None):
+        """|mu| of every query with the shared sample set (q x m float32),
+        the scores kerdock_apply_shared ranks (kerdock_apply_shared_scores)."""
+        t = self.torch
+        assert X.dtype == t.float32 and X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        q = X.shape[0]
+        out = out if out is not None else t.empty((q, self.info["m"]), dtype=t.float32,
+                                                  device=self.device)
+        ws, nb = self.shared_workspace(q)
+        self._sync_stream()
+        kerdock_apply_shared_scores(self.handle, X.data_ptr(), q, X.stride(0), int(seed),
+                                    out.data_ptr(), ws.data_ptr(), nb)
+        return out
 
     def apply_shared(self, X, eps, seed, flags=0, out=None):
         """All rows of X share one sample set (kerdock_apply_shared)."""
