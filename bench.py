@@ -408,12 +408,13 @@ def collect_forms(args, K, torch, peak):
     """The three forms on this GPU, each summarised as a sub-object of the
     main line: precision (n = 4096, bfloat16 beside plain float32), batching
     (2048 mixed queries, one graph-captured launch) and the learned proposal
-    (n = 2048) against the plain method at equal support recall."""
+    (n = 2048) against the plain method at equal support recall; and Sec. 4's
+    (J, K) grid at n = 4096 in compact form."""
     fargs = argparse.Namespace(**vars(args))
     fargs.steps, fargs.warmup = min(args.steps, 5), 3
     out = {}
     for name, fn in (("precision_n4096", run_precision), ("batching_mixed_2048", run_batch),
-                     ("learned_n2048", run_learned)):
+                     ("learned_n2048", run_learned), ("fig1_grid_n4096", run_fig1_summary)):
         t0 = time.perf_counter()
         try:
             line = fn(fargs, K, torch, peak)
@@ -786,6 +787,20 @@ def run_fig1(args, K, torch, peak):
                   "note": "cuBLAS float32 through torch; gemv with A resident in L2"},
         "grid": grid, "gpu_launches": launches,
     }
+
+
+def run_fig1_summary(args, K, torch, peak):
+    """run_fig1 with its grid compacted for the main line: the paper's setting
+    (J = 375, K = 2) in full, and the fraction of exact trials per (J, K)."""
+    line = run_fig1(args, K, torch, peak)
+    grid = line.pop("grid")
+    Js = sorted({g["J"] for g in grid})
+    Ks = sorted({g["K"] for g in grid})
+    cell = {(g["J"], g["K"]): g for g in grid}
+    line["at_J375_K2"] = cell[(375, 2)]
+    line["exact_frac"] = {"J": Js, **{f"K={k}": [cell[(j, k)]["exact_frac"] for j in Js]
+                                       for k in Ks}}
+    return line
 
 
 def run_shared(args, K, torch, peak):

@@ -99,6 +99,20 @@ def test_fig1_errors_worst_case_over_trials():
     assert exact == pytest.approx(2 / 3)
 
 
+def test_fig1_summary_compacts_the_grid(monkeypatch):
+    # the main line carries the paper's cell (J = 375, K = 2) in full and the
+    # exact-trial fraction of every (J, K) cell, rows by K, columns by J
+    import bench
+    grid = [{"J": J, "K": Kk, "exact_frac": round(J / 1000 + Kk / 100, 4), "us_per_query": 1.0}
+            for Kk in (1, 2) for J in (375, 25, 1000)]
+    monkeypatch.setattr(bench, "run_fig1", lambda *a: {"value": 1.0, "grid": list(grid)})
+    line = bench.run_fig1_summary(None, None, None, None)
+    assert "grid" not in line
+    assert line["at_J375_K2"] == {"J": 375, "K": 2, "exact_frac": 0.395, "us_per_query": 1.0}
+    assert line["exact_frac"] == {"J": [25, 375, 1000], "K=1": [0.035, 0.385, 1.01],
+                                  "K=2": [0.045, 0.395, 1.02]}
+
+
 def test_profiled_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
     # committed DRAM counters count only while the profiled kernel's own source
     # files are unchanged, and only for the workload they were taken on
