@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <queue>
+#include <unordered_map>
 #include <vector>
 
 #include "kerdock_internal.cuh"
@@ -118,25 +119,21 @@ void destroy_graph(kerdock_batch_s* b) {
 void deal(kerdock_batch_s* b, const std::vector<double>& cost) {
   const size_t count = cost.size();
   // plan groups, identified by representation, in order of first appearance
-  std::vector<const void*> reprs;
+  std::unordered_map<const void*, int> group_of;
   std::vector<uint32_t> group_row_bytes;
   std::vector<int> group(count);
   for (size_t i = 0; i < count; ++i) {
-    const void* r = b->descs[i].R;
-    size_t g = 0;
-    while (g < reprs.size() && reprs[g] != r) ++g;
-    if (g == reprs.size()) {
-      reprs.push_back(r);
-      group_row_bytes.push_back(b->descs[i].row_bytes);
-    }
-    group[i] = int(g);
+    const auto ins = group_of.emplace(b->descs[i].R, int(group_row_bytes.size()));
+    if (ins.second) group_row_bytes.push_back(b->descs[i].row_bytes);
+    group[i] = ins.first->second;
   }
-  std::vector<int> gorder(reprs.size());
+  const size_t ngroups = group_row_bytes.size();
+  std::vector<int> gorder(ngroups);
   for (size_t g = 0; g < gorder.size(); ++g) gorder[g] = int(g);
   std::stable_sort(gorder.begin(), gorder.end(), [&](int x, int y) {
     return group_row_bytes[size_t(x)] > group_row_bytes[size_t(y)];
   });
-  std::vector<int> grank(reprs.size());
+  std::vector<int> grank(ngroups);
   for (size_t k = 0; k < gorder.size(); ++k) grank[size_t(gorder[k])] = int(k);
   std::vector<int32_t> by_cost(count);
   for (size_t i = 0; i < count; ++i) by_cost[i] = int32_t(i);
