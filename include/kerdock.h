@@ -243,6 +243,19 @@ int kerdock_batch_set_tuning(kerdock_batch_t batch, int32_t ring_kb, int32_t cro
  * NaN cost. */
 int kerdock_batch_set_costs(kerdock_batch_t batch, const double* cost, int64_t count);
 
+/* Test entry (host only, no device work): the schedule kerdock_batch_create
+ * makes for count queries over grid CTAs, where plan_ids[i] identifies query
+ * i's plan (any value, equal for queries of one plan), row_bytes[i] is that
+ * plan's representation row size and cost[i] the query's estimated cost.
+ * Plans in decreasing row size (ties: first appearance), each plan's queries
+ * longest first (ties: list order) onto the least-loaded CTA (ties: lowest
+ * index), loads carried from plan to plan.  order_out: count int32, the
+ * queries CTA by CTA; cta_start_out: grid + 1 int64.  INVALID_ARG for a NULL
+ * pointer, count < 1, grid < 1 or a negative, infinite or NaN cost. */
+int kerdock_debug_batch_schedule(const void* const* plan_ids, const uint32_t* row_bytes,
+                                 const double* cost, int64_t count, int32_t grid,
+                                 int32_t* order_out, int64_t* cta_start_out);
+
 /* CTAs of the batch's launch (one per SM, at most one per query); 0 for a
  * null batch. */
 int32_t kerdock_batch_ctas(kerdock_batch_t batch);

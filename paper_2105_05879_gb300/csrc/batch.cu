@@ -107,6 +107,54 @@ void destroy_graph(kerdock_batch_s* b) {
   b->graph = nullptr;
 }
 
+// The schedule of deal() as a pure function of the queries' plans (any
+// pointer identifying each query's plan), row bytes and costs: order[] lists
+// the queries CTA by CTA, CTA c's from cta_start[c] to cta_start[c + 1].
+void plan_major_schedule(const void* const* plan_ids, const uint32_t* row_bytes,
+                         const double* cost, int64_t count, int grid, std::vector<int32_t>& order,
+                         std::vector<int64_t>& cta_start) {
+  // plan groups in order of first appearance
+  std::unordered_map<const void*, int> group_of;
+  std::vector<uint32_t> group_row_bytes;
+  std::vector<int> group(static_cast<size_t>(count));
+  for (int64_t i = 0; i < count; ++i) {
+    const auto ins = group_of.emplace(plan_ids[i], int(group_row_bytes.size()));
+    if (ins.second) group_row_bytes.push_back(row_bytes[i]);
+    group[size_t(i)] = ins.first->second;
+  }
+  const size_t ngroups = group_row_bytes.size();
+  std::vector<int> gorder(ngroups);
+  for (size_t g = 0; g < ngroups; ++g) gorder[g] = int(g);
+  std::stable_sort(gorder.begin(), gorder.end(), [&](int x, int y) {
+    return group_row_bytes[size_t(x)] > group_row_bytes[size_t(y)];
+  });
+  std::vector<int> grank(ngroups);
+  for (size_t k = 0; k < ngroups; ++k) grank[size_t(gorder[k])] = int(k);
+  std::vector<int32_t> by_cost(static_cast<size_t>(count));
+  for (int64_t i = 0; i < count; ++i) by_cost[size_t(i)] = int32_t(i);
+  std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t x, int32_t y) {
+    const int gx = grank[size_t(group[size_t(x)])], gy = grank[size_t(group[size_t(y)])];
+    return gx != gy ? gx < gy : cost[x] > cost[y];
+  });
+  using Load = std::pair<double, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+  std::vector<std::vector<int32_t>> per_cta(static_cast<size_t>(grid));
+  for (int32_t qi : by_cost) {
+    Load top = heap.top();
+    heap.pop();
+    per_cta[size_t(top.second)].push_back(qi);
+    top.first += cost[qi];
+    heap.push(top);
+  }
+  order.clear();
+  cta_start.assign(size_t(grid) + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    cta_start[size_t(c) + 1] = cta_start[size_t(c)] + int64_t(per_cta[size_t(c)].size());
+    for (int32_t qi : per_cta[size_t(c)]) order.push_back(qi);
+  }
+}
+
 // Deal the queries to the CTAs by cost (any unit), plan by plan: the plans in
 // decreasing order of row size, each plan's queries longest first onto the
 // least-loaded CTA (loads carried from plan to plan), every CTA running its
@@ -118,46 +166,14 @@ void destroy_graph(kerdock_batch_s* b) {
 // shuffled.  Fills the host order and per-CTA start arrays.
 void deal(kerdock_batch_s* b, const std::vector<double>& cost) {
   const size_t count = cost.size();
-  // plan groups, identified by representation, in order of first appearance
-  std::unordered_map<const void*, int> group_of;
-  std::vector<uint32_t> group_row_bytes;
-  std::vector<int> group(count);
+  std::vector<const void*> plan_ids(count);
+  std::vector<uint32_t> row_bytes(count);
   for (size_t i = 0; i < count; ++i) {
-    const auto ins = group_of.emplace(b->descs[i].R, int(group_row_bytes.size()));
-    if (ins.second) group_row_bytes.push_back(b->descs[i].row_bytes);
-    group[i] = ins.first->second;
+    plan_ids[i] = b->descs[i].R;
+    row_bytes[i] = b->descs[i].row_bytes;
   }
-  const size_t ngroups = group_row_bytes.size();
-  std::vector<int> gorder(ngroups);
-  for (size_t g = 0; g < gorder.size(); ++g) gorder[g] = int(g);
-  std::stable_sort(gorder.begin(), gorder.end(), [&](int x, int y) {
-    return group_row_bytes[size_t(x)] > group_row_bytes[size_t(y)];
-  });
-  std::vector<int> grank(ngroups);
-  for (size_t k = 0; k < gorder.size(); ++k) grank[size_t(gorder[k])] = int(k);
-  std::vector<int32_t> by_cost(count);
-  for (size_t i = 0; i < count; ++i) by_cost[i] = int32_t(i);
-  std::stable_sort(by_cost.begin(), by_cost.end(), [&](int32_t x, int32_t y) {
-    const int gx = grank[size_t(group[size_t(x)])], gy = grank[size_t(group[size_t(y)])];
-    return gx != gy ? gx < gy : cost[size_t(x)] > cost[size_t(y)];
-  });
-  using Load = std::pair<double, int>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
-  std::vector<std::vector<int32_t>> per_cta(size_t(b->grid));
-  for (int32_t qi : by_cost) {
-    Load top = heap.top();
-    heap.pop();
-    per_cta[size_t(top.second)].push_back(qi);
-    top.first += cost[size_t(qi)];
-    heap.push(top);
-  }
-  b->order.clear();
-  b->cta_start.assign(size_t(b->grid) + 1, 0);
-  for (int c = 0; c < b->grid; ++c) {
-    b->cta_start[size_t(c) + 1] = b->cta_start[size_t(c)] + int64_t(per_cta[size_t(c)].size());
-    for (int32_t qi : per_cta[size_t(c)]) b->order.push_back(qi);
-  }
+  plan_major_schedule(plan_ids.data(), row_bytes.data(), cost.data(), int64_t(count), b->grid,
+                      b->order, b->cta_start);
 }
 
 // Upload the schedule (order and per-CTA starts) on the batch's stream and
@@ -339,6 +355,22 @@ int kerdock_batch_set_costs(kerdock_batch_t batch, const double* cost, int64_t c
   // the kernel (and a captured graph) reads the schedule through the same
   // device arrays, so the new one takes effect from the next launch
   if (upload_schedule(batch) != cudaSuccess) return KERDOCK_ERR_CUDA;
+  return KERDOCK_OK;
+}
+
+int kerdock_debug_batch_schedule(const void* const* plan_ids, const uint32_t* row_bytes,
+                                 const double* cost, int64_t count, int32_t grid,
+                                 int32_t* order_out, int64_t* cta_start_out) {
+  if (plan_ids == nullptr || row_bytes == nullptr || cost == nullptr || order_out == nullptr ||
+      cta_start_out == nullptr || count < 1 || count > (int64_t(1) << 31) - 1 || grid < 1)
+    return KERDOCK_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < count; ++i)
+    if (!(cost[i] >= 0.0) || !(cost[i] <= 1e300)) return KERDOCK_ERR_INVALID_ARG;
+  std::vector<int32_t> order;
+  std::vector<int64_t> cta_start;
+  plan_major_schedule(plan_ids, row_bytes, cost, count, grid, order, cta_start);
+  std::copy(order.begin(), order.end(), order_out);
+  std::copy(cta_start.begin(), cta_start.end(), cta_start_out);
   return KERDOCK_OK;
 }
 

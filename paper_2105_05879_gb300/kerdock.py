@@ -34,7 +34,7 @@ EXPORTED = [
     "kerdock_strerror", "kerdock_version", "kerdock_apply_noalloc",
     "kerdock_batch_workspace_bytes", "kerdock_batch_create", "kerdock_batch_launch",
     "kerdock_batch_set_tuning", "kerdock_batch_set_costs", "kerdock_batch_ctas",
-    "kerdock_batch_set_schedule", "kerdock_batch_tune",
+    "kerdock_batch_set_schedule", "kerdock_debug_batch_schedule", "kerdock_batch_tune",
     "kerdock_batch_sync",
     "kerdock_batch_destroy", "kerdock_plan_set_tuning", "kerdock_plan_tune",
     "kerdock_mlp_create", "kerdock_mlp_sizes", "kerdock_mlp_bind", "kerdock_mlp_pointers",
@@ -119,6 +119,11 @@ def load_library(path=None):
         "kerdock_batch_set_tuning": (ctypes.c_int, [P, c_i32, c_i32]),
         "kerdock_batch_set_costs": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double), c_i64]),
         "kerdock_batch_ctas": (c_i32, [P]),
+        "kerdock_debug_batch_schedule": (ctypes.c_int, [ctypes.POINTER(c_vp),
+                                                        ctypes.POINTER(ctypes.c_uint32),
+                                                        ctypes.POINTER(ctypes.c_double), c_i64,
+                                                        c_i32, ctypes.POINTER(c_i32),
+                                                        ctypes.POINTER(c_i64)]),
         "kerdock_batch_set_schedule": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32),
                                                       ctypes.POINTER(c_i64), c_i32]),
         "kerdock_batch_tune": (ctypes.c_int, [P, c_i32, ctypes.POINTER(ctypes.c_int32),
@@ -285,6 +290,23 @@ def kerdock_batch_set_costs(batch, costs):
     c = np.ascontiguousarray(costs, dtype=np.float64)
     _check(load_library().kerdock_batch_set_costs(
         batch, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), c.size), "kerdock_batch_set_costs")
+
+
+def kerdock_debug_batch_schedule(plan_ids, row_bytes, costs, grid):
+    """The library's batch schedule for these queries (host only): a list of
+    per-CTA lists of query indices."""
+    n = len(costs)
+    ids = (ctypes.c_void_p * n)(*[int(p) for p in plan_ids])
+    rb = np.ascontiguousarray(row_bytes, dtype=np.uint32)
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    start = np.zeros(max(grid, 0) + 1, dtype=np.int64)
+    _check(load_library().kerdock_debug_batch_schedule(
+        ids, rb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+        c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n, grid,
+        order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        start.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "kerdock_debug_batch_schedule")
+    return [order[start[g]:start[g + 1]].tolist() for g in range(grid)]
 
 
 def kerdock_batch_ctas(batch):

@@ -81,3 +81,66 @@ def test_support_recall_counts_entries_and_exact_queries():
     recall, exact = learned.support_recall(idx, cnt, truth)
     assert recall == pytest.approx(4 / 6)             # 3 + 1 + 0 of 3 + 2 + 1
     assert exact == pytest.approx(1 / 3)              # only query 0 is exact
+
+
+def _schedule_reference(plan_ids, row_bytes, costs, grid):
+    # the batch schedule restated: plan groups by first appearance, ordered by
+    # decreasing row size (stable); queries by group, then decreasing cost
+    # (stable); each onto the least-loaded CTA, lowest index on ties
+    import heapq
+    first = {}
+    for i, p in enumerate(plan_ids):
+        first.setdefault(p, (len(first), row_bytes[i]))
+    groups = sorted(first, key=lambda p: (-first[p][1], first[p][0]))
+    rank = {p: r for r, p in enumerate(groups)}
+    qs = sorted(range(len(costs)), key=lambda i: (rank[plan_ids[i]], -costs[i], i))
+    heap = [(0.0, c) for c in range(grid)]
+    lists = [[] for _ in range(grid)]
+    for q in qs:
+        load, c = heapq.heappop(heap)
+        lists[c].append(q)
+        heapq.heappush(heap, (load + costs[q], c))
+    return lists
+
+
+@pytest.mark.parametrize("seed,grid,nplans", [(0, 4, 3), (1, 7, 1), (2, 152, 7), (3, 3, 5)])
+def test_batch_schedule_is_plan_major_longest_first(seed, grid, nplans):
+    from paper_2105_05879_gb300 import build as kbuild
+    from paper_2105_05879_gb300 import kerdock as K
+    kbuild.build()
+    K.load_library()
+    rng = np.random.default_rng(seed)
+    count = int(rng.integers(grid, 6 * grid + 20))
+    plans = [0x1000 * (p + 1) for p in range(nplans)]
+    prow = {p: int(rng.choice([256, 1024, 2048, 4096, 8192, 16384])) for p in plans}
+    ids = [plans[int(rng.integers(nplans))] for _ in range(count)]
+    rb = [prow[p] for p in ids]
+    costs = rng.integers(1, 50, count).astype(np.float64) * 1e6   # repeated values: ties
+    got = K.kerdock_debug_batch_schedule(ids, rb, costs, grid)
+    assert got == _schedule_reference(ids, rb, costs.tolist(), grid)
+    assert sorted(q for lst in got for q in lst) == list(range(count))
+    # every CTA runs its queries plan by plan, larger rows first (equal rows:
+    # the plan met first in the list), and each plan's longest first
+    first = {}
+    for i, p in enumerate(ids):
+        first.setdefault(p, i)
+    for lst in got:
+        keys = [(-rb[q], first[ids[q]], -costs[q]) for q in lst]
+        assert keys == sorted(keys)
+    # greedy balance: no CTA ends more than one query's cost above another
+    loads = [sum(costs[q] for q in lst) for lst in got]
+    assert max(loads) - min(loads) <= costs.max()
+
+
+def test_batch_schedule_rejects_bad_arguments():
+    from paper_2105_05879_gb300 import build as kbuild
+    from paper_2105_05879_gb300 import kerdock as K
+    kbuild.build()
+    K.load_library()
+    for costs in ([1.0, -1.0], [1.0, float("nan")], [float("inf"), 1.0]):
+        with pytest.raises(K.KerdockError) as e:
+            K.kerdock_debug_batch_schedule([1, 2], [4, 4], costs, 2)
+        assert e.value.code == -1
+    with pytest.raises(K.KerdockError) as e:
+        K.kerdock_debug_batch_schedule([1], [4], [1.0], 0)
+    assert e.value.code == -1
