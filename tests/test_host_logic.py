@@ -144,3 +144,32 @@ def test_batch_schedule_rejects_bad_arguments():
     with pytest.raises(K.KerdockError) as e:
         K.kerdock_debug_batch_schedule([1], [4], [1.0], 0)
     assert e.value.code == -1
+
+
+def test_clock_sampler_summarises_the_record(tmp_path):
+    # nvidia-smi's CSV (no header, no units): the median SM clock under load,
+    # the maximum clock, and every throttle reason seen Active; lines that do
+    # not parse are skipped
+    import bench
+
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    s.fh = open(s.path, "w")
+    s.fh.write("0, 2070, 2070, 800.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+               "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+               "0, [N/A], 2070, 0.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+               "garbage\n"
+               "0, 2070, 2070, 900.0, 0x20, Not Active, Active, Not Active, Not Active\n")
+    s.proc = _Proc()
+    out = s.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0,
+                   "reasons": ["hw_thermal_slowdown", "sw_power_cap"], "samples": 3}
+    assert not (tmp_path / "clocks.csv").exists()
+    assert bench.ClockSampler(0).stop() is None     # never started: no record
